@@ -1,0 +1,656 @@
+/*
+ * wcns_oracle.c -- plain, slow FP64 CPU oracle of the TCNS scheme
+ * (fifth-order WCNS with TENO-style ENO-like stencil selection) of
+ * Zhang, Zhang & Xu, "Towards optimal high-order compact schemes for
+ * simulating compressible flows" (arXiv 1810.07806).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the correctness reference that
+ * the CUDA library is compared against.  Only the test suite, the package
+ * smoke check and the CPU-baseline leg of the benchmark may load it.  It
+ * shares no code, header, table or helper with the CUDA path.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fopenmp -shared -fPIC (no FMA
+ * contraction, so every product and sum below rounds as written).
+ *
+ * What it computes, step by step, in the paper's order:
+ *   Eq. 2    du_i/dt = -f'_i, summed over directions (dimension by dimension)
+ *   Eq. 3    sixth-order explicit midpoint-to-node difference (MD)
+ *   Eq. 6    scalar upwind midpoint flux (scalar problems)
+ *   Eq. 8-11 three 3-point sub-stencils and their Taylor interpolants
+ *   Eq. 12-13 convex combination, optimal weights d = (1, 10, 5)/16
+ *   Eq. 14-15 Jiang-Shu weights and the WCNS smoothness indicator beta_k
+ *   Eq. 16-19 TENO scale separation gamma_k, normalisation chi_k, sharp
+ *            cutoff delta_k, and the final weights omega_k^(T)
+ *   Sec. 3   characteristic-variable interpolation, ideal gas, van Leer or
+ *            Roe midpoint flux, third-order SSP Runge-Kutta under a CFL rule.
+ *
+ * Readings of points the paper leaves open (each one is listed in the
+ * design notes with its reason):
+ *   - MD coefficients a = (75/64, -25/384, 3/640): sixth-order Taylor
+ *     matching of Eq. 3 (the paper defers them to its references).
+ *   - The characteristic projection uses the eigenvectors of the flux
+ *     Jacobian at the Roe average of the two nodes that bound the face; the
+ *     same projection serves the left- and right-biased interpolations.
+ *   - The right-biased value u_R at face j+1/2 is the left-biased procedure
+ *     applied to the mirrored stencil (u_{j+3}, u_{j+2}, u_{j+1}, u_j, u_{j-1}).
+ *   - chi_k is evaluated in a ratio form (divide every gamma by the largest
+ *     before the q-th power), algebraically identical to Eq. 17 but free of
+ *     overflow; the literal form is also evaluated and the two must agree
+ *     where the literal form is finite.  delta_k = 0 iff chi_k < C_T.
+ *   - SSP-RK3 in Shu-Osher form; dt = CFL / max_i sum_d (|u_d| + c)/h_d.
+ *   - Transmissive boundaries copy the boundary node into 5 ghost nodes;
+ *     periodic boundaries wrap.
+ *   - If an interpolated midpoint state has rho <= 0 or p <= 0 the face
+ *     falls back to first order (U_L = U_j, U_R = U_{j+1}) and is counted.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORA_MAXV 5
+#define ORA_GHOST 5
+
+/* Scheme switches (the oracle's own numbering). */
+enum { ORA_FLUX_ROE = 0, ORA_FLUX_VANLEER = 1 };
+enum { ORA_W_TENO = 0, ORA_W_JS = 1, ORA_W_LINEAR = 2 };
+
+typedef struct {
+    int ndim;             /* 1, 2 or 3                                   */
+    int n[3];             /* nodes per direction (x, y, z)               */
+    double h[3];          /* node spacing per direction                  */
+    int periodic[3];      /* 1 = periodic, 0 = transmissive              */
+    double gamma;         /* ratio of specific heats                     */
+    int flux;             /* ORA_FLUX_*                                  */
+    int weights;          /* ORA_W_*                                     */
+    double C, eps, CT;    /* Eq. 16, 18: 1, 1e-40, 1e-5                  */
+    int q;                /* Eq. 16: 6                                   */
+    double eps_js;        /* Eq. 14: 1e-6                                */
+    int characteristic;   /* 1 = interpolate characteristic variables    */
+} ora_cfg;
+
+/* ------------------------------------------------------------------ */
+/* Eq. 3: the MD coefficients from sixth-order Taylor matching.        */
+/* sum a_m (2m-1) = 1, sum a_m (2m-1)^3 = 0, sum a_m (2m-1)^5 = 0.     */
+/* ------------------------------------------------------------------ */
+static const double MD_A1 = 75.0 / 64.0;
+static const double MD_A2 = -25.0 / 384.0;
+static const double MD_A3 = 3.0 / 640.0;
+
+void ora_md_coeffs(double a[3]) { a[0] = MD_A1; a[1] = MD_A2; a[2] = MD_A3; }
+
+/* ------------------------------------------------------------------ */
+/* Eq. 10-11 times h and h^2 (the h-free forms), Eq. 9, Eq. 15.        */
+/* s[0..4] = u_{i-2}, u_{i-1}, u_i, u_{i+1}, u_{i+2}.                  */
+/* ------------------------------------------------------------------ */
+static void substencil_derivatives(const double s[5], double D1[3], double D2[3])
+{
+    /* h u^(1)_{i,k}, Eq. 10 */
+    D1[0] = 0.5 * (s[0] - 4.0 * s[1] + 3.0 * s[2]);
+    D1[1] = 0.5 * (s[3] - s[1]);
+    D1[2] = 0.5 * (-3.0 * s[2] + 4.0 * s[3] - s[4]);
+    /* h^2 u^(2)_{i,k}, Eq. 11 */
+    D2[0] = s[0] - 2.0 * s[1] + s[2];
+    D2[1] = s[1] - 2.0 * s[2] + s[3];
+    D2[2] = s[2] - 2.0 * s[3] + s[4];
+}
+
+/* Eq. 16-18 in ratio form: returns flags (bit k-1 = delta_k); writes chi
+ * (ratio form), chi_lit (literal Eq. 16-17, may be inf/nan). */
+static int teno_select(const double beta[3], double C, double eps, double CT, int q,
+                       double chi[3], double chi_lit[3])
+{
+    double tau = fabs(beta[0] - beta[2]);             /* tau_5 */
+    double g[3], gmax = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        g[k] = C + tau / (beta[k] + eps);
+        if (g[k] > gmax) gmax = g[k];
+    }
+    double s[3], ssum = 0.0, lit[3], litsum = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        double r = g[k] / gmax, p = 1.0, pl = 1.0;
+        for (int e = 0; e < q; ++e) { p *= r; pl *= g[k]; }
+        s[k] = p; ssum += p;
+        lit[k] = pl; litsum += pl;
+    }
+    int flags = 0;
+    for (int k = 0; k < 3; ++k) {
+        chi[k] = s[k] / ssum;
+        chi_lit[k] = lit[k] / litsum;
+        if (!(chi[k] < CT)) flags |= 1 << k;         /* Eq. 18: kept unless chi < C_T */
+    }
+    return flags;
+}
+
+/* Left-biased node-to-midpoint interpolation u_{L,i+1/2} from s[0..4].
+ * force_flags >= 0 forces delta (for tests); otherwise the weights are
+ * chosen by cfg->weights.  Returns the flags used (TENO) or 7. */
+static double interp_left(const ora_cfg* cfg, const double s[5], int force_flags,
+                          int* flags_out, double* margin_out, double* litdev_out)
+{
+    static const double d[3] = {1.0 / 16.0, 10.0 / 16.0, 5.0 / 16.0};  /* Eq. 13 */
+    double D1[3], D2[3], beta[3], uk[3], w[3];
+    substencil_derivatives(s, D1, D2);
+    for (int k = 0; k < 3; ++k) {
+        uk[k] = s[2] + D1[k] * 0.5 + D2[k] * 0.125;          /* Eq. 9, dx = h/2 */
+        beta[k] = D1[k] * D1[k] + D2[k] * D2[k];             /* Eq. 15 */
+    }
+    int flags = 7;
+    double margin = INFINITY, litdev = 0.0;
+    if (force_flags >= 0) {
+        flags = force_flags;
+    } else if (cfg->weights == ORA_W_TENO) {
+        double chi[3], chi_lit[3];
+        flags = teno_select(beta, cfg->C, cfg->eps, cfg->CT, cfg->q, chi, chi_lit);
+        for (int k = 0; k < 3; ++k) {
+            double m = fabs(chi[k] - cfg->CT);
+            if (m < margin) margin = m;
+            if (isfinite(chi_lit[k])) {
+                double dv = fabs(chi_lit[k] - chi[k]);
+                if (dv > litdev) litdev = dv;
+            }
+        }
+    }
+    if (force_flags < 0 && cfg->weights == ORA_W_JS) {
+        double a[3], asum = 0.0;                               /* Eq. 14 */
+        for (int k = 0; k < 3; ++k) {
+            double b = beta[k] + cfg->eps_js;
+            a[k] = d[k] / (b * b);
+            asum += a[k];
+        }
+        for (int k = 0; k < 3; ++k) w[k] = a[k] / asum;
+    } else {
+        double dsum = 0.0;                                     /* Eq. 19 */
+        for (int k = 0; k < 3; ++k) dsum += ((flags >> k) & 1) ? d[k] : 0.0;
+        for (int k = 0; k < 3; ++k) w[k] = (((flags >> k) & 1) ? d[k] : 0.0) / dsum;
+    }
+    double u = 0.0;                                            /* Eq. 12 */
+    for (int k = 0; k < 3; ++k) u += w[k] * uk[k];
+    if (flags_out) *flags_out = flags;
+    if (margin_out) *margin_out = margin;
+    if (litdev_out) *litdev_out = litdev;
+    return u;
+}
+
+/* Exported point kernel for tests: left-biased interpolation of one
+ * 5-point stencil.  Returns u_L; writes delta flags, cutoff margin
+ * min_k |chi_k - C_T| and the ratio-vs-literal chi deviation. */
+double ora_interp_left(const ora_cfg* cfg, const double s[5], int force_flags,
+                       int* flags, double* margin, double* litdev)
+{
+    return interp_left(cfg, s, force_flags, flags, margin, litdev);
+}
+
+/* Exported: the chi_k and flags of one stencil (ratio form), for tests. */
+int ora_teno_chi(const ora_cfg* cfg, const double s[5], double chi[3], double chi_lit[3],
+                 double beta_out[3])
+{
+    double D1[3], D2[3], beta[3];
+    substencil_derivatives(s, D1, D2);
+    for (int k = 0; k < 3; ++k) beta[k] = D1[k] * D1[k] + D2[k] * D2[k];
+    if (beta_out) for (int k = 0; k < 3; ++k) beta_out[k] = beta[k];
+    return teno_select(beta, cfg->C, cfg->eps, cfg->CT, cfg->q, chi, chi_lit);
+}
+
+/* ------------------------------------------------------------------ */
+/* Euler equations, ideal gas (Sec. 3): U = (rho, rho u_1..u_nd, E).   */
+/* ------------------------------------------------------------------ */
+static double pressure(int nd, double gamma, const double* U)
+{
+    double ke = 0.0;
+    for (int a = 0; a < nd; ++a) ke += U[1 + a] * U[1 + a];
+    ke = 0.5 * ke / U[0];
+    return (gamma - 1.0) * (U[nd + 1] - ke);
+}
+
+/* Physical flux in direction d. */
+static void phys_flux(int nd, int d, double gamma, const double* U, double* F)
+{
+    double rho = U[0], un = U[1 + d] / rho, p = pressure(nd, gamma, U);
+    F[0] = U[1 + d];
+    for (int a = 0; a < nd; ++a) F[1 + a] = U[1 + a] * un;
+    F[1 + d] += p;
+    F[nd + 1] = (U[nd + 1] + p) * un;
+}
+
+void ora_phys_flux(int nd, int d, double gamma, const double* U, double* F)
+{
+    phys_flux(nd, d, gamma, U, F);
+}
+
+/* Eigen-system of dF_d/dU at the Roe average of states Ua and Ub.
+ * R is nv x nv row-major with right eigenvectors as COLUMNS; L holds the
+ * left eigenvectors as ROWS, L = R^{-1}; lam the eigenvalues.  Field order:
+ * (u_n - c, u_n [entropy], tangential shear waves in axis order, u_n + c). */
+static void roe_eigen(int nd, int d, double gamma, const double* Ua, const double* Ub,
+                      double* R, double* L, double* lam)
+{
+    const int nv = nd + 2;
+    double ra = sqrt(Ua[0]), rb = sqrt(Ub[0]);
+    double vel[3] = {0, 0, 0}, q2 = 0.0;
+    double Ha = (Ua[nd + 1] + pressure(nd, gamma, Ua)) / Ua[0];
+    double Hb = (Ub[nd + 1] + pressure(nd, gamma, Ub)) / Ub[0];
+    for (int a = 0; a < nd; ++a) {
+        vel[a] = (ra * (Ua[1 + a] / Ua[0]) + rb * (Ub[1 + a] / Ub[0])) / (ra + rb);
+        q2 += vel[a] * vel[a];
+    }
+    double H = (ra * Ha + rb * Hb) / (ra + rb);
+    double c2 = (gamma - 1.0) * (H - 0.5 * q2);
+    double c = sqrt(c2);
+    double un = vel[d];
+    double b1 = (gamma - 1.0) / c2, b2 = 0.5 * b1 * q2;
+    memset(R, 0, sizeof(double) * nv * nv);
+    memset(L, 0, sizeof(double) * nv * nv);
+#define RR(i, j) R[(i) * nv + (j)]
+#define LL(i, j) L[(i) * nv + (j)]
+    /* column 0: acoustic u_n - c */
+    RR(0, 0) = 1.0;
+    for (int a = 0; a < nd; ++a) RR(1 + a, 0) = vel[a] - (a == d ? c : 0.0);
+    RR(nv - 1, 0) = H - un * c;
+    /* column 1: entropy */
+    RR(0, 1) = 1.0;
+    for (int a = 0; a < nd; ++a) RR(1 + a, 1) = vel[a];
+    RR(nv - 1, 1) = 0.5 * q2;
+    /* shear columns */
+    int col = 2;
+    for (int t = 0; t < nd; ++t) {
+        if (t == d) continue;
+        RR(1 + t, col) = 1.0;
+        RR(nv - 1, col) = vel[t];
+        ++col;
+    }
+    /* last column: acoustic u_n + c */
+    RR(0, nv - 1) = 1.0;
+    for (int a = 0; a < nd; ++a) RR(1 + a, nv - 1) = vel[a] + (a == d ? c : 0.0);
+    RR(nv - 1, nv - 1) = H + un * c;
+
+    /* rows of L */
+    LL(0, 0) = 0.5 * (b2 + un / c);
+    for (int a = 0; a < nd; ++a) LL(0, 1 + a) = 0.5 * (-b1 * vel[a] - (a == d ? 1.0 / c : 0.0));
+    LL(0, nv - 1) = 0.5 * b1;
+    LL(1, 0) = 1.0 - b2;
+    for (int a = 0; a < nd; ++a) LL(1, 1 + a) = b1 * vel[a];
+    LL(1, nv - 1) = -b1;
+    int row = 2;
+    for (int t = 0; t < nd; ++t) {
+        if (t == d) continue;
+        LL(row, 0) = -vel[t];
+        LL(row, 1 + t) = 1.0;
+        ++row;
+    }
+    LL(nv - 1, 0) = 0.5 * (b2 - un / c);
+    for (int a = 0; a < nd; ++a) LL(nv - 1, 1 + a) = 0.5 * (-b1 * vel[a] + (a == d ? 1.0 / c : 0.0));
+    LL(nv - 1, nv - 1) = 0.5 * b1;
+#undef RR
+#undef LL
+    lam[0] = un - c;
+    for (int k = 1; k < nv - 1; ++k) lam[k] = un;
+    lam[nv - 1] = un + c;
+}
+
+void ora_roe_eigen(int nd, int d, double gamma, const double* Ua, const double* Ub,
+                   double* R, double* L, double* lam)
+{
+    roe_eigen(nd, d, gamma, Ua, Ub, R, L, lam);
+}
+
+/* Roe flux-difference splitting (Roe 1981):
+ * F = 1/2 (F(U_L) + F(U_R)) - 1/2 R |Lambda| L (U_R - U_L), Roe average of U_L, U_R. */
+static void roe_flux(int nd, int d, double gamma, const double* UL, const double* UR, double* F)
+{
+    const int nv = nd + 2;
+    double R[ORA_MAXV * ORA_MAXV], Lm[ORA_MAXV * ORA_MAXV], lam[ORA_MAXV];
+    double FL[ORA_MAXV], FR[ORA_MAXV], dU[ORA_MAXV], alpha[ORA_MAXV];
+    phys_flux(nd, d, gamma, UL, FL);
+    phys_flux(nd, d, gamma, UR, FR);
+    roe_eigen(nd, d, gamma, UL, UR, R, Lm, lam);
+    for (int v = 0; v < nv; ++v) dU[v] = UR[v] - UL[v];
+    for (int k = 0; k < nv; ++k) {
+        double s = 0.0;
+        for (int v = 0; v < nv; ++v) s += Lm[k * nv + v] * dU[v];
+        alpha[k] = fabs(lam[k]) * s;
+    }
+    for (int v = 0; v < nv; ++v) {
+        double s = 0.0;
+        for (int k = 0; k < nv; ++k) s += R[v * nv + k] * alpha[k];
+        F[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * s;
+    }
+}
+
+/* van Leer (1982) flux-vector splitting, one half.  sign = +1 gives F+,
+ * sign = -1 gives F-. */
+static void vanleer_half(int nd, int d, double gamma, const double* U, int sign, double* F)
+{
+    const int nv = nd + 2;
+    double rho = U[0], p = pressure(nd, gamma, U);
+    double c = sqrt(gamma * p / rho), un = U[1 + d] / rho, M = un / c;
+    if (M >= 1.0) {
+        if (sign > 0) phys_flux(nd, d, gamma, U, F); else for (int v = 0; v < nv; ++v) F[v] = 0.0;
+        return;
+    }
+    if (M <= -1.0) {
+        if (sign < 0) phys_flux(nd, d, gamma, U, F); else for (int v = 0; v < nv; ++v) F[v] = 0.0;
+        return;
+    }
+    double s = (double)sign;
+    double fm = s * 0.25 * rho * c * (M + s) * (M + s);        /* mass flux */
+    double t2 = 0.0;
+    for (int a = 0; a < nd; ++a) if (a != d) t2 += (U[1 + a] / rho) * (U[1 + a] / rho);
+    double wn = (gamma - 1.0) * un + s * 2.0 * c;
+    F[0] = fm;
+    for (int a = 0; a < nd; ++a) F[1 + a] = fm * (U[1 + a] / rho);
+    F[1 + d] = fm * wn / gamma;
+    F[nv - 1] = fm * (wn * wn / (2.0 * (gamma * gamma - 1.0)) + 0.5 * t2);
+}
+
+void ora_vanleer_half(int nd, int d, double gamma, const double* U, int sign, double* F)
+{
+    vanleer_half(nd, d, gamma, U, sign, F);
+}
+
+void ora_roe_flux(int nd, int d, double gamma, const double* UL, const double* UR, double* F)
+{
+    roe_flux(nd, d, gamma, UL, UR, F);
+}
+
+/* ------------------------------------------------------------------ */
+/* One direction of the semi-discrete operator on one grid line.       */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    long nonphys;        /* faces that fell back to first order */
+    double litdev;       /* max |chi_ratio - chi_literal|         */
+} ora_stats;
+
+/* line: pointer to the n_d nodes' variables, stride between nodes, stride
+ * between variables.  Writes -f' contributions into Lout (same strides),
+ * adding to what is there.  flags/margin: per face (n_d + 5 faces,
+ * j = f - 3) per characteristic field, may be NULL. */
+static void euler_line(const ora_cfg* cfg, int d, const double* line, long node_stride,
+                       long var_stride, double* Lout, uint8_t* flags, double* margin,
+                       long fl_field_stride, ora_stats* st)
+{
+    const int nd = cfg->ndim, nv = nd + 2, n = cfg->n[d];
+    const int np = n + 2 * ORA_GHOST, nf = n + 5;
+    double* P = (double*)malloc(sizeof(double) * np * nv);   /* padded nodes */
+    double* Fc = (double*)malloc(sizeof(double) * nf * nv);  /* face fluxes  */
+    /* A1: ghost nodes */
+    for (int m = -ORA_GHOST; m < n + ORA_GHOST; ++m) {
+        int src = m;
+        if (cfg->periodic[d]) src = ((m % n) + n) % n;
+        else if (m < 0) src = 0;
+        else if (m >= n) src = n - 1;
+        for (int v = 0; v < nv; ++v)
+            P[(m + ORA_GHOST) * nv + v] = line[src * node_stride + v * var_stride];
+    }
+    for (int f = 0; f < nf; ++f) {
+        int j = f - 3;                                          /* face j+1/2 */
+        const double* Uj = &P[(j + ORA_GHOST) * nv];
+        const double* Uj1 = &P[(j + 1 + ORA_GHOST) * nv];
+        double R[ORA_MAXV * ORA_MAXV], Lm[ORA_MAXV * ORA_MAXV], lam[ORA_MAXV];
+        double W[6][ORA_MAXV];                                  /* nodes j-2..j+3 */
+        if (cfg->characteristic) {
+            roe_eigen(nd, d, cfg->gamma, Uj, Uj1, R, Lm, lam);  /* A2 */
+            for (int m = 0; m < 6; ++m) {                       /* A3 */
+                const double* Um = &P[(j - 2 + m + ORA_GHOST) * nv];
+                for (int k = 0; k < nv; ++k) {
+                    double s = 0.0;
+                    for (int v = 0; v < nv; ++v) s += Lm[k * nv + v] * Um[v];
+                    W[m][k] = s;
+                }
+            }
+        } else {
+            for (int m = 0; m < 6; ++m)
+                for (int k = 0; k < nv; ++k) W[m][k] = P[(j - 2 + m + ORA_GHOST) * nv + k];
+        }
+        double wL[ORA_MAXV], wR[ORA_MAXV];
+        for (int k = 0; k < nv; ++k) {                          /* A4-A5 */
+            double sl[5], sr[5];
+            for (int m = 0; m < 5; ++m) { sl[m] = W[m][k]; sr[m] = W[5 - m][k]; }
+            int fL, fR; double mL, mR, dl, dr;
+            wL[k] = interp_left(cfg, sl, -1, &fL, &mL, &dl);
+            wR[k] = interp_left(cfg, sr, -1, &fR, &mR, &dr);
+            if (flags) flags[k * fl_field_stride + f] = (uint8_t)(fL | (fR << 3));
+            if (margin) margin[k * fl_field_stride + f] = mL < mR ? mL : mR;
+            if (dl > st->litdev) st->litdev = dl;
+            if (dr > st->litdev) st->litdev = dr;
+        }
+        double UL[ORA_MAXV], UR[ORA_MAXV];
+        if (cfg->characteristic) {
+            for (int v = 0; v < nv; ++v) {
+                double sl = 0.0, sr = 0.0;
+                for (int k = 0; k < nv; ++k) { sl += R[v * nv + k] * wL[k]; sr += R[v * nv + k] * wR[k]; }
+                UL[v] = sl; UR[v] = sr;
+            }
+        } else {
+            for (int v = 0; v < nv; ++v) { UL[v] = wL[v]; UR[v] = wR[v]; }
+        }
+        if (!(UL[0] > 0.0) || !(UR[0] > 0.0) || !(pressure(nd, cfg->gamma, UL) > 0.0) ||
+            !(pressure(nd, cfg->gamma, UR) > 0.0)) {
+            for (int v = 0; v < nv; ++v) { UL[v] = Uj[v]; UR[v] = Uj1[v]; }
+            st->nonphys++;
+        }
+        double* F = &Fc[f * nv];                                /* A6 */
+        if (cfg->flux == ORA_FLUX_ROE) {
+            roe_flux(nd, d, cfg->gamma, UL, UR, F);
+        } else {
+            double Fp[ORA_MAXV], Fm[ORA_MAXV];
+            vanleer_half(nd, d, cfg->gamma, UL, +1, Fp);
+            vanleer_half(nd, d, cfg->gamma, UR, -1, Fm);
+            for (int v = 0; v < nv; ++v) F[v] = Fp[v] + Fm[v];
+        }
+    }
+    /* A7: Eq. 3.  Node i: faces i+1/2 -> f = i+3, i-1/2 -> i+2, i+3/2 -> i+4,
+     * i-3/2 -> i+1, i+5/2 -> i+5, i-5/2 -> i. */
+    const double ih = 1.0 / cfg->h[d];
+    for (int i = 0; i < n; ++i) {
+        for (int v = 0; v < nv; ++v) {
+            double fp = MD_A1 * (Fc[(i + 3) * nv + v] - Fc[(i + 2) * nv + v])
+                      + MD_A2 * (Fc[(i + 4) * nv + v] - Fc[(i + 1) * nv + v])
+                      + MD_A3 * (Fc[(i + 5) * nv + v] - Fc[(i + 0) * nv + v]);
+            Lout[i * node_stride + v * var_stride] -= fp * ih;  /* Eq. 2 */
+        }
+    }
+    free(P);
+    free(Fc);
+}
+
+/* Number of lines in direction d and the mapping line -> base offset. */
+static long n_nodes(const ora_cfg* cfg)
+{
+    long N = 1;
+    for (int a = 0; a < cfg->ndim; ++a) N *= cfg->n[a];
+    return N;
+}
+
+static long lines_in(const ora_cfg* cfg, int d) { return n_nodes(cfg) / cfg->n[d]; }
+
+/* Element stride of axis a in the SoA array U[var][z][y][x]. */
+static long axis_stride(const ora_cfg* cfg, int a)
+{
+    long s = 1;
+    for (int b = 0; b < a; ++b) s *= cfg->n[b];
+    return s;
+}
+
+/* Base offset of line `ln` in direction d: the other axes in (z, y, x)
+ * order with x fastest among them. */
+static long line_base(const ora_cfg* cfg, int d, long ln)
+{
+    long base = 0;
+    for (int a = 0; a < cfg->ndim; ++a) {
+        if (a == d) continue;
+        long c = ln % cfg->n[a];
+        ln /= cfg->n[a];
+        base += c * axis_stride(cfg, a);
+    }
+    return base;
+}
+
+/* Offset of direction d's block in the flags / margin arrays. */
+long ora_flags_offset(const ora_cfg* cfg, int d)
+{
+    long off = 0;
+    int nv = cfg->ndim + 2;
+    for (int a = 0; a < d; ++a) off += (long)nv * lines_in(cfg, a) * (cfg->n[a] + 5);
+    return off;
+}
+
+long ora_flags_size(const ora_cfg* cfg) { return ora_flags_offset(cfg, cfg->ndim); }
+
+/* Semi-discrete RHS (Eq. 2) of the Euler equations: L = -sum_d dF_d/dx_d.
+ * U, L: SoA [var][z][y][x].  flags/margin: optional, ora_flags_size bytes /
+ * doubles, layout [d][field][line][face].  Returns number of fallback faces;
+ * writes the max ratio-vs-literal chi deviation into *litdev if given. */
+long ora_euler_rhs(const ora_cfg* cfg, const double* U, double* L, uint8_t* flags,
+                   double* margin, double* litdev)
+{
+    const int nv = cfg->ndim + 2;
+    const long N = n_nodes(cfg);
+    for (long i = 0; i < (long)nv * N; ++i) L[i] = 0.0;
+    long nonphys = 0;
+    double ld = 0.0;
+    for (int d = 0; d < cfg->ndim; ++d) {
+        const long nl = lines_in(cfg, d), nf = cfg->n[d] + 5;
+        const long stride = axis_stride(cfg, d);
+        const long foff = ora_flags_offset(cfg, d);
+        #pragma omp parallel for schedule(static) reduction(+ : nonphys) reduction(max : ld)
+        for (long ln = 0; ln < nl; ++ln) {
+            ora_stats st = {0, 0.0};
+            long base = line_base(cfg, d, ln);
+            euler_line(cfg, d, U + base, stride, N, L + base,
+                       flags ? flags + foff + ln * nf : NULL,
+                       margin ? margin + foff + ln * nf : NULL, nl * nf, &st);
+            nonphys += st.nonphys;
+            if (st.litdev > ld) ld = st.litdev;
+        }
+    }
+    if (litdev) *litdev = ld;
+    return nonphys;
+}
+
+/* A9: dt = CFL / max_i sum_d (|u_d| + c) / h_d. */
+double ora_cfl_dt(const ora_cfg* cfg, const double* U, double cfl)
+{
+    const int nd = cfg->ndim;
+    const long N = n_nodes(cfg);
+    double lmax = 0.0;
+    #pragma omp parallel for schedule(static) reduction(max : lmax)
+    for (long i = 0; i < N; ++i) {
+        double Ui[ORA_MAXV];
+        for (int v = 0; v < nd + 2; ++v) Ui[v] = U[v * N + i];
+        double c = sqrt(cfg->gamma * pressure(nd, cfg->gamma, Ui) / Ui[0]);
+        double s = 0.0;
+        for (int a = 0; a < nd; ++a) s += (fabs(Ui[1 + a] / Ui[0]) + c) / cfg->h[a];
+        if (s > lmax) lmax = s;
+    }
+    return cfl / lmax;
+}
+
+/* A10: one SSP-RK3 step (Shu-Osher form) of size dt, in place. */
+long ora_rk3_step(const ora_cfg* cfg, double* U, double dt)
+{
+    const long M = (long)(cfg->ndim + 2) * n_nodes(cfg);
+    double* U1 = (double*)malloc(sizeof(double) * M);
+    double* Lr = (double*)malloc(sizeof(double) * M);
+    long np = 0;
+    np += ora_euler_rhs(cfg, U, Lr, NULL, NULL, NULL);
+    for (long i = 0; i < M; ++i) U1[i] = U[i] + dt * Lr[i];
+    np += ora_euler_rhs(cfg, U1, Lr, NULL, NULL, NULL);
+    for (long i = 0; i < M; ++i) U1[i] = 0.75 * U[i] + 0.25 * (U1[i] + dt * Lr[i]);
+    np += ora_euler_rhs(cfg, U1, Lr, NULL, NULL, NULL);
+    for (long i = 0; i < M; ++i) U[i] = U[i] / 3.0 + 2.0 / 3.0 * (U1[i] + dt * Lr[i]);
+    free(U1);
+    free(Lr);
+    return np;
+}
+
+/* Advance to t_end (or max_steps) with the CFL rule; the last step is
+ * clipped to land on t_end.  Returns fallback faces; writes t and steps. */
+long ora_euler_run(const ora_cfg* cfg, double* U, double cfl, double t_end, int max_steps,
+                   double* t_out, int* steps_out)
+{
+    double t = 0.0;
+    int s = 0;
+    long np = 0;
+    while (t < t_end && s < max_steps) {
+        double dt = ora_cfl_dt(cfg, U, cfl);
+        if (t + dt > t_end) dt = t_end - t;
+        np += ora_rk3_step(cfg, U, dt);
+        t += dt;
+        ++s;
+    }
+    if (t_out) *t_out = t;
+    if (steps_out) *steps_out = s;
+    return np;
+}
+
+/* A11: sum_i U_i * prod_d h_d per variable. */
+void ora_conserved(const ora_cfg* cfg, const double* U, double* out)
+{
+    const long N = n_nodes(cfg);
+    double vol = 1.0;
+    for (int a = 0; a < cfg->ndim; ++a) vol *= cfg->h[a];
+    for (int v = 0; v < cfg->ndim + 2; ++v) {
+        double s = 0.0;
+        for (long i = 0; i < N; ++i) s += U[v * N + i];
+        out[v] = s * vol;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Scalar conservation laws on a periodic grid (Sec. 3.2-3.3).         */
+/* kind 0: linear advection f = u, a_hat = 1.                          */
+/* kind 1: inviscid Burgers f = u^2/2, a_hat = (u_L + u_R)/2.          */
+/* ------------------------------------------------------------------ */
+static double scalar_f(int kind, double u) { return kind == 0 ? u : 0.5 * u * u; }
+
+void ora_scalar_rhs(const ora_cfg* cfg, int kind, int n, double h, const double* u, double* L)
+{
+    const int nf = n + 5;
+    double* F = (double*)malloc(sizeof(double) * nf);
+    for (int f = 0; f < nf; ++f) {
+        int j = f - 3;
+        double sl[5], sr[5];
+        for (int m = 0; m < 5; ++m) {
+            int il = ((j - 2 + m) % n + n) % n;      /* u_{j-2..j+2}      */
+            int ir = ((j + 3 - m) % n + n) % n;      /* u_{j+3..j-1}      */
+            sl[m] = u[il];
+            sr[m] = u[ir];
+        }
+        double uL = interp_left(cfg, sl, -1, NULL, NULL, NULL);
+        double uR = interp_left(cfg, sr, -1, NULL, NULL, NULL);
+        double a = kind == 0 ? 1.0 : 0.5 * (uL + uR);
+        F[f] = 0.5 * ((scalar_f(kind, uR) + scalar_f(kind, uL)) - fabs(a) * (uR - uL)); /* Eq. 6 */
+    }
+    for (int i = 0; i < n; ++i) {
+        double fp = MD_A1 * (F[i + 3] - F[i + 2]) + MD_A2 * (F[i + 4] - F[i + 1])
+                  + MD_A3 * (F[i + 5] - F[i + 0]);
+        L[i] = -fp / h;
+    }
+    free(F);
+}
+
+/* SSP-RK3 with a fixed number of equal steps reaching t_end. */
+void ora_scalar_run(const ora_cfg* cfg, int kind, int n, double h, double t_end, int nsteps,
+                    double* u)
+{
+    double* u1 = (double*)malloc(sizeof(double) * n);
+    double* L = (double*)malloc(sizeof(double) * n);
+    double dt = t_end / nsteps;
+    for (int s = 0; s < nsteps; ++s) {
+        ora_scalar_rhs(cfg, kind, n, h, u, L);
+        for (int i = 0; i < n; ++i) u1[i] = u[i] + dt * L[i];
+        ora_scalar_rhs(cfg, kind, n, h, u1, L);
+        for (int i = 0; i < n; ++i) u1[i] = 0.75 * u[i] + 0.25 * (u1[i] + dt * L[i]);
+        ora_scalar_rhs(cfg, kind, n, h, u1, L);
+        for (int i = 0; i < n; ++i) u[i] = u[i] / 3.0 + 2.0 / 3.0 * (u1[i] + dt * L[i]);
+    }
+    free(u1);
+    free(L);
+}
+
+/* One RK3 step for the scalar operator (for the Taylor-polynomial pin). */
+void ora_scalar_rk3_step(const ora_cfg* cfg, int kind, int n, double h, double dt, double* u)
+{
+    ora_scalar_run(cfg, kind, n, h, dt, 1, u);
+}
