@@ -1,0 +1,145 @@
+/*
+ * wcns.h -- C ABI of the GB300 TCNS library (libwcns.so).
+ *
+ * The library evaluates the semi-discrete right-hand side of the
+ * fifth-order weighted compact nonlinear scheme with TENO-style stencil
+ * selection ("TCNS") of Zhang, Zhang & Xu (arXiv 1810.07806) for the
+ * compressible Euler equations of an ideal gas, dimension by dimension, and
+ * advances it with third-order SSP Runge-Kutta under a CFL rule.
+ *
+ * Conventions shared by every call:
+ *  - Every call returns a wcns_status and never aborts the process.  On
+ *    failure wcns_last_error() gives a message (thread-local).
+ *  - State arrays are caller-owned DEVICE pointers in structure-of-arrays
+ *    layout U[var][z][y][x] (x fastest, no padding), with the conserved
+ *    variables (rho, rho*u_1 .. rho*u_ndim, E), nv = ndim + 2.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Device work is stream-ordered; calls do not synchronise
+ *    unless they return a host value (stated per call).
+ *  - Asynchronous CUDA errors surface as WCNS_ERR_CUDA on a later call.
+ *  - Handles are not thread-safe; use one handle per host thread.
+ */
+#ifndef WCNS_H
+#define WCNS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    WCNS_OK = 0,
+    WCNS_ERR_INVALID = 1,     /* bad argument or unsupported combination        */
+    WCNS_ERR_NOMEM = 2,       /* device or host allocation failed / over budget */
+    WCNS_ERR_NONPHYSICAL = 3, /* rho <= 0 or p <= 0 met (first-order fallback)  */
+    WCNS_ERR_TIMEOUT = 4,     /* a bounded wait gave up                          */
+    WCNS_ERR_BUSY = 5,        /* no free slot / queue full                       */
+    WCNS_ERR_CUDA = 6         /* a CUDA runtime call failed                      */
+} wcns_status;
+
+enum { WCNS_BC_TRANSMISSIVE = 0, WCNS_BC_PERIODIC = 1 };
+enum { WCNS_FLUX_ROE = 0, WCNS_FLUX_VANLEER = 1 };
+enum { WCNS_DIFF_MD6 = 0 };
+enum { WCNS_W_TENO = 0 };
+enum { WCNS_FP64 = 0, WCNS_FP32 = 1 };
+
+/* Uniform grid.  Axis a has n[a] nodes on [lo[a], hi[a]].  A transmissive
+ * axis places nodes on both end points, h = (hi - lo)/(n - 1); a periodic
+ * axis has n unique nodes, h = (hi - lo)/n.  bc[a][0] / bc[a][1] are the
+ * low / high side; periodic must be set on both sides.  Axes >= ndim are
+ * ignored.  n[a] >= 2 (transmissive) or >= 1 (periodic). */
+typedef struct {
+    int ndim;
+    int n[3];
+    double lo[3], hi[3];
+    int bc[3][2];
+} wcns_grid;
+
+/* Scheme parameters (Sec. 2 of the paper).  wcns_default_params() fills the
+ * paper's values: TENO weights with C = 1, eps = 1e-40, q = 6 (Eq. 16) and
+ * C_T = 1e-5 (Sec. 2.3), characteristic interpolation (Sec. 3), sixth-order
+ * MD differencing (Eq. 3), Roe flux, FP64, CFL 0.5. */
+typedef struct {
+    int flux;            /* WCNS_FLUX_ROE | WCNS_FLUX_VANLEER                 */
+    int diff;            /* WCNS_DIFF_MD6                                     */
+    int weights;         /* WCNS_W_TENO                                       */
+    double C, eps, CT;   /* Eq. 16 and Eq. 18 constants                       */
+    int q;               /* Eq. 16 power, 1..16                               */
+    int characteristic;  /* must be 1: interpolate characteristic variables   */
+    int precision;       /* WCNS_FP64 | WCNS_FP32                             */
+    double cfl;          /* CFL number of the time-step rule                  */
+    int entropy_fix;     /* must be 0 (the paper uses none)                   */
+} wcns_scheme_params;
+
+typedef struct wcns_handle wcns_handle;
+
+void wcns_default_params(wcns_scheme_params* p);
+
+/* Thread-local message of the last failed call on this thread ("" if none). */
+const char* wcns_last_error(void);
+
+/* Library version string. */
+const char* wcns_version(void);
+
+/* Create a solver for one grid.  Allocates the handle's device scratch on
+ * the current CUDA device (two state-sized arrays plus small reduction
+ * buffers; FP32 mode adds three single-precision state-sized arrays).
+ * gamma > 1.  The handle owns its scratch; free it with wcns_destroy. */
+wcns_status wcns_create(const wcns_grid* grid, double gamma, const wcns_scheme_params* params,
+                        wcns_handle** out);
+wcns_status wcns_destroy(wcns_handle* h);
+
+/* Bytes of device scratch the handle holds (for admission budgets). */
+size_t wcns_handle_bytes(const wcns_handle* h);
+
+/* Semi-discrete RHS, Eq. 2: L = -sum_d dF_d/dx_d with each derivative from
+ * Eq. 3 over midpoint fluxes of the TCNS characteristic interpolation
+ * (Eq. 8-19) and the chosen flux.  U and L are device arrays in the handle's
+ * precision (double for WCNS_FP64, float for WCNS_FP32), nv * N elements.
+ * flags (nullable, device, wcns_flags_bytes bytes) receives per direction d,
+ * characteristic field k, grid line and face j + 1/2 (j = -3 .. n_d + 1)
+ * one byte: bits 0-2 = delta_1..3 of the left-biased value, bits 3-5 = the
+ * same for the right-biased value; layout [d][k][line][j + 3], where lines
+ * of direction d enumerate the other axes in (z, y, x) order, x fastest.
+ * Faces whose interpolated state had rho <= 0 or p <= 0 use first-order
+ * values and are counted (wcns_fallback_count).  Stream-ordered. */
+wcns_status wcns_rhs(wcns_handle* h, const void* U, void* L, uint8_t* flags, void* stream);
+
+/* Size in bytes of the flags array of wcns_rhs. */
+size_t wcns_flags_bytes(const wcns_handle* h);
+
+/* One SSP-RK3 step (Shu-Osher form) in place on the FP64 device state U
+ * (double, nv * N; in FP32 mode the right-hand sides run in single precision
+ * with compensated single-precision stage values and an FP64 final
+ * combination).  dt > 0 uses that step; dt <= 0 computes
+ * dt = cfl / max_i sum_d (|u_d| + c)/h_d in FP64 on the device.  If dt_used
+ * is non-NULL the call copies the step to the host and synchronises the
+ * stream; otherwise nothing is synchronised. */
+wcns_status wcns_step_rk3(wcns_handle* h, void* U, double dt, double* dt_used, void* stream);
+
+/* Advance U (FP64 device state) from t = 0 to t_end with CFL steps, the
+ * last one clipped to land on t_end, or until max_steps.  The time and step
+ * size stay on the device; the host loop checks completion every `check`
+ * steps (one small device-to-host read).  Writes the reached time and the
+ * number of steps.  Synchronises the stream before returning. */
+wcns_status wcns_advance(wcns_handle* h, void* U, double t_end, int max_steps, int check,
+                         double* t_out, int* steps_out, void* stream);
+
+/* FP64 conserved totals sum_i U_v,i * prod_d h_d for each variable (host
+ * array of nv doubles), from an FP64 device state.  Deterministic order.
+ * Synchronises the stream. */
+wcns_status wcns_conserved(wcns_handle* h, const void* U, double* out, void* stream);
+
+/* The CFL time step of an FP64 device state (host result; synchronises). */
+wcns_status wcns_cfl_dt(wcns_handle* h, const void* U, double* dt, void* stream);
+
+/* Number of first-order fallback faces since creation or the last reset
+ * (synchronises the stream). */
+wcns_status wcns_fallback_count(wcns_handle* h, long long* count, int reset, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WCNS_H */

@@ -48,6 +48,8 @@ def lib():
         L.ora_flags_size.argtypes = [C.POINTER(OraCfg)]
         L.ora_euler_rhs.restype = C.c_long
         L.ora_euler_rhs.argtypes = [C.POINTER(OraCfg), _dp, _dp, _u8p, _dp, _dp]
+        L.ora_euler_rhs_at.restype = C.c_long
+        L.ora_euler_rhs_at.argtypes = [C.POINTER(OraCfg), _dp, C.c_long, C.POINTER(C.c_long), _dp]
         L.ora_cfl_dt.restype = C.c_double
         L.ora_cfl_dt.argtypes = [C.POINTER(OraCfg), _dp, C.c_double]
         L.ora_rk3_step.restype = C.c_long
@@ -162,6 +164,15 @@ def euler_rhs(cfg, U, want_flags=False):
     ld = C.c_double()
     np_ = lib().ora_euler_rhs(C.byref(cfg), _p(U), _p(L), fp, mp, C.byref(ld))
     return L, fl, mg, np_, ld.value
+
+
+def euler_rhs_at(cfg, U, idx):
+    """RHS at the flattened node indices idx (x fastest): array [nv, len(idx)]."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    out = np.zeros((cfg.ndim + 2, idx.size))
+    lib().ora_euler_rhs_at(C.byref(cfg), _p(U), idx.size, idx.ctypes.data_as(C.POINTER(C.c_long)), _p(out))
+    return out
 
 
 def cfl_dt(cfg, U, cfl):

@@ -361,10 +361,83 @@ typedef struct {
     double litdev;       /* max |chi_ratio - chi_literal|         */
 } ora_stats;
 
-/* line: pointer to the n_d nodes' variables, stride between nodes, stride
- * between variables.  Writes -f' contributions into Lout (same strides),
- * adding to what is there.  flags/margin: per face (n_d + 5 faces,
- * j = f - 3) per characteristic field, may be NULL. */
+/* A2-A6 for one face j+1/2 of a padded line P (node m at P[(m + GHOST) * nv]).
+ * Writes the midpoint flux F[nv], the flags of each characteristic field
+ * (bits 0-2 left-biased, 3-5 right-biased) and the cutoff margin. */
+static void face_flux(const ora_cfg* cfg, int d, const double* P, int j, double* F,
+                      uint8_t* flags, double* margin, ora_stats* st)
+{
+    const int nd = cfg->ndim, nv = nd + 2;
+    const double* Uj = &P[(j + ORA_GHOST) * nv];
+    const double* Uj1 = &P[(j + 1 + ORA_GHOST) * nv];
+    double R[ORA_MAXV * ORA_MAXV], Lm[ORA_MAXV * ORA_MAXV], lam[ORA_MAXV];
+    double W[6][ORA_MAXV];                                      /* nodes j-2..j+3 */
+    if (cfg->characteristic) {
+        roe_eigen(nd, d, cfg->gamma, Uj, Uj1, R, Lm, lam);      /* A2 */
+        for (int m = 0; m < 6; ++m) {                           /* A3 */
+            const double* Um = &P[(j - 2 + m + ORA_GHOST) * nv];
+            for (int k = 0; k < nv; ++k) {
+                double s = 0.0;
+                for (int v = 0; v < nv; ++v) s += Lm[k * nv + v] * Um[v];
+                W[m][k] = s;
+            }
+        }
+    } else {
+        for (int m = 0; m < 6; ++m)
+            for (int k = 0; k < nv; ++k) W[m][k] = P[(j - 2 + m + ORA_GHOST) * nv + k];
+    }
+    double wL[ORA_MAXV], wR[ORA_MAXV];
+    for (int k = 0; k < nv; ++k) {                              /* A4-A5 */
+        double sl[5], sr[5];
+        for (int m = 0; m < 5; ++m) { sl[m] = W[m][k]; sr[m] = W[5 - m][k]; }
+        int fL, fR; double mL, mR, dl, dr;
+        wL[k] = interp_left(cfg, sl, -1, &fL, &mL, &dl);
+        wR[k] = interp_left(cfg, sr, -1, &fR, &mR, &dr);
+        if (flags) flags[k] = (uint8_t)(fL | (fR << 3));
+        if (margin) margin[k] = mL < mR ? mL : mR;
+        if (dl > st->litdev) st->litdev = dl;
+        if (dr > st->litdev) st->litdev = dr;
+    }
+    double UL[ORA_MAXV], UR[ORA_MAXV];
+    if (cfg->characteristic) {
+        for (int v = 0; v < nv; ++v) {
+            double sl = 0.0, sr = 0.0;
+            for (int k = 0; k < nv; ++k) { sl += R[v * nv + k] * wL[k]; sr += R[v * nv + k] * wR[k]; }
+            UL[v] = sl; UR[v] = sr;
+        }
+    } else {
+        for (int v = 0; v < nv; ++v) { UL[v] = wL[v]; UR[v] = wR[v]; }
+    }
+    if (!(UL[0] > 0.0) || !(UR[0] > 0.0) || !(pressure(nd, cfg->gamma, UL) > 0.0) ||
+        !(pressure(nd, cfg->gamma, UR) > 0.0)) {
+        for (int v = 0; v < nv; ++v) { UL[v] = Uj[v]; UR[v] = Uj1[v]; }
+        st->nonphys++;
+    }
+    if (cfg->flux == ORA_FLUX_ROE) {                            /* A6 */
+        roe_flux(nd, d, cfg->gamma, UL, UR, F);
+    } else {
+        double Fp[ORA_MAXV], Fm[ORA_MAXV];
+        vanleer_half(nd, d, cfg->gamma, UL, +1, Fp);
+        vanleer_half(nd, d, cfg->gamma, UR, -1, Fm);
+        for (int v = 0; v < nv; ++v) F[v] = Fp[v] + Fm[v];
+    }
+}
+
+/* A1: node m of a line (any integer m) under the boundary rule of d. */
+static int ghost_source(const ora_cfg* cfg, int d, int m)
+{
+    const int n = cfg->n[d];
+    if (cfg->periodic[d]) return ((m % n) + n) % n;
+    if (m < 0) return 0;
+    if (m >= n) return n - 1;
+    return m;
+}
+
+/* One direction of the semi-discrete operator on one grid line.
+ * line: pointer to the n_d nodes' variables, stride between nodes, stride
+ * between variables.  Adds the -f' contributions into Lout (same strides).
+ * flags/margin: per face (n_d + 5 faces, j = f - 3) per characteristic
+ * field, may be NULL. */
 static void euler_line(const ora_cfg* cfg, int d, const double* line, long node_stride,
                        long var_stride, double* Lout, uint8_t* flags, double* margin,
                        long fl_field_stride, ora_stats* st)
@@ -373,70 +446,18 @@ static void euler_line(const ora_cfg* cfg, int d, const double* line, long node_
     const int np = n + 2 * ORA_GHOST, nf = n + 5;
     double* P = (double*)malloc(sizeof(double) * np * nv);   /* padded nodes */
     double* Fc = (double*)malloc(sizeof(double) * nf * nv);  /* face fluxes  */
-    /* A1: ghost nodes */
-    for (int m = -ORA_GHOST; m < n + ORA_GHOST; ++m) {
-        int src = m;
-        if (cfg->periodic[d]) src = ((m % n) + n) % n;
-        else if (m < 0) src = 0;
-        else if (m >= n) src = n - 1;
+    for (int m = -ORA_GHOST; m < n + ORA_GHOST; ++m) {       /* A1 */
+        int src = ghost_source(cfg, d, m);
         for (int v = 0; v < nv; ++v)
             P[(m + ORA_GHOST) * nv + v] = line[src * node_stride + v * var_stride];
     }
     for (int f = 0; f < nf; ++f) {
-        int j = f - 3;                                          /* face j+1/2 */
-        const double* Uj = &P[(j + ORA_GHOST) * nv];
-        const double* Uj1 = &P[(j + 1 + ORA_GHOST) * nv];
-        double R[ORA_MAXV * ORA_MAXV], Lm[ORA_MAXV * ORA_MAXV], lam[ORA_MAXV];
-        double W[6][ORA_MAXV];                                  /* nodes j-2..j+3 */
-        if (cfg->characteristic) {
-            roe_eigen(nd, d, cfg->gamma, Uj, Uj1, R, Lm, lam);  /* A2 */
-            for (int m = 0; m < 6; ++m) {                       /* A3 */
-                const double* Um = &P[(j - 2 + m + ORA_GHOST) * nv];
-                for (int k = 0; k < nv; ++k) {
-                    double s = 0.0;
-                    for (int v = 0; v < nv; ++v) s += Lm[k * nv + v] * Um[v];
-                    W[m][k] = s;
-                }
-            }
-        } else {
-            for (int m = 0; m < 6; ++m)
-                for (int k = 0; k < nv; ++k) W[m][k] = P[(j - 2 + m + ORA_GHOST) * nv + k];
-        }
-        double wL[ORA_MAXV], wR[ORA_MAXV];
-        for (int k = 0; k < nv; ++k) {                          /* A4-A5 */
-            double sl[5], sr[5];
-            for (int m = 0; m < 5; ++m) { sl[m] = W[m][k]; sr[m] = W[5 - m][k]; }
-            int fL, fR; double mL, mR, dl, dr;
-            wL[k] = interp_left(cfg, sl, -1, &fL, &mL, &dl);
-            wR[k] = interp_left(cfg, sr, -1, &fR, &mR, &dr);
-            if (flags) flags[k * fl_field_stride + f] = (uint8_t)(fL | (fR << 3));
-            if (margin) margin[k * fl_field_stride + f] = mL < mR ? mL : mR;
-            if (dl > st->litdev) st->litdev = dl;
-            if (dr > st->litdev) st->litdev = dr;
-        }
-        double UL[ORA_MAXV], UR[ORA_MAXV];
-        if (cfg->characteristic) {
-            for (int v = 0; v < nv; ++v) {
-                double sl = 0.0, sr = 0.0;
-                for (int k = 0; k < nv; ++k) { sl += R[v * nv + k] * wL[k]; sr += R[v * nv + k] * wR[k]; }
-                UL[v] = sl; UR[v] = sr;
-            }
-        } else {
-            for (int v = 0; v < nv; ++v) { UL[v] = wL[v]; UR[v] = wR[v]; }
-        }
-        if (!(UL[0] > 0.0) || !(UR[0] > 0.0) || !(pressure(nd, cfg->gamma, UL) > 0.0) ||
-            !(pressure(nd, cfg->gamma, UR) > 0.0)) {
-            for (int v = 0; v < nv; ++v) { UL[v] = Uj[v]; UR[v] = Uj1[v]; }
-            st->nonphys++;
-        }
-        double* F = &Fc[f * nv];                                /* A6 */
-        if (cfg->flux == ORA_FLUX_ROE) {
-            roe_flux(nd, d, cfg->gamma, UL, UR, F);
-        } else {
-            double Fp[ORA_MAXV], Fm[ORA_MAXV];
-            vanleer_half(nd, d, cfg->gamma, UL, +1, Fp);
-            vanleer_half(nd, d, cfg->gamma, UR, -1, Fm);
-            for (int v = 0; v < nv; ++v) F[v] = Fp[v] + Fm[v];
+        uint8_t fl[ORA_MAXV];
+        double mg[ORA_MAXV];
+        face_flux(cfg, d, P, f - 3, &Fc[f * nv], fl, mg, st);  /* face j+1/2, j = f-3 */
+        for (int k = 0; k < nv; ++k) {
+            if (flags) flags[k * fl_field_stride + f] = fl[k];
+            if (margin) margin[k * fl_field_stride + f] = mg[k];
         }
     }
     /* A7: Eq. 3.  Node i: faces i+1/2 -> f = i+3, i-1/2 -> i+2, i+3/2 -> i+4,
@@ -525,6 +546,47 @@ long ora_euler_rhs(const ora_cfg* cfg, const double* U, double* L, uint8_t* flag
         }
     }
     if (litdev) *litdev = ld;
+    return nonphys;
+}
+
+/* The RHS at selected nodes only (same arithmetic as ora_euler_rhs): for
+ * each node index idx[p] (flattened x-fastest), L_out[v * npts + p]. */
+long ora_euler_rhs_at(const ora_cfg* cfg, const double* U, long npts, const long* idx,
+                      double* Lout)
+{
+    const int nd = cfg->ndim, nv = nd + 2;
+    const long N = n_nodes(cfg);
+    long nonphys = 0;
+    #pragma omp parallel for schedule(dynamic, 16) reduction(+ : nonphys)
+    for (long p = 0; p < npts; ++p) {
+        ora_stats st = {0, 0.0};
+        long coord[3] = {0, 0, 0}, rest = idx[p];
+        for (int a = 0; a < nd; ++a) { coord[a] = rest % cfg->n[a]; rest /= cfg->n[a]; }
+        double acc[ORA_MAXV];
+        for (int v = 0; v < nv; ++v) acc[v] = 0.0;
+        for (int d = 0; d < nd; ++d) {
+            double P[(2 * ORA_GHOST + 1) * ORA_MAXV];   /* nodes i-5 .. i+5 */
+            for (int m = -ORA_GHOST; m <= ORA_GHOST; ++m) {
+                long c[3] = {coord[0], coord[1], coord[2]};
+                c[d] = ghost_source(cfg, d, (int)coord[d] + m);
+                long off = 0;
+                for (int a = nd - 1; a >= 0; --a) off = off * cfg->n[a] + c[a];
+                for (int v = 0; v < nv; ++v) P[(m + ORA_GHOST) * nv + v] = U[v * N + off];
+            }
+            /* faces i-5/2 .. i+5/2 are j = i-3 .. i+2; with the padded origin at
+             * node i, j runs -3 .. 2 and the face array index is j + 3 */
+            double Fc[6][ORA_MAXV];
+            for (int f = 0; f < 6; ++f) face_flux(cfg, d, P, f - 3, Fc[f], NULL, NULL, &st);
+            const double ih = 1.0 / cfg->h[d];
+            for (int v = 0; v < nv; ++v) {
+                double fp = MD_A1 * (Fc[3][v] - Fc[2][v]) + MD_A2 * (Fc[4][v] - Fc[1][v])
+                          + MD_A3 * (Fc[5][v] - Fc[0][v]);
+                acc[v] -= fp * ih;
+            }
+        }
+        for (int v = 0; v < nv; ++v) Lout[v * npts + p] = acc[v];
+        nonphys += st.nonphys;
+    }
     return nonphys;
 }
 

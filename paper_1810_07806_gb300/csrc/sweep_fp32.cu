@@ -1,0 +1,66 @@
+// sweep_fp32.cu -- FP32 instances of the fused sweep (rescaled smoothness
+// indicators).  The input state is either the FP64 base state (first RK
+// stage, rounded on load) or the FP32 stage state.
+#include "wcns_internal.h"
+
+namespace wcns {
+
+template <typename LT, int ND, int DIR, int FLUX>
+static cudaError_t go(const SweepArgs& a, cudaStream_t s, bool prepare)
+{
+    using G = TileGeom<float, ND, DIR>;
+    auto k = sweep_kernel<float, LT, ND, DIR, FLUX>;
+    const size_t smem = G::smem_bytes();
+    if (prepare) return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid;
+    const int nd = a.n[DIR];
+    if (DIR == 0) {
+        const long long rows = a.N / a.n[0];
+        grid = dim3((unsigned)((rows + G::TL - 1) / G::TL), (nd + G::TS - 1) / G::TS, 1);
+    } else {
+        grid = dim3((a.n[0] + G::TL - 1) / G::TL, (nd + G::TS - 1) / G::TS,
+                    DIR == 1 ? (ND == 3 ? a.n[2] : 1) : a.n[1]);
+    }
+    k<<<grid, G::THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename LT, int FLUX>
+static cudaError_t dispatch(int nd, int dir, const SweepArgs& a, cudaStream_t s, bool prep)
+{
+    if (nd == 1) return go<LT, 1, 0, FLUX>(a, s, prep);
+    if (nd == 2) return dir == 0 ? go<LT, 2, 0, FLUX>(a, s, prep) : go<LT, 2, 1, FLUX>(a, s, prep);
+    if (dir == 0) return go<LT, 3, 0, FLUX>(a, s, prep);
+    if (dir == 1) return go<LT, 3, 1, FLUX>(a, s, prep);
+    return go<LT, 3, 2, FLUX>(a, s, prep);
+}
+
+cudaError_t launch_sweep_fp32(int nd, int dir, int flux, bool load_fp64, const SweepArgs& a,
+                              cudaStream_t s)
+{
+    if (load_fp64)
+        return flux == FLUX_ROE ? dispatch<double, FLUX_ROE>(nd, dir, a, s, false)
+                                : dispatch<double, FLUX_VANLEER>(nd, dir, a, s, false);
+    return flux == FLUX_ROE ? dispatch<float, FLUX_ROE>(nd, dir, a, s, false)
+                            : dispatch<float, FLUX_VANLEER>(nd, dir, a, s, false);
+}
+
+cudaError_t prepare_sweeps_fp32()
+{
+    SweepArgs a{};
+    for (int nd = 1; nd <= 3; ++nd)
+        for (int d = 0; d < nd; ++d)
+            for (int f = 0; f < 4; ++f) {
+                cudaError_t e;
+                switch (f) {
+                    case 0: e = dispatch<double, FLUX_ROE>(nd, d, a, 0, true); break;
+                    case 1: e = dispatch<double, FLUX_VANLEER>(nd, d, a, 0, true); break;
+                    case 2: e = dispatch<float, FLUX_ROE>(nd, d, a, 0, true); break;
+                    default: e = dispatch<float, FLUX_VANLEER>(nd, d, a, 0, true); break;
+                }
+                if (e != cudaSuccess) return e;
+            }
+    return cudaSuccess;
+}
+
+}  // namespace wcns

@@ -1,0 +1,373 @@
+// wcns_api.cu -- the C ABI of libwcns (declared in include/wcns.h).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+
+#include "../../include/wcns.h"
+#include "wcns_internal.h"
+
+using namespace wcns;
+
+struct wcns_handle {
+    int ndim = 0, nv = 0;
+    int n[3] = {1, 1, 1};
+    long long N = 0;
+    double h[3] = {1, 1, 1}, inv_h[3] = {0, 0, 0};
+    int periodic[3] = {0, 0, 0};
+    double gamma = 1.4;
+    wcns_scheme_params p{};
+    SchemeConst K{};
+    float sqrt_eps_f = 0.f;
+    int device = 0;
+    // device scratch
+    void* L = nullptr;          // RHS, handle precision
+    void* U1 = nullptr;         // FP64: stage state; FP32: stage sweep input (float)
+    float* D = nullptr;         // FP32: stage increment
+    StepScalars* sc = nullptr;
+    long long* fallback = nullptr;
+    double* partials = nullptr;
+    int nblk_cons = 0;
+    size_t bytes = 0;
+};
+
+static thread_local std::string g_err;
+
+static wcns_status fail(wcns_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+static wcns_status cuda_fail(cudaError_t e, const char* where)
+{
+    return fail(WCNS_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(call, where)                                         \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where);     \
+    } while (0)
+
+extern "C" {
+
+const char* wcns_last_error(void) { return g_err.c_str(); }
+
+const char* wcns_version(void) { return "wcns-gb300 0.1 (sm_103a)"; }
+
+void wcns_default_params(wcns_scheme_params* p)
+{
+    if (!p) return;
+    p->flux = WCNS_FLUX_ROE;
+    p->diff = WCNS_DIFF_MD6;
+    p->weights = WCNS_W_TENO;
+    p->C = 1.0;
+    p->eps = 1e-40;
+    p->CT = 1e-5;
+    p->q = 6;
+    p->characteristic = 1;
+    p->precision = WCNS_FP64;
+    p->cfl = 0.5;
+    p->entropy_fix = 0;
+}
+
+static bool prepared_fp64[64], prepared_fp32[64];
+
+wcns_status wcns_create(const wcns_grid* g, double gamma, const wcns_scheme_params* prm,
+                        wcns_handle** out)
+{
+    g_err.clear();
+    if (!g || !prm || !out) return fail(WCNS_ERR_INVALID, "wcns_create: null argument");
+    *out = nullptr;
+    if (g->ndim < 1 || g->ndim > 3) return fail(WCNS_ERR_INVALID, "ndim must be 1, 2 or 3");
+    if (!(gamma > 1.0)) return fail(WCNS_ERR_INVALID, "gamma must exceed 1");
+    if (prm->flux != WCNS_FLUX_ROE && prm->flux != WCNS_FLUX_VANLEER)
+        return fail(WCNS_ERR_INVALID, "unsupported flux %d", prm->flux);
+    if (prm->diff != WCNS_DIFF_MD6) return fail(WCNS_ERR_INVALID, "unsupported difference scheme");
+    if (prm->weights != WCNS_W_TENO) return fail(WCNS_ERR_INVALID, "unsupported weights");
+    if (prm->characteristic != 1) return fail(WCNS_ERR_INVALID, "characteristic must be 1");
+    if (prm->entropy_fix != 0) return fail(WCNS_ERR_INVALID, "entropy_fix must be 0");
+    if (!(prm->C > 0.0) || !(prm->eps > 0.0) || !(prm->CT > 0.0) || !(prm->CT < 1.0 / 3.0))
+        return fail(WCNS_ERR_INVALID, "need C > 0, eps > 0, 0 < C_T < 1/3");
+    if (prm->q < 1 || prm->q > 16) return fail(WCNS_ERR_INVALID, "q must be in 1..16");
+    if (prm->precision != WCNS_FP64 && prm->precision != WCNS_FP32)
+        return fail(WCNS_ERR_INVALID, "precision must be WCNS_FP64 or WCNS_FP32");
+    if (!(prm->cfl > 0.0)) return fail(WCNS_ERR_INVALID, "cfl must be positive");
+
+    wcns_handle* h = new wcns_handle();
+    h->ndim = g->ndim;
+    h->nv = g->ndim + 2;
+    h->N = 1;
+    for (int a = 0; a < g->ndim; ++a) {
+        const int per = g->bc[a][0] == WCNS_BC_PERIODIC;
+        if ((g->bc[a][1] == WCNS_BC_PERIODIC) != per) {
+            delete h;
+            return fail(WCNS_ERR_INVALID, "axis %d: periodic must be set on both sides", a);
+        }
+        for (int sd = 0; sd < 2; ++sd)
+            if (g->bc[a][sd] != WCNS_BC_PERIODIC && g->bc[a][sd] != WCNS_BC_TRANSMISSIVE) {
+                delete h;
+                return fail(WCNS_ERR_INVALID, "axis %d: unknown boundary kind", a);
+            }
+        if (g->n[a] < (per ? 1 : 2) || !(g->hi[a] > g->lo[a])) {
+            delete h;
+            return fail(WCNS_ERR_INVALID, "axis %d: bad node count or extent", a);
+        }
+        h->n[a] = g->n[a];
+        h->periodic[a] = per;
+        h->h[a] = (g->hi[a] - g->lo[a]) / (per ? g->n[a] : g->n[a] - 1);
+        h->inv_h[a] = 1.0 / h->h[a];
+        h->N *= g->n[a];
+    }
+    // launch limits: the outer axis of the y and z sweeps is a grid z-dimension
+    if ((h->ndim == 3 && (h->n[1] > 65535 || h->n[2] > 65535)) || h->N > (1LL << 40)) {
+        delete h;
+        return fail(WCNS_ERR_INVALID, "grid too large");
+    }
+    h->gamma = gamma;
+    h->p = *prm;
+    h->K.gamma = gamma;
+    h->K.gm1 = gamma - 1.0;
+    h->K.C = prm->C;
+    h->K.eps = prm->eps;
+    h->K.CT = prm->CT;
+    h->K.q = prm->q;
+    // A stencil can only be cut if max g / min g exceeds (3 C_T)^(-1/q); since
+    // max g / min g <= 1 + tau / (C (min beta + eps)), tau below
+    // 0.98 (ratio - 1) C (min beta + eps) keeps all three.
+    const double ratio = pow(3.0 * prm->CT, -1.0 / prm->q);
+    h->K.keep_all_K = 0.98 * (ratio - 1.0) * prm->C;
+    h->K.Cf = (float)prm->C;
+    h->K.CTf = (float)prm->CT;
+    h->K.Kf = (float)h->K.keep_all_K;
+    h->sqrt_eps_f = (float)sqrt(prm->eps);
+
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaGetDevice"); }
+    const bool fp32 = prm->precision == WCNS_FP32;
+    const int slot = h->device & 63;
+    if (!fp32 && !prepared_fp64[slot]) {
+        e = prepare_sweeps_fp64();
+        if (e != cudaSuccess) { delete h; return cuda_fail(e, "prepare fp64 sweeps"); }
+        prepared_fp64[slot] = true;
+    }
+    if (fp32 && !prepared_fp32[slot]) {
+        e = prepare_sweeps_fp32();
+        if (e != cudaSuccess) { delete h; return cuda_fail(e, "prepare fp32 sweeps"); }
+        prepared_fp32[slot] = true;
+    }
+    const size_t M = (size_t)h->nv * h->N;
+    const size_t w = fp32 ? 4 : 8;
+    h->nblk_cons = conserved_blocks(h->N);
+    size_t bytes = M * w * 2 + (fp32 ? M * 4 : 0) + sizeof(StepScalars) + 64 +
+                   sizeof(double) * (h->nblk_cons + 1) * h->nv;
+    char* base = nullptr;
+    e = cudaMalloc((void**)&base, bytes + 2048);
+    if (e != cudaSuccess) {
+        delete h;
+        cudaGetLastError();
+        return fail(WCNS_ERR_NOMEM, "cudaMalloc of %zu bytes failed", bytes);
+    }
+    size_t off = 0;
+    auto carve = [&](size_t sz) { void* p = base + off; off = (off + sz + 255) & ~(size_t)255; return p; };
+    h->L = carve(M * w);
+    h->U1 = carve(M * w);
+    if (fp32) h->D = (float*)carve(M * 4);
+    h->sc = (StepScalars*)carve(sizeof(StepScalars));
+    h->fallback = (long long*)carve(64);
+    h->partials = (double*)carve(sizeof(double) * (h->nblk_cons + 1) * h->nv);
+    h->bytes = bytes + 2048;
+    e = cudaMemset(h->sc, 0, sizeof(StepScalars));
+    if (e == cudaSuccess) e = cudaMemset(h->fallback, 0, 64);
+    if (e != cudaSuccess) { cudaFree(base); delete h; return cuda_fail(e, "cudaMemset"); }
+    *out = h;
+    return WCNS_OK;
+}
+
+wcns_status wcns_destroy(wcns_handle* h)
+{
+    if (!h) return WCNS_OK;
+    cudaError_t e = cudaFree(h->L);
+    delete h;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFree");
+    return WCNS_OK;
+}
+
+size_t wcns_handle_bytes(const wcns_handle* h) { return h ? h->bytes : 0; }
+
+size_t wcns_flags_bytes(const wcns_handle* h)
+{
+    if (!h) return 0;
+    size_t s = 0;
+    for (int d = 0; d < h->ndim; ++d) s += (size_t)h->nv * (h->N / h->n[d]) * (h->n[d] + 5);
+    return s;
+}
+
+static size_t flags_offset(const wcns_handle* h, int d)
+{
+    size_t s = 0;
+    for (int a = 0; a < d; ++a) s += (size_t)h->nv * (h->N / h->n[a]) * (h->n[a] + 5);
+    return s;
+}
+
+// Evaluate L = RHS(U) with all directions; U is LT, L is the handle precision.
+static cudaError_t run_rhs(wcns_handle* h, const void* U, bool u_fp64, void* L, uint8_t* flags,
+                           const double* dtp, cudaStream_t s)
+{
+    const bool fp32 = h->p.precision == WCNS_FP32;
+    for (int d = 0; d < h->ndim; ++d) {
+        SweepArgs a{};
+        a.U = U;
+        a.L = L;
+        a.N = h->N;
+        a.n[0] = h->n[0];
+        a.n[1] = h->n[1];
+        a.n[2] = h->n[2];
+        a.periodic = h->periodic[d];
+        a.inv_h = h->inv_h[d];
+        a.accumulate = d > 0;
+        a.flags = flags ? flags + flags_offset(h, d) : nullptr;
+        a.fallback = h->fallback;
+        a.dt = dtp;
+        a.K = h->K;
+        a.sqrt_eps_f = h->sqrt_eps_f;
+        cudaError_t e = fp32 ? launch_sweep_fp32(h->ndim, d, h->p.flux, u_fp64, a, s)
+                             : launch_sweep_fp64(h->ndim, d, h->p.flux, a, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+wcns_status wcns_rhs(wcns_handle* h, const void* U, void* L, uint8_t* flags, void* stream)
+{
+    g_err.clear();
+    if (!h || !U || !L) return fail(WCNS_ERR_INVALID, "wcns_rhs: null argument");
+    CK(cudaGetLastError(), "pending CUDA error");
+    CK(run_rhs(h, U, h->p.precision == WCNS_FP64, L, flags, nullptr, (cudaStream_t)stream),
+       "wcns_rhs launch");
+    return WCNS_OK;
+}
+
+// The three stages of one step after dt has been placed in h->sc.
+static cudaError_t run_stages(wcns_handle* h, double* U, cudaStream_t s)
+{
+    const long long M = (long long)h->nv * h->N;
+    const double* dtp = &h->sc->dt;
+    cudaError_t e;
+    if (h->p.precision == WCNS_FP64) {
+        double* U1 = (double*)h->U1;
+        double* L = (double*)h->L;
+        if ((e = run_rhs(h, U, true, L, nullptr, dtp, s)) != cudaSuccess) return e;
+        if ((e = launch_rk_fp64(1, U, U1, L, M, h->sc, s)) != cudaSuccess) return e;
+        if ((e = run_rhs(h, U1, true, L, nullptr, dtp, s)) != cudaSuccess) return e;
+        if ((e = launch_rk_fp64(2, U, U1, L, M, h->sc, s)) != cudaSuccess) return e;
+        if ((e = run_rhs(h, U1, true, L, nullptr, dtp, s)) != cudaSuccess) return e;
+        return launch_rk_fp64(3, U, U1, L, M, h->sc, s);
+    }
+    float* S = (float*)h->U1;
+    float* L = (float*)h->L;
+    if ((e = run_rhs(h, U, true, L, nullptr, dtp, s)) != cudaSuccess) return e;
+    if ((e = launch_rk_fp32(1, U, S, h->D, L, M, h->sc, s)) != cudaSuccess) return e;
+    if ((e = run_rhs(h, S, false, L, nullptr, dtp, s)) != cudaSuccess) return e;
+    if ((e = launch_rk_fp32(2, U, S, h->D, L, M, h->sc, s)) != cudaSuccess) return e;
+    if ((e = run_rhs(h, S, false, L, nullptr, dtp, s)) != cudaSuccess) return e;
+    return launch_rk_fp32(3, U, S, h->D, L, M, h->sc, s);
+}
+
+static cudaError_t reset_clock(wcns_handle* h, double t_end, cudaStream_t s)
+{
+    return launch_reset_clock(t_end, h->sc, s);
+}
+
+wcns_status wcns_step_rk3(wcns_handle* h, void* U, double dt, double* dt_used, void* stream)
+{
+    g_err.clear();
+    if (!h || !U) return fail(WCNS_ERR_INVALID, "wcns_step_rk3: null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaGetLastError(), "pending CUDA error");
+    CK(reset_clock(h, INFINITY, s), "reset clock");
+    if (dt > 0.0) CK(launch_set_dt(dt, 0, h->sc, s), "set dt");
+    else CK(launch_cfl(h->ndim, (const double*)U, h->N, h->inv_h, h->gamma, h->p.cfl, 0, h->sc, s), "cfl");
+    CK(run_stages(h, (double*)U, s), "rk3 stages");
+    if (dt_used) {
+        CK(cudaMemcpyAsync(dt_used, &h->sc->dt, sizeof(double), cudaMemcpyDeviceToHost, s), "dt copy");
+        CK(cudaStreamSynchronize(s), "sync");
+    }
+    return WCNS_OK;
+}
+
+wcns_status wcns_advance(wcns_handle* h, void* U, double t_end, int max_steps, int check,
+                         double* t_out, int* steps_out, void* stream)
+{
+    g_err.clear();
+    if (!h || !U || !(t_end >= 0.0) || max_steps < 0)
+        return fail(WCNS_ERR_INVALID, "wcns_advance: bad argument");
+    if (check < 1) check = 1;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaGetLastError(), "pending CUDA error");
+    CK(reset_clock(h, t_end, s), "reset clock");
+    long long issued = 0;
+    StepScalars cur{};
+    while (issued < max_steps) {
+        const long long left = max_steps - issued;
+        const int batch = left < check ? (int)left : check;
+        for (int k = 0; k < batch; ++k) {
+            CK(launch_cfl(h->ndim, (const double*)U, h->N, h->inv_h, h->gamma, h->p.cfl, 1, h->sc, s), "cfl");
+            CK(run_stages(h, (double*)U, s), "rk3 stages");
+        }
+        issued += batch;
+        CK(cudaMemcpyAsync(&cur, h->sc, sizeof cur, cudaMemcpyDeviceToHost, s), "clock copy");
+        CK(cudaStreamSynchronize(s), "sync");
+        if (cur.t >= t_end) break;
+    }
+    if (t_out) *t_out = cur.t;
+    if (steps_out) *steps_out = (int)cur.steps;
+    return WCNS_OK;
+}
+
+wcns_status wcns_conserved(wcns_handle* h, const void* U, double* out, void* stream)
+{
+    g_err.clear();
+    if (!h || !U || !out) return fail(WCNS_ERR_INVALID, "wcns_conserved: null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    double vol = 1.0;
+    for (int a = 0; a < h->ndim; ++a) vol *= h->h[a];
+    CK(launch_conserved(h->nv, (const double*)U, h->N, vol, h->partials, h->nblk_cons, s), "conserved");
+    CK(cudaMemcpyAsync(out, h->partials + (size_t)h->nv * h->nblk_cons, sizeof(double) * h->nv,
+                       cudaMemcpyDeviceToHost, s), "conserved copy");
+    CK(cudaStreamSynchronize(s), "sync");
+    return WCNS_OK;
+}
+
+wcns_status wcns_cfl_dt(wcns_handle* h, const void* U, double* dt, void* stream)
+{
+    g_err.clear();
+    if (!h || !U || !dt) return fail(WCNS_ERR_INVALID, "wcns_cfl_dt: null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(reset_clock(h, INFINITY, s), "reset clock");
+    CK(launch_cfl(h->ndim, (const double*)U, h->N, h->inv_h, h->gamma, h->p.cfl, 0, h->sc, s), "cfl");
+    CK(cudaMemcpyAsync(dt, &h->sc->dt, sizeof(double), cudaMemcpyDeviceToHost, s), "dt copy");
+    CK(cudaStreamSynchronize(s), "sync");
+    return WCNS_OK;
+}
+
+wcns_status wcns_fallback_count(wcns_handle* h, long long* count, int reset, void* stream)
+{
+    g_err.clear();
+    if (!h || !count) return fail(WCNS_ERR_INVALID, "wcns_fallback_count: null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(count, h->fallback, sizeof(long long), cudaMemcpyDeviceToHost, s), "copy");
+    if (reset) CK(cudaMemsetAsync(h->fallback, 0, sizeof(long long), s), "reset");
+    CK(cudaStreamSynchronize(s), "sync");
+    return WCNS_OK;
+}
+
+}  // extern "C"

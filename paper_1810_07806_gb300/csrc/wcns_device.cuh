@@ -1,0 +1,354 @@
+// wcns_device.cuh -- device building blocks of the TCNS sweep (sm_103a).
+//
+// Per face j+1/2 of one grid line the sweep computes (arXiv 1810.07806):
+//   Roe-averaged eigen-system of the two bounding nodes (Sec. 3: the
+//   interpolation runs on characteristic variables),
+//   characteristic variables of the six stencil nodes j-2 .. j+3,
+//   per field: smoothness indicators beta_k (Eq. 10, 11, 15), the TENO
+//   scale separation gamma_k (Eq. 16), normalisation chi_k (Eq. 17) and
+//   cutoff delta_k (Eq. 18) for the left-biased stencil and its mirror,
+//   the interpolated value from the equivalent five-point stencil of the
+//   retained set (Table 1; Eq. 12 with the weights of Eq. 19),
+//   back-projection, and the Roe or van Leer midpoint flux.
+// The node update is the sixth-order MD difference of Eq. 3.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace wcns {
+
+constexpr int GHOST = 5;   // node i reads nodes i-5 .. i+5
+
+// Eq. 3 coefficients from sixth-order Taylor matching:
+// sum a_m (2m-1) = 1, sum a_m (2m-1)^3 = 0, sum a_m (2m-1)^5 = 0.
+constexpr double MD_A1 = 75.0 / 64.0;
+constexpr double MD_A2 = -25.0 / 384.0;
+constexpr double MD_A3 = 3.0 / 640.0;
+
+// Table 1: coefficients (a_{i-2} .. a_{i+2}) of the single five-point
+// stencil equivalent to each retained set, indexed by the flag word
+// delta_1 | delta_2 << 1 | delta_3 << 2.  Index 0 (nothing retained) cannot
+// occur because the largest chi_k is at least 1/3; it maps to S_0*.
+#define WCNS_TABLE1_ROWS                                                   \
+    {{3.0 / 128, -5.0 / 32, 45.0 / 64, 15.0 / 32, -5.0 / 128},  /* -    */ \
+     {3.0 / 8, -5.0 / 4, 15.0 / 8, 0.0, 0.0},                   /* 100  */ \
+     {0.0, -1.0 / 8, 3.0 / 4, 3.0 / 8, 0.0},                    /* 010  */ \
+     {3.0 / 88, -5.0 / 22, 75.0 / 88, 15.0 / 44, 0.0},          /* 110  */ \
+     {0.0, 0.0, 3.0 / 8, 3.0 / 4, -1.0 / 8},                    /* 001  */ \
+     {1.0 / 16, -5.0 / 24, 5.0 / 8, 5.0 / 8, -5.0 / 48},        /* 101  */ \
+     {0.0, -1.0 / 12, 5.0 / 8, 1.0 / 2, -1.0 / 24},             /* 011  */ \
+     {3.0 / 128, -5.0 / 32, 45.0 / 64, 15.0 / 32, -5.0 / 128}}  /* 111  */
+static __constant__ double c_table1_f64[8][5] = WCNS_TABLE1_ROWS;
+static __constant__ float c_table1_f32[8][5] = WCNS_TABLE1_ROWS;
+
+struct SchemeConst {
+    double gamma, gm1;
+    double C, eps, CT;
+    int q;
+    double keep_all_K;   // tau < K * (min beta + eps) guarantees no cut (exact test)
+    float Cf, CTf, Kf;
+};
+
+// ------------------------------------------------------------------------
+// Exact-order FP64 arithmetic for the parts that decide the stencil flags.
+// These replay one fixed evaluation order with no FMA contraction, so the
+// flags are a deterministic function of the node values.
+// ------------------------------------------------------------------------
+__device__ __forceinline__ double mul_(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double add_(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sub_(double a, double b) { return __dadd_rn(a, -b); }
+__device__ __forceinline__ double div_(double a, double b) { return __ddiv_rn(a, b); }
+
+// p = (gamma-1) (E - (0.5 * sum m_a^2) / rho), sum taken in axis order.
+template <int ND>
+__device__ __forceinline__ double pressure_exact(const double* U, double gm1)
+{
+    double ke = mul_(U[1], U[1]);
+#pragma unroll
+    for (int a = 1; a < ND; ++a) ke = add_(ke, mul_(U[1 + a], U[1 + a]));
+    ke = div_(mul_(0.5, ke), U[0]);
+    return mul_(gm1, sub_(U[ND + 1], ke));
+}
+
+// Roe-averaged left eigenvectors of dF_d/dU between nodes a and b, in the
+// form needed for projection.  Field order: (u_n - c, entropy, shear waves
+// of the tangential axes in axis order, u_n + c).
+template <int ND>
+struct ProjFP64 {
+    double vel[ND];
+    double q2, H, c, un;
+    double l0[ND + 2];   // row of u_n - c
+    double l1[ND + 2];   // entropy row
+    double lN[ND + 2];   // row of u_n + c
+};
+
+template <int ND, int D>
+__device__ __forceinline__ void proj_setup_fp64(const double* Ua, const double* Ub, double gm1,
+                                                ProjFP64<ND>& P)
+{
+    const double ra = __dsqrt_rn(Ua[0]);
+    const double rb = __dsqrt_rn(Ub[0]);
+    const double Ha = div_(add_(Ua[ND + 1], pressure_exact<ND>(Ua, gm1)), Ua[0]);
+    const double Hb = div_(add_(Ub[ND + 1], pressure_exact<ND>(Ub, gm1)), Ub[0]);
+    const double den = add_(ra, rb);
+    double q2 = 0.0;
+#pragma unroll
+    for (int a = 0; a < ND; ++a) {
+        P.vel[a] = div_(add_(mul_(ra, div_(Ua[1 + a], Ua[0])), mul_(rb, div_(Ub[1 + a], Ub[0]))), den);
+        q2 = (a == 0) ? mul_(P.vel[0], P.vel[0]) : add_(q2, mul_(P.vel[a], P.vel[a]));
+    }
+    P.q2 = q2;
+    P.H = div_(add_(mul_(ra, Ha), mul_(rb, Hb)), den);
+    const double c2 = mul_(gm1, sub_(P.H, mul_(0.5, q2)));
+    P.c = __dsqrt_rn(c2);
+    P.un = P.vel[D];
+    const double b1 = div_(gm1, c2);
+    const double b2 = mul_(mul_(0.5, b1), q2);
+    const double unc = div_(P.un, P.c);
+    const double ic = div_(1.0, P.c);
+    P.l0[0] = mul_(0.5, add_(b2, unc));
+    P.lN[0] = mul_(0.5, sub_(b2, unc));
+    P.l1[0] = sub_(1.0, b2);
+#pragma unroll
+    for (int a = 0; a < ND; ++a) {
+        const double t = mul_(-b1, P.vel[a]);
+        P.l0[1 + a] = mul_(0.5, a == D ? sub_(t, ic) : t);
+        P.lN[1 + a] = mul_(0.5, a == D ? add_(t, ic) : t);
+        P.l1[1 + a] = mul_(b1, P.vel[a]);
+    }
+    P.l0[ND + 1] = mul_(0.5, b1);
+    P.lN[ND + 1] = mul_(0.5, b1);
+    P.l1[ND + 1] = -b1;
+}
+
+// Characteristic variables of one node, left-to-right sums.
+template <int ND, int D>
+__device__ __forceinline__ void project_fp64(const ProjFP64<ND>& P, const double* U, double* W)
+{
+    double s0 = mul_(P.l0[0], U[0]), s1 = mul_(P.l1[0], U[0]), sN = mul_(P.lN[0], U[0]);
+#pragma unroll
+    for (int v = 1; v < ND + 2; ++v) {
+        s0 = add_(s0, mul_(P.l0[v], U[v]));
+        s1 = add_(s1, mul_(P.l1[v], U[v]));
+        sN = add_(sN, mul_(P.lN[v], U[v]));
+    }
+    W[0] = s0;
+    W[1] = s1;
+    int k = 2;
+#pragma unroll
+    for (int t = 0; t < ND; ++t) {
+        if (t == D) continue;
+        W[k++] = add_(mul_(-P.vel[t], U[0]), U[1 + t]);
+    }
+    W[ND + 1] = sN;
+}
+
+// Eq. 10, 11, 15 and 16-18 on one stencil s[0..4] = u_{i-2} .. u_{i+2},
+// in one fixed order; chi_k is evaluated as s_k / sum s with
+// s_k = (g_k / max g)^q, which equals Eq. 17 and cannot overflow.
+__device__ __forceinline__ int select_fp64(const double s[5], const SchemeConst& K)
+{
+    double D1[3], D2[3], beta[3];
+    D1[0] = mul_(0.5, add_(sub_(s[0], mul_(4.0, s[1])), mul_(3.0, s[2])));
+    D1[1] = mul_(0.5, sub_(s[3], s[1]));
+    D1[2] = mul_(0.5, sub_(add_(mul_(-3.0, s[2]), mul_(4.0, s[3])), s[4]));
+    D2[0] = add_(sub_(s[0], mul_(2.0, s[1])), s[2]);
+    D2[1] = add_(sub_(s[1], mul_(2.0, s[2])), s[3]);
+    D2[2] = add_(sub_(s[2], mul_(2.0, s[3])), s[4]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) beta[k] = add_(mul_(D1[k], D1[k]), mul_(D2[k], D2[k]));
+    const double tau = fabs(sub_(beta[0], beta[2]));
+    // No stencil can be cut unless the largest gamma exceeds the smallest by
+    // the factor (3 C_T)^(-1/q); this bound (with a 2% margin) lets smooth
+    // stencils skip the divisions while deciding exactly as the full test.
+    const double bmin = fmin(fmin(beta[0], beta[1]), beta[2]) + K.eps;
+    if (tau < K.keep_all_K * bmin) return 7;
+    double g[3], gmax = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        g[k] = add_(K.C, div_(tau, add_(beta[k], K.eps)));
+        if (g[k] > gmax) gmax = g[k];
+    }
+    double sk[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double r = div_(g[k], gmax);
+        double p = r;
+        for (int e = 1; e < K.q; ++e) p = mul_(p, r);
+        sk[k] = p;
+    }
+    const double ssum = add_(add_(sk[0], sk[1]), sk[2]);
+    int flags = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        if (!(div_(sk[k], ssum) < K.CT)) flags |= 1 << k;
+    return flags;
+}
+
+// FP32 selection.  chi_k is invariant under s -> s/sc except through eps, so
+// the stencil is rescaled by sc = max |s_m| (beta, tau become O(1) and cannot
+// underflow), eps becomes max(eps/sc^2, FLT_MIN), tau = 0 keeps every stencil
+// without dividing, and the cutoff chi_k < C_T is tested as
+// s_k < C_T * sum s with s_k = (g_k / max g)^q.
+__device__ __forceinline__ int select_fp32(const float s[5], float inv_sc, float eps_s,
+                                           const SchemeConst& K)
+{
+    float t[5];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) t[m] = s[m] * inv_sc;
+    float D1[3], D2[3], beta[3];
+    D1[0] = 0.5f * (t[0] - 4.0f * t[1] + 3.0f * t[2]);
+    D1[1] = 0.5f * (t[3] - t[1]);
+    D1[2] = 0.5f * (-3.0f * t[2] + 4.0f * t[3] - t[4]);
+    D2[0] = t[0] - 2.0f * t[1] + t[2];
+    D2[1] = t[1] - 2.0f * t[2] + t[3];
+    D2[2] = t[2] - 2.0f * t[3] + t[4];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) beta[k] = D1[k] * D1[k] + D2[k] * D2[k];
+    const float tau = fabsf(beta[0] - beta[2]);
+    const float bmin = fminf(fminf(beta[0], beta[1]), beta[2]) + eps_s;
+    if (!(tau >= K.Kf * bmin)) return 7;           // also catches tau == 0
+    float g[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) g[k] = K.Cf + tau * __frcp_rn(beta[k] + eps_s);
+    const float gmax = fmaxf(fmaxf(g[0], g[1]), g[2]);
+    const float ig = __frcp_rn(gmax);
+    float sk[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float r = g[k] * ig;
+        float p = r;
+        for (int e = 1; e < K.q; ++e) p *= r;
+        sk[k] = p;
+    }
+    const float lim = K.CTf * (sk[0] + sk[1] + sk[2]);
+    int flags = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        if (!(sk[k] < lim)) flags |= 1 << k;
+    return flags;
+}
+
+// Eq. 12 with the weights of Eq. 19, as the equivalent Table-1 stencil.
+// The all-retained row (Eq. 7) is inlined; reduced rows come from constant
+// memory (only cut faces take that branch).
+template <typename T>
+__device__ __forceinline__ T interp_row(int flags, const T s[5])
+{
+    if (flags == 7) {
+        T u = T(3.0 / 128) * s[0];
+        u = fma(T(-5.0 / 32), s[1], u);
+        u = fma(T(45.0 / 64), s[2], u);
+        u = fma(T(15.0 / 32), s[3], u);
+        return fma(T(-5.0 / 128), s[4], u);
+    }
+    const T* row;
+    if constexpr (sizeof(T) == 8) row = c_table1_f64[flags];
+    else row = c_table1_f32[flags];
+    T u = row[0] * s[0];
+#pragma unroll
+    for (int j = 1; j < 5; ++j) u = fma(row[j], s[j], u);
+    return u;
+}
+
+// ------------------------------------------------------------------------
+// Euler primitives and midpoint fluxes (any evaluation order).
+// ------------------------------------------------------------------------
+template <int ND, typename T>
+__device__ __forceinline__ T pressure_of(const T* U, T gm1)
+{
+    T m2 = U[1] * U[1];
+#pragma unroll
+    for (int a = 1; a < ND; ++a) m2 = fma(U[1 + a], U[1 + a], m2);
+    return gm1 * (U[ND + 1] - T(0.5) * m2 / U[0]);
+}
+
+template <int ND, int D, typename T>
+__device__ __forceinline__ void phys_flux(const T* U, T p, T* F)
+{
+    const T un = U[1 + D] / U[0];
+    F[0] = U[1 + D];
+#pragma unroll
+    for (int a = 0; a < ND; ++a) F[1 + a] = U[1 + a] * un;
+    F[1 + D] += p;
+    F[ND + 1] = (U[ND + 1] + p) * un;
+}
+
+// Roe (1981) flux difference splitting, F = (F_L + F_R - sum |lam_k| alpha_k r_k)/2
+// with the wave strengths alpha_k of the Roe-averaged state.
+template <int ND, int D, typename T>
+__device__ __forceinline__ void roe_flux(const T* UL, const T* UR, T pL, T pR, T gm1, T* F)
+{
+    constexpr int NV = ND + 2;
+    T FL[NV], FR[NV];
+    phys_flux<ND, D>(UL, pL, FL);
+    phys_flux<ND, D>(UR, pR, FR);
+    const T sL = sqrt(UL[0]), sR = sqrt(UR[0]);
+    const T iL = T(1) / UL[0], iR = T(1) / UR[0];
+    const T w = T(1) / (sL + sR);
+    T vel[ND], dv[ND], q2 = 0;
+#pragma unroll
+    for (int a = 0; a < ND; ++a) {
+        const T uL = UL[1 + a] * iL, uR = UR[1 + a] * iR;
+        vel[a] = (sL * uL + sR * uR) * w;
+        dv[a] = uR - uL;
+        q2 = fma(vel[a], vel[a], q2);
+    }
+    const T H = (sL * (UL[ND + 1] + pL) * iL + sR * (UR[ND + 1] + pR) * iR) * w;
+    const T c2 = gm1 * (H - T(0.5) * q2);
+    const T c = sqrt(c2);
+    const T rho = sL * sR;
+    const T un = vel[D];
+    const T drho = UR[0] - UL[0], dp = pR - pL;
+    const T ic2 = T(1) / c2;
+    const T a0 = T(0.5) * (dp - rho * c * dv[D]) * ic2;
+    const T aN = T(0.5) * (dp + rho * c * dv[D]) * ic2;
+    const T a1 = drho - dp * ic2;
+    const T l0 = fabs(un - c) * a0, l1 = fabs(un) * a1, lN = fabs(un + c) * aN;
+    const T lt = fabs(un) * rho;
+    // sum of |lam_k| alpha_k r_k
+    T Dm[NV];
+    Dm[0] = l0 + l1 + lN;
+#pragma unroll
+    for (int a = 0; a < ND; ++a) Dm[1 + a] = vel[a] * Dm[0] + (a == D ? c * (lN - l0) : lt * dv[a]);
+    T e = H * (l0 + lN) + un * c * (lN - l0) + T(0.5) * q2 * l1;
+#pragma unroll
+    for (int a = 0; a < ND; ++a)
+        if (a != D) e = fma(vel[a], lt * dv[a], e);
+    Dm[ND + 1] = e;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) F[v] = T(0.5) * (FL[v] + FR[v] - Dm[v]);
+}
+
+// van Leer (1982) flux vector splitting: F = F+(U_L) + F-(U_R).
+template <int ND, int D, typename T>
+__device__ __forceinline__ void vanleer_half(const T* U, T p, T gamma, T gm1, T sgn, T* F)
+{
+    constexpr int NV = ND + 2;
+    const T ir = T(1) / U[0];
+    const T c = sqrt(gamma * p * ir);
+    const T un = U[1 + D] * ir;
+    const T M = un / c;
+    if (M >= T(1) || M <= T(-1)) {
+        if ((M >= T(1)) == (sgn > T(0))) {
+            phys_flux<ND, D>(U, p, F);
+        } else {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) F[v] = T(0);
+        }
+        return;
+    }
+    const T fm = sgn * T(0.25) * U[0] * c * (M + sgn) * (M + sgn);
+    T t2 = 0;
+#pragma unroll
+    for (int a = 0; a < ND; ++a)
+        if (a != D) t2 = fma(U[1 + a] * ir, U[1 + a] * ir, t2);
+    const T wn = gm1 * un + sgn * T(2) * c;
+    F[0] = fm;
+#pragma unroll
+    for (int a = 0; a < ND; ++a) F[1 + a] = fm * (U[1 + a] * ir);
+    F[1 + D] = fm * wn / gamma;
+    F[NV - 1] = fm * (wn * wn / (T(2) * (gamma * gamma - T(1))) + T(0.5) * t2);
+}
+
+}  // namespace wcns

@@ -1,0 +1,40 @@
+// wcns_internal.h -- launch interface between the C ABI and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include "wcns_sweep.cuh"
+
+namespace wcns {
+
+// Launch one sweep of direction dir.  T = double (fp64) or float (fp32);
+// load_fp64 selects a double input state for the float sweep.
+cudaError_t launch_sweep_fp64(int nd, int dir, int flux, const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_sweep_fp32(int nd, int dir, int flux, bool load_fp64, const SweepArgs& a,
+                              cudaStream_t s);
+// Raise the dynamic shared-memory limit of every sweep instance (once per device).
+cudaError_t prepare_sweeps_fp64();
+cudaError_t prepare_sweeps_fp32();
+
+// Time step, RK stages, reductions (wcns_rk.cu).
+struct StepScalars {      // device-resident
+    double dt;            // step of the current RK step (0 = finished)
+    double t;             // time reached at the end of the current step
+    double t_end;         // clip target (inf when unused)
+    unsigned long long lam_bits;   // max wave-speed sum (non-negative double bits)
+    unsigned long long steps;      // steps that advanced time since the last reset
+};
+
+cudaError_t launch_cfl(int nd, const double* U, long long N, const double* inv_h, double gamma,
+                       double cfl, int clip, StepScalars* sc, cudaStream_t s);
+cudaError_t launch_set_dt(double dt, int clip, StepScalars* sc, cudaStream_t s);
+cudaError_t launch_reset_clock(double t_end, StepScalars* sc, cudaStream_t s);
+// FP64 stage combinations (Shu-Osher SSP-RK3) over M = nv*N values.
+cudaError_t launch_rk_fp64(int stage, double* U0, double* U1, const double* L, long long M,
+                           const StepScalars* sc, cudaStream_t s);
+// FP32 stages: increments relative to the FP64 base state U0.
+cudaError_t launch_rk_fp32(int stage, double* U0, float* S, float* D, const float* L, long long M,
+                           const StepScalars* sc, cudaStream_t s);
+cudaError_t launch_conserved(int nv, const double* U, long long N, double vol, double* partials,
+                             int nblocks, cudaStream_t s);
+int conserved_blocks(long long N);
+
+}  // namespace wcns

@@ -1,0 +1,264 @@
+// wcns_rk.cu -- time step and stage kernels: the CFL reduction (FP64), the
+// SSP-RK3 stage combinations (Shu-Osher form, the third-order strong
+// stability preserving method the paper cites for time integration) and the
+// deterministic FP64 conservation totals.
+#include <math.h>
+
+#include "wcns_internal.h"
+
+namespace wcns {
+
+struct InvH {
+    double v[3];
+};
+
+__device__ __forceinline__ double warp_max(double x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+
+__device__ __forceinline__ double warp_sum(double x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// lambda = max_i sum_d (|u_d| + c) / h_d over all nodes, FP64.
+template <int ND>
+__global__ void __launch_bounds__(256) cfl_reduce_kernel(const double* __restrict__ U, long long N,
+                                                         InvH ih, double gamma,
+                                                         StepScalars* sc, int clip)
+{
+    if (clip && sc->t >= sc->t_end) return;   // finished: nothing to do
+    double m = 0.0;
+    const double gm1 = gamma - 1.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double rho = U[i];
+        const double ir = 1.0 / rho;
+        double m2 = 0.0, s = 0.0;
+        double vel[ND];
+#pragma unroll
+        for (int a = 0; a < ND; ++a) {
+            const double mv = U[(1 + a) * N + i];
+            m2 = fma(mv, mv, m2);
+            vel[a] = fabs(mv * ir);
+        }
+        const double p = gm1 * (U[(ND + 1) * N + i] - 0.5 * m2 * ir);
+        const double c = sqrt(gamma * p * ir);
+#pragma unroll
+        for (int a = 0; a < ND; ++a) s = fma(vel[a] + c, ih.v[a], s);
+        m = fmax(m, s);
+    }
+    m = warp_max(m);
+    __shared__ double red[8];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        m = warp_max(m);
+        if (threadIdx.x == 0)
+            atomicMax(&sc->lam_bits, (unsigned long long)__double_as_longlong(m));
+    }
+}
+
+// dt = CFL / lambda, clipped so the step lands on t_end.
+__global__ void cfl_finalize_kernel(StepScalars* sc, double cfl, int clip)
+{
+    const double t = sc->t;
+    const double lam = __longlong_as_double((long long)sc->lam_bits);
+    sc->lam_bits = 0ull;   // ready for the next reduction
+    if (clip && t >= sc->t_end) { sc->dt = 0.0; return; }
+    double dt = cfl / lam;
+    if (clip && t + dt > sc->t_end) {
+        dt = sc->t_end - t;
+        sc->t = sc->t_end;
+    } else {
+        sc->t = t + dt;
+    }
+    sc->dt = dt;
+    sc->steps += 1ull;
+}
+
+__global__ void set_dt_kernel(StepScalars* sc, double dt, int clip)
+{
+    const double t = sc->t;
+    if (clip && t >= sc->t_end) { sc->dt = 0.0; return; }
+    if (clip && t + dt > sc->t_end) { dt = sc->t_end - t; sc->t = sc->t_end; }
+    else sc->t = t + dt;
+    sc->dt = dt;
+    sc->steps += 1ull;
+}
+
+__global__ void reset_clock_kernel(StepScalars* sc, double t_end)
+{
+    sc->dt = 0.0;
+    sc->t = 0.0;
+    sc->t_end = t_end;
+    sc->lam_bits = 0ull;
+    sc->steps = 0ull;
+}
+
+cudaError_t launch_reset_clock(double t_end, StepScalars* sc, cudaStream_t s)
+{
+    reset_clock_kernel<<<1, 1, 0, s>>>(sc, t_end);
+    return cudaGetLastError();
+}
+
+static int reduce_blocks(long long N)
+{
+    long long b = (N + 255) / 256;
+    return (int)(b < 1216 ? (b < 1 ? 1 : b) : 1216);
+}
+
+cudaError_t launch_cfl(int nd, const double* U, long long N, const double* inv_h, double gamma,
+                       double cfl, int clip, StepScalars* sc, cudaStream_t s)
+{
+    InvH ih{{inv_h[0], inv_h[1], inv_h[2]}};
+    const int nb = reduce_blocks(N);
+    if (nd == 1) cfl_reduce_kernel<1><<<nb, 256, 0, s>>>(U, N, ih, gamma, sc, clip);
+    else if (nd == 2) cfl_reduce_kernel<2><<<nb, 256, 0, s>>>(U, N, ih, gamma, sc, clip);
+    else cfl_reduce_kernel<3><<<nb, 256, 0, s>>>(U, N, ih, gamma, sc, clip);
+    cfl_finalize_kernel<<<1, 1, 0, s>>>(sc, cfl, clip);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_dt(double dt, int clip, StepScalars* sc, cudaStream_t s)
+{
+    set_dt_kernel<<<1, 1, 0, s>>>(sc, dt, clip);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- FP64 stages
+// U1 = U0 + dt L;  U1 = 3/4 U0 + 1/4 (U1 + dt L);  U0 = 1/3 U0 + 2/3 (U1 + dt L)
+template <int STAGE>
+__global__ void __launch_bounds__(256) rk_fp64_kernel(double* __restrict__ U0, double* __restrict__ U1,
+                                                      const double* __restrict__ L, long long M,
+                                                      const StepScalars* sc)
+{
+    const double dt = sc->dt;
+    if (dt == 0.0) return;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double l = L[i];
+        if (STAGE == 1) {
+            U1[i] = fma(dt, l, U0[i]);
+        } else if (STAGE == 2) {
+            U1[i] = fma(0.75, U0[i], 0.25 * fma(dt, l, U1[i]));
+        } else {
+            U0[i] = fma(1.0 / 3.0, U0[i], (2.0 / 3.0) * fma(dt, l, U1[i]));
+        }
+    }
+}
+
+static int stream_blocks(long long M)
+{
+    long long b = (M + 255) / 256;
+    return (int)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
+}
+
+cudaError_t launch_rk_fp64(int stage, double* U0, double* U1, const double* L, long long M,
+                           const StepScalars* sc, cudaStream_t s)
+{
+    const int nb = stream_blocks(M);
+    if (stage == 1) rk_fp64_kernel<1><<<nb, 256, 0, s>>>(U0, U1, L, M, sc);
+    else if (stage == 2) rk_fp64_kernel<2><<<nb, 256, 0, s>>>(U0, U1, L, M, sc);
+    else rk_fp64_kernel<3><<<nb, 256, 0, s>>>(U0, U1, L, M, sc);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- FP32 stages
+// Stage values are U^(s) = U0 + D^(s): the FP64 base carries the magnitude,
+// the FP32 increment D carries the stage update, so nothing of the update is
+// lost to the size of U.  S = float(U0) + D is the next sweep's input.
+//   D1 = dt L,  D2 = (D1 + dt L)/4,  U0 += 2/3 (D2 + dt L)   (FP64 accumulation)
+template <int STAGE>
+__global__ void __launch_bounds__(256) rk_fp32_kernel(double* __restrict__ U0, float* __restrict__ S,
+                                                      float* __restrict__ D, const float* __restrict__ L,
+                                                      long long M, const StepScalars* sc)
+{
+    const double dtd = sc->dt;
+    if (dtd == 0.0) return;
+    const float dt = (float)dtd;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float l = L[i];
+        if (STAGE == 1) {
+            const float d = dt * l;
+            D[i] = d;
+            S[i] = __double2float_rn(U0[i]) + d;
+        } else if (STAGE == 2) {
+            const float d = 0.25f * fmaf(dt, l, D[i]);
+            D[i] = d;
+            S[i] = __double2float_rn(U0[i]) + d;
+        } else {
+            const float d = (2.0f / 3.0f) * fmaf(dt, l, D[i]);
+            U0[i] += (double)d;
+        }
+    }
+}
+
+cudaError_t launch_rk_fp32(int stage, double* U0, float* S, float* D, const float* L, long long M,
+                           const StepScalars* sc, cudaStream_t s)
+{
+    const int nb = stream_blocks(M);
+    if (stage == 1) rk_fp32_kernel<1><<<nb, 256, 0, s>>>(U0, S, D, L, M, sc);
+    else if (stage == 2) rk_fp32_kernel<2><<<nb, 256, 0, s>>>(U0, S, D, L, M, sc);
+    else rk_fp32_kernel<3><<<nb, 256, 0, s>>>(U0, S, D, L, M, sc);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- conservation
+// Deterministic: block b sums a fixed slice in a fixed tree order; one block
+// then sums the partials in index order.
+int conserved_blocks(long long N)
+{
+    long long b = (N + 2047) / 2048;
+    return (int)(b < 512 ? (b < 1 ? 1 : b) : 512);
+}
+
+__global__ void __launch_bounds__(256) conserved_partial_kernel(const double* __restrict__ U, long long N,
+                                                                int nv, double* partials)
+{
+    const long long chunk = (N + gridDim.x - 1) / gridDim.x;
+    const long long lo = blockIdx.x * chunk;
+    const long long hi = lo + chunk < N ? lo + chunk : N;
+    __shared__ double red[8];
+    for (int v = 0; v < nv; ++v) {
+        double s = 0.0;
+        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) s += U[v * N + i];
+        s = warp_sum(s);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+            partials[v * gridDim.x + blockIdx.x] = t;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void conserved_final_kernel(double* partials, int nb, int nv, double vol)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        for (int v = 0; v < nv; ++v) {
+            double t = 0.0;
+            for (int b = 0; b < nb; ++b) t += partials[v * nb + b];
+            partials[nv * nb + v] = t * vol;
+        }
+    }
+}
+
+cudaError_t launch_conserved(int nv, const double* U, long long N, double vol, double* partials,
+                             int nblocks, cudaStream_t s)
+{
+    conserved_partial_kernel<<<nblocks, 256, 0, s>>>(U, N, nv, partials);
+    conserved_final_kernel<<<1, 32, 0, s>>>(partials, nblocks, nv, vol);
+    return cudaGetLastError();
+}
+
+}  // namespace wcns

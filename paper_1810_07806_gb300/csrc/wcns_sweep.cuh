@@ -1,0 +1,356 @@
+// wcns_sweep.cuh -- the fused per-direction sweep kernel.
+//
+// One CTA owns a tile of TL grid lines x TS nodes along direction DIR.  It
+//  (1) stages the TS + 10 nodes of each line (5 ghost nodes per side: node i
+//      reads faces i +- 1/2, 3/2, 5/2 and face j + 1/2 reads nodes
+//      j-2 .. j+3) in shared memory, coalesced along x, applying the
+//      boundary rule (transmissive = copy the boundary node, periodic = wrap);
+//  (2) computes the TS + 5 midpoint fluxes of each line, one face per
+//      thread: characteristic projection, TENO selection and Table-1
+//      interpolation of both biased values, back-projection, Roe or van
+//      Leer flux (Sec. 2-3 of arXiv 1810.07806), into shared memory;
+//  (3) forms -f'_i by the sixth-order MD difference (Eq. 3) and writes or
+//      accumulates it into L (Eq. 2: the directions are summed).
+#pragma once
+#include "wcns_device.cuh"
+
+namespace wcns {
+
+enum { FLUX_ROE = 0, FLUX_VANLEER = 1 };
+
+struct SweepArgs {
+    const void* U;            // input state, LT, SoA
+    void* L;                  // output RHS, T, SoA
+    long long N;              // nodes
+    int n[3];                 // nodes per axis
+    int periodic;             // boundary rule of this direction
+    double inv_h;             // 1 / h_DIR
+    int accumulate;           // 0: L = -f'   1: L -= f'
+    uint8_t* flags;           // nullable debug output, block of this direction
+    long long* fallback;      // count of first-order fallback faces
+    const double* dt;         // nullable: skip all work when *dt == 0 (finished)
+    SchemeConst K;
+    float sqrt_eps_f;         // sqrt(eps) in float, for the FP32 rescaled eps
+};
+
+template <typename T, int ND, int DIR>
+struct TileGeom {
+    static constexpr int TL = (ND == 1) ? 1 : (DIR == 0 ? 4 : 16);   // lines per tile
+    static constexpr int TS = (ND == 1) ? 251 : 59;                   // nodes per line
+    static constexpr int P = TS + 2 * GHOST;                          // staged nodes
+    static constexpr int NF = TS + 5;                                 // faces
+    static constexpr int THREADS = 256;
+    static constexpr size_t smem_bytes()
+    {
+        return sizeof(T) * (size_t)(ND + 2) * TL * (P + NF);
+    }
+};
+
+// Shared-memory index: the memory-contiguous index is the fastest one.
+template <int DIR, int TL, int W>
+__device__ __forceinline__ int sidx(int v, int l, int s)
+{
+    return DIR == 0 ? (v * TL + l) * W + s : (v * W + s) * TL + l;
+}
+
+// ---------------------------------------------------------------- FP64 face
+template <int ND, int DIR, int FLUX>
+__device__ __forceinline__ void face_flux(double (&u)[6][ND + 2], const SweepArgs& a, double* F,
+                                          uint8_t* fl, bool& fell_back)
+{
+    constexpr int NV = ND + 2;
+    const double gm1 = a.K.gm1;
+    ProjFP64<ND> P;
+    proj_setup_fp64<ND, DIR>(u[2], u[3], gm1, P);
+    double Uj[NV], Uj1[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) { Uj[v] = u[2][v]; Uj1[v] = u[3][v]; }
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+        double W[NV];
+        project_fp64<ND, DIR>(P, u[m], W);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) u[m][v] = W[v];
+    }
+    double wL[NV], wR[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double sl[5], sr[5];
+#pragma unroll
+        for (int m = 0; m < 5; ++m) { sl[m] = u[m][k]; sr[m] = u[5 - m][k]; }
+        const int fL = select_fp64(sl, a.K);
+        const int fR = select_fp64(sr, a.K);
+        wL[k] = interp_row<double>(fL, sl);
+        wR[k] = interp_row<double>(fR, sr);
+        fl[k] = (uint8_t)(fL | (fR << 3));
+    }
+    // back-projection U = R w
+    double UL[NV], UR[NV];
+    {
+        const double c = P.c, un = P.un;
+        const double rl = wL[0] + wL[1] + wL[NV - 1], rr = wR[0] + wR[1] + wR[NV - 1];
+        const double dl = wL[NV - 1] - wL[0], dr = wR[NV - 1] - wR[0];
+        UL[0] = rl;
+        UR[0] = rr;
+        double el = fma(P.H, wL[0] + wL[NV - 1], fma(un * c, dl, 0.5 * P.q2 * wL[1]));
+        double er = fma(P.H, wR[0] + wR[NV - 1], fma(un * c, dr, 0.5 * P.q2 * wR[1]));
+        int k = 2;
+#pragma unroll
+        for (int t = 0; t < ND; ++t) {
+            if (t == DIR) {
+                UL[1 + t] = fma(P.vel[t], rl, c * dl);
+                UR[1 + t] = fma(P.vel[t], rr, c * dr);
+            } else {
+                UL[1 + t] = fma(P.vel[t], rl, wL[k]);
+                UR[1 + t] = fma(P.vel[t], rr, wR[k]);
+                el = fma(P.vel[t], wL[k], el);
+                er = fma(P.vel[t], wR[k], er);
+                ++k;
+            }
+        }
+        UL[NV - 1] = el;
+        UR[NV - 1] = er;
+    }
+    double pL = pressure_of<ND>(UL, gm1), pR = pressure_of<ND>(UR, gm1);
+    if (!(UL[0] > 0.0) || !(UR[0] > 0.0) || !(pL > 0.0) || !(pR > 0.0)) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) { UL[v] = Uj[v]; UR[v] = Uj1[v]; }
+        pL = pressure_of<ND>(UL, gm1);
+        pR = pressure_of<ND>(UR, gm1);
+        fell_back = true;
+    }
+    if (FLUX == FLUX_ROE) {
+        roe_flux<ND, DIR>(UL, UR, pL, pR, gm1, F);
+    } else {
+        double Fp[NV], Fm[NV];
+        vanleer_half<ND, DIR>(UL, pL, a.K.gamma, gm1, 1.0, Fp);
+        vanleer_half<ND, DIR>(UR, pR, a.K.gamma, gm1, -1.0, Fm);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) F[v] = Fp[v] + Fm[v];
+    }
+}
+
+// ---------------------------------------------------------------- FP32 face
+template <int ND, int DIR, int FLUX>
+__device__ __forceinline__ void face_flux(float (&u)[6][ND + 2], const SweepArgs& a, float* F,
+                                          uint8_t* fl, bool& fell_back)
+{
+    constexpr int NV = ND + 2;
+    const float gm1 = (float)a.K.gm1;
+    // Roe average of nodes j, j+1 and the closed form of L U:
+    //   P = b1 (E - vel.m + q2 rho / 2), Q = (u_n rho - m_n) / c,
+    //   w_0 = (P + Q)/2, w_1 = rho - P, w_t = m_t - vel_t rho, w_N = (P - Q)/2.
+    const float* Ua = u[2];
+    const float* Ub = u[3];
+    const float sa = sqrtf(Ua[0]), sb = sqrtf(Ub[0]);
+    const float ia = __frcp_rn(Ua[0]), ib = __frcp_rn(Ub[0]);
+    const float wsum = __frcp_rn(sa + sb);
+    float vel[ND], q2 = 0.f;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+        vel[d] = (sa * Ua[1 + d] * ia + sb * Ub[1 + d] * ib) * wsum;
+        q2 = fmaf(vel[d], vel[d], q2);
+    }
+    const float pa = pressure_of<ND>(Ua, gm1), pb = pressure_of<ND>(Ub, gm1);
+    const float H = (sa * (Ua[ND + 1] + pa) * ia + sb * (Ub[ND + 1] + pb) * ib) * wsum;
+    const float c2 = gm1 * (H - 0.5f * q2);
+    const float c = sqrtf(c2);
+    const float ic = __frcp_rn(c);
+    const float hb1 = 0.5f * gm1 * __frcp_rn(c2);   // b1 / 2
+    const float un = vel[DIR];
+    float Uj[NV], Uj1[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) { Uj[v] = Ua[v]; Uj1[v] = Ub[v]; }
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+        float* U = u[m];
+        float vm = vel[0] * U[1];
+#pragma unroll
+        for (int d = 1; d < ND; ++d) vm = fmaf(vel[d], U[1 + d], vm);
+        const float Ph = hb1 * (fmaf(0.5f * q2, U[0], U[ND + 1]) - vm);   // P/2
+        const float Qh = 0.5f * ic * fmaf(un, U[0], -U[1 + DIR]);         // Q/2
+        float W[NV];
+        W[0] = Ph + Qh;
+        W[1] = fmaf(-2.f, Ph, U[0]);
+        int k = 2;
+#pragma unroll
+        for (int t = 0; t < ND; ++t) {
+            if (t == DIR) continue;
+            W[k++] = fmaf(-vel[t], U[0], U[1 + t]);
+        }
+        W[NV - 1] = Ph - Qh;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) U[v] = W[v];
+    }
+    float wL[NV], wR[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        float sl[5], sr[5];
+        float sc = 0.f;
+#pragma unroll
+        for (int m = 0; m < 6; ++m) sc = fmaxf(sc, fabsf(u[m][k]));
+#pragma unroll
+        for (int m = 0; m < 5; ++m) { sl[m] = u[m][k]; sr[m] = u[5 - m][k]; }
+        int fL = 7, fR = 7;
+        if (sc > 0.f) {
+            const float inv = __frcp_rn(sc);
+            const float e = a.sqrt_eps_f * inv;
+            const float eps_s = fmaxf(e * e, 1.17549435e-38f);
+            fL = select_fp32(sl, inv, eps_s, a.K);
+            fR = select_fp32(sr, inv, eps_s, a.K);
+        }
+        wL[k] = interp_row<float>(fL, sl);
+        wR[k] = interp_row<float>(fR, sr);
+        fl[k] = (uint8_t)(fL | (fR << 3));
+    }
+    float UL[NV], UR[NV];
+    {
+        const float rl = wL[0] + wL[1] + wL[NV - 1], rr = wR[0] + wR[1] + wR[NV - 1];
+        const float dl = wL[NV - 1] - wL[0], dr = wR[NV - 1] - wR[0];
+        UL[0] = rl;
+        UR[0] = rr;
+        float el = fmaf(H, wL[0] + wL[NV - 1], fmaf(un * c, dl, 0.5f * q2 * wL[1]));
+        float er = fmaf(H, wR[0] + wR[NV - 1], fmaf(un * c, dr, 0.5f * q2 * wR[1]));
+        int k = 2;
+#pragma unroll
+        for (int t = 0; t < ND; ++t) {
+            if (t == DIR) {
+                UL[1 + t] = fmaf(vel[t], rl, c * dl);
+                UR[1 + t] = fmaf(vel[t], rr, c * dr);
+            } else {
+                UL[1 + t] = fmaf(vel[t], rl, wL[k]);
+                UR[1 + t] = fmaf(vel[t], rr, wR[k]);
+                el = fmaf(vel[t], wL[k], el);
+                er = fmaf(vel[t], wR[k], er);
+                ++k;
+            }
+        }
+        UL[NV - 1] = el;
+        UR[NV - 1] = er;
+    }
+    float pL = pressure_of<ND>(UL, gm1), pR = pressure_of<ND>(UR, gm1);
+    if (!(UL[0] > 0.f) || !(UR[0] > 0.f) || !(pL > 0.f) || !(pR > 0.f)) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) { UL[v] = Uj[v]; UR[v] = Uj1[v]; }
+        pL = pressure_of<ND>(UL, gm1);
+        pR = pressure_of<ND>(UR, gm1);
+        fell_back = true;
+    }
+    if (FLUX == FLUX_ROE) {
+        roe_flux<ND, DIR>(UL, UR, pL, pR, gm1, F);
+    } else {
+        float Fp[NV], Fm[NV];
+        vanleer_half<ND, DIR>(UL, pL, (float)a.K.gamma, gm1, 1.f, Fp);
+        vanleer_half<ND, DIR>(UR, pR, (float)a.K.gamma, gm1, -1.f, Fm);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) F[v] = Fp[v] + Fm[v];
+    }
+}
+
+// ---------------------------------------------------------------- kernel
+template <typename T, typename LT, int ND, int DIR, int FLUX>
+__global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a)
+{
+    constexpr int NV = ND + 2;
+    using G = TileGeom<T, ND, DIR>;
+    constexpr int TL = G::TL, TS = G::TS, P = G::P, NF = G::NF;
+    if (a.dt != nullptr && *a.dt == 0.0) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sS = reinterpret_cast<T*>(smem_raw);
+    T* sF = sS + NV * TL * P;
+
+    const int nx = a.n[0], ny = a.n[1];
+    const int nd = a.n[DIR];
+    const long long N = a.N;
+    long long sd;
+    int pos0, lfirst, lcount;
+    long long base0, lstride;   // base offset of local line l = base0 + l * lstride
+    long long line0;            // global line index of local line 0 (for flags)
+    if (DIR == 0) {
+        const int rows = (int)(N / nx);
+        sd = 1;
+        pos0 = blockIdx.y * TS;
+        lfirst = blockIdx.x * TL;
+        lcount = min(TL, rows - lfirst);
+        base0 = (long long)lfirst * nx;
+        lstride = nx;
+        line0 = lfirst;
+    } else {
+        sd = (DIR == 1) ? (long long)nx : (long long)nx * ny;
+        pos0 = blockIdx.y * TS;
+        lfirst = blockIdx.x * TL;
+        lcount = min(TL, nx - lfirst);
+        const long long outer = blockIdx.z;   // z for DIR 1, y for DIR 2
+        base0 = (DIR == 1 ? outer * nx * ny : outer * nx) + lfirst;
+        lstride = 1;
+        line0 = outer * nx + lfirst;
+    }
+    const int tcount = min(TS, nd - pos0);
+    const int nfaces = tcount + 5;
+
+    // (1) stage nodes pos0-5 .. pos0+TS+4 of each line
+    const LT* U = reinterpret_cast<const LT*>(a.U);
+    for (int e = threadIdx.x; e < NV * TL * P; e += blockDim.x) {
+        int v, l, s;
+        if (DIR == 0) { s = e % P; const int r = e / P; l = r % TL; v = r / TL; }
+        else { l = e % TL; const int r = e / TL; s = r % P; v = r / P; }
+        if (l >= lcount) continue;
+        int p = pos0 - GHOST + s;
+        if (a.periodic) { p %= nd; if (p < 0) p += nd; }
+        else p = min(max(p, 0), nd - 1);
+        sS[sidx<DIR, TL, P>(v, l, s)] = (T)U[v * N + base0 + l * lstride + (long long)p * sd];
+    }
+    __syncthreads();
+
+    // (2) midpoint fluxes of faces j + 1/2, j = pos0 - 3 + f
+    int fb = 0;
+    for (int e = threadIdx.x; e < TL * NF; e += blockDim.x) {
+        int l, f;
+        if (DIR == 0) { f = e % NF; l = e / NF; } else { l = e % TL; f = e / TL; }
+        if (l >= lcount || f >= nfaces) continue;
+        T u[6][NV];
+#pragma unroll
+        for (int m = 0; m < 6; ++m)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) u[m][v] = sS[sidx<DIR, TL, P>(v, l, f + m)];
+        T F[NV];
+        uint8_t fl[NV];
+        bool fell = false;
+        face_flux<ND, DIR, FLUX>(u, a, F, fl, fell);
+        fb += fell ? 1 : 0;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sF[sidx<DIR, TL, NF>(v, l, f)] = F[v];
+        if (a.flags != nullptr && (f < TS || pos0 + TS >= nd)) {
+            const long long lines = N / nd;
+            const long long j3 = pos0 + f;   // j + 3
+#pragma unroll
+            for (int k = 0; k < NV; ++k)
+                a.flags[((long long)k * lines + line0 + l) * (nd + 5) + j3] = fl[k];
+        }
+    }
+    if (fb) atomicAdd((unsigned long long*)a.fallback, (unsigned long long)fb);
+    __syncthreads();
+
+    // (3) Eq. 3 at nodes pos0 .. pos0 + tcount - 1
+    T* L = reinterpret_cast<T*>(a.L);
+    const T ih = (T)a.inv_h;
+    for (int e = threadIdx.x; e < TL * TS; e += blockDim.x) {
+        int l, t;
+        if (DIR == 0) { t = e % TS; l = e / TS; } else { l = e % TL; t = e / TL; }
+        if (l >= lcount || t >= tcount) continue;
+        const long long g = base0 + l * lstride + (long long)(pos0 + t) * sd;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const T* Fv = sF;
+            const T d1 = Fv[sidx<DIR, TL, NF>(v, l, t + 3)] - Fv[sidx<DIR, TL, NF>(v, l, t + 2)];
+            const T d2 = Fv[sidx<DIR, TL, NF>(v, l, t + 4)] - Fv[sidx<DIR, TL, NF>(v, l, t + 1)];
+            const T d3 = Fv[sidx<DIR, TL, NF>(v, l, t + 5)] - Fv[sidx<DIR, TL, NF>(v, l, t + 0)];
+            const T fp = fma(T(MD_A1), d1, fma(T(MD_A2), d2, T(MD_A3) * d3));
+            const T val = -fp * ih;
+            if (a.accumulate) L[v * N + g] += val;
+            else L[v * N + g] = val;
+        }
+    }
+}
+
+}  // namespace wcns

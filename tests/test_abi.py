@@ -1,0 +1,69 @@
+"""CPU checks of the C ABI: the library loads, exports every declared entry
+point, and validates its arguments before touching a GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_1810_07806_gb300 import wcns
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(wcns_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    names = _declared()
+    assert {"wcns_create", "wcns_rhs", "wcns_step_rk3", "wcns_destroy"} <= names
+    lib = C.CDLL(wcns.LIB_PATH)
+    missing = [n for n in sorted(names) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_default_params_are_the_papers():
+    p = wcns.default_params()
+    assert (p.C, p.eps, p.CT, p.q) == (1.0, 1e-40, 1e-5, 6)   # Eq. 16, Sec. 2.3
+    assert p.characteristic == 1 and p.weights == 0 and p.diff == 0
+    assert p.precision == wcns.FP64
+
+
+def _create(grid, gamma=1.4, **kw):
+    p = wcns.default_params(**kw)
+    h = C.c_void_p()
+    st = wcns.lib().wcns_create(C.byref(grid), gamma, C.byref(p), C.byref(h))
+    return st, h
+
+
+@pytest.mark.parametrize("bad", [
+    dict(ndim=0), dict(ndim=4), dict(gamma=1.0), dict(q=0), dict(CT=0.5), dict(C=0.0),
+    dict(flux=7), dict(characteristic=0), dict(entropy_fix=1), dict(precision=3), dict(cfl=0.0),
+    dict(n=(1,)), dict(half_periodic=True)])
+def test_create_rejects_bad_arguments_without_a_gpu(bad):
+    ndim = bad.get("ndim", 1)
+    n = bad.get("n", (16,))
+    g = wcns.make_grid(max(1, min(ndim, 3)), n + (1, 1), (0, 0, 0), (1, 1, 1), (0, 0, 0))
+    g.ndim = ndim
+    if bad.get("half_periodic"):
+        g.bc[0][0] = wcns.BC_PERIODIC
+    kw = {k: v for k, v in bad.items() if k not in ("ndim", "n", "gamma", "half_periodic")}
+    st, h = _create(g, bad.get("gamma", 1.4), **kw)
+    assert st == wcns.ERR_INVALID
+    assert h.value is None
+    assert len(wcns.lib().wcns_last_error()) > 0
+
+
+def test_null_arguments_are_rejected():
+    L = wcns.lib()
+    assert L.wcns_create(None, 1.4, None, None) == wcns.ERR_INVALID
+    assert L.wcns_rhs(None, None, None, None, None) == wcns.ERR_INVALID
+    assert L.wcns_step_rk3(None, None, 0.0, None, None) == wcns.ERR_INVALID
+    assert L.wcns_destroy(None) == wcns.OK

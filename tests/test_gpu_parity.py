@@ -1,0 +1,276 @@
+"""GPU parity of libwcns against the FP64 CPU oracle, through the C ABI.
+
+FP64 path: per RHS, |L_gpu - L_ora| <= 1e-13 (|L_ora| + S_v) element by
+element, where S_v = sum_d max_i (|F_d,v(U_i)| + c_i |U_v,i|) / h_d is the
+flux scale of variable v (the MD difference of Eq. 3 subtracts fluxes of
+that size, so round-off in them appears divided by h); stencil flags
+identical.  End time: L1 difference <= 1e-10.  FP32 path: stated error
+bounds against the same oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1810_07806_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1810_07806_gb300 import wcns  # noqa: E402
+
+DEV = "cuda:0"
+RTOL = 1e-13
+
+
+def ora_cfg(pb, flux):
+    return O.make_cfg(ndim=pb.ndim, n=pb.n, h=pb.h, periodic=pb.periodic, gamma=pb.gamma,
+                      flux=O.FLUX_ROE if flux == wcns.FLUX_ROE else O.FLUX_VANLEER)
+
+
+def flux_scale(U, pb):
+    nd = pb.ndim
+    rho, vel, p = inputs.cons_to_prim(U, pb.gamma)
+    c = np.sqrt(pb.gamma * np.abs(p) / rho)
+    S = np.zeros(nd + 2)
+    for d in range(nd):
+        F = np.zeros_like(U)
+        F[0] = U[1 + d]
+        for a in range(nd):
+            F[1 + a] = U[1 + a] * vel[d]
+        F[1 + d] += p
+        F[nd + 1] = (U[nd + 1] + p) * vel[d]
+        for v in range(nd + 2):
+            S[v] += np.max(np.abs(F[v]) + c * np.abs(U[v])) / pb.h[d]
+    return S
+
+
+def gpu_rhs(pb, U, flux=wcns.FLUX_ROE, fp32=False, want_flags=True):
+    s = wcns.Solver.for_problem(pb, flux=flux, precision=wcns.FP32 if fp32 else wcns.FP64)
+    dt = torch.float32 if fp32 else torch.float64
+    Ud = torch.from_numpy(np.ascontiguousarray(U)).to(DEV, dt)
+    Ld = torch.empty_like(Ud)
+    fl = torch.zeros(s.flags_bytes, dtype=torch.uint8, device=DEV) if want_flags else None
+    s.rhs(Ud, Ld, fl)
+    torch.cuda.synchronize()
+    out = Ld.double().cpu().numpy(), (fl.cpu().numpy() if want_flags else None), s.fallback_count()
+    s.close()
+    return out
+
+
+def assert_rhs_parity(pb, U, flux):
+    cfg = ora_cfg(pb, flux)
+    Lo, flo, _, np_o, _ = O.euler_rhs(cfg, U, want_flags=True)
+    Lg, flg, np_g = gpu_rhs(pb, U, flux)
+    S = flux_scale(U, pb).reshape((-1,) + (1,) * pb.ndim)
+    err = np.abs(Lg - Lo)
+    tol = RTOL * (np.abs(Lo) + S)
+    bad = err > tol
+    assert not bad.any(), "max err/tol %.3g at %s" % ((err / tol).max(), np.argwhere(bad)[:5])
+    assert flo.shape == flg.shape
+    mism = np.count_nonzero(flo != flg)
+    assert mism == 0, "%d flag bytes differ" % mism
+    assert np_g == np_o
+    return Lo, flo
+
+
+STATES = {
+    "sod400": lambda: inputs.shock_tube(400),
+    "lax157": lambda: inputs.shock_tube(157, states=inputs.LAX, t_end=0.14, name="lax"),
+    "quad67x45": lambda: inputs.four_quadrant(67, ny=45),
+    "quad6_40": lambda: inputs.four_quadrant(40, quads=inputs.LAX_LIU_6, name="lax_liu_6"),
+    "tgv20": lambda: inputs.taylor_green(20),
+}
+
+
+@pytest.mark.parametrize("flux", [wcns.FLUX_ROE, wcns.FLUX_VANLEER])
+@pytest.mark.parametrize("name", sorted(STATES))
+def test_rhs_parity_initial_states(name, flux):
+    pb = STATES[name]()
+    assert_rhs_parity(pb, pb.U0, flux)
+
+
+@pytest.mark.parametrize("flux", [wcns.FLUX_ROE, wcns.FLUX_VANLEER])
+@pytest.mark.parametrize("name,steps", [("sod400", 60), ("quad67x45", 12), ("lax157", 40)])
+def test_rhs_parity_evolved_states(name, steps, flux):
+    """States with smeared shocks and contacts exercise every cut pattern."""
+    pb = STATES[name]()
+    cfg = ora_cfg(pb, flux)
+    U = pb.U0.copy()
+    O.euler_run(cfg, U, 0.5, 10.0, max_steps=steps)
+    _, flo = assert_rhs_parity(pb, U, flux)
+    assert np.count_nonzero(flo != 0x3F) > 0   # some stencils were cut
+
+
+def _rough(nd, n, periodic, seed):
+    U = inputs.random_rough_state(nd, n, seed)
+    lo = (0.0,) * nd
+    hi = tuple(1.0 + 0.3 * a for a in range(nd))
+    return inputs._finish("rough", nd, n, lo, hi, periodic, 1.4, U, 0.0)
+
+
+@pytest.mark.parametrize("flux", [wcns.FLUX_ROE, wcns.FLUX_VANLEER])
+@pytest.mark.parametrize("nd,n,periodic", [
+    (1, (517,), (0,)), (1, (61,), (1,)), (2, (70, 61), (1, 0)), (2, (131, 7), (0, 1)),
+    (3, (21, 19, 17), (1, 0, 1)), (3, (64, 5, 9), (0, 0, 0))])
+def test_rhs_parity_rough_states(nd, n, periodic, flux):
+    pb = _rough(nd, n, periodic, seed=sum(n))
+    assert_rhs_parity(pb, pb.U0, flux)
+
+
+@pytest.mark.parametrize("nd,n,periodic", [
+    (1, (2,), (0,)), (1, (1,), (1,)), (2, (3, 2), (0, 0)), (2, (5, 1), (0, 1)), (3, (2, 3, 1), (0, 0, 1))])
+def test_rhs_parity_degenerate_sizes(nd, n, periodic):
+    pb = _rough(nd, n, periodic, seed=3)
+    assert_rhs_parity(pb, pb.U0, wcns.FLUX_ROE)
+
+
+def test_free_stream_rhs_is_exactly_zero_on_gpu():
+    pb = inputs.taylor_green(12)
+    U = np.empty_like(pb.U0)
+    for v, val in enumerate((1.3, 0.4, -0.2, 0.1, 3.0)):
+        U[v] = val
+    for fp32 in (False, True):
+        L, _, _ = gpu_rhs(pb, U, fp32=fp32)
+        assert np.all(L == 0.0)
+
+
+def test_sod_end_state_matches_oracle():
+    """Sod, 400 nodes, t = 0.2, CFL 0.5, Roe: L1 difference <= 1e-10."""
+    pb = inputs.shock_tube(400)
+    cfg = ora_cfg(pb, wcns.FLUX_ROE)
+    Uo = pb.U0.copy()
+    t_o, steps_o, _ = O.euler_run(cfg, Uo, 0.5, 0.2)
+    s = wcns.Solver.for_problem(pb, flux=wcns.FLUX_ROE, cfl=0.5)
+    Ud = torch.from_numpy(pb.U0.copy()).to(DEV)
+    t_g, steps_g = s.advance(Ud, 0.2, check_every=16)
+    Ug = Ud.cpu().numpy()
+    assert t_g == t_o == 0.2
+    assert steps_g == steps_o
+    l1 = np.mean(np.abs(Ug - Uo), axis=1)
+    assert np.all(l1 <= 1e-10), l1
+
+
+def test_quadrant_end_state_matches_oracle():
+    pb = inputs.four_quadrant(48, t_end=0.1)
+    cfg = ora_cfg(pb, wcns.FLUX_ROE)
+    Uo = pb.U0.copy()
+    t_o, steps_o, _ = O.euler_run(cfg, Uo, 0.5, 0.1)
+    s = wcns.Solver.for_problem(pb)
+    Ud = torch.from_numpy(pb.U0.copy()).to(DEV)
+    t_g, steps_g = s.advance(Ud, 0.1)
+    assert steps_g == steps_o and t_g == t_o
+    l1 = np.mean(np.abs(Ud.cpu().numpy() - Uo).reshape(4, -1), axis=1)
+    assert np.all(l1 <= 1e-10), l1
+
+
+def test_step_with_given_dt_and_cfl_dt_match_oracle():
+    pb = inputs.taylor_green(16)
+    cfg = ora_cfg(pb, wcns.FLUX_ROE)
+    s = wcns.Solver.for_problem(pb)
+    Ud = torch.from_numpy(pb.U0.copy()).to(DEV)
+    dt_g = s.cfl_dt(Ud)
+    dt_o = O.cfl_dt(cfg, pb.U0, 0.5)
+    assert dt_g == pytest.approx(dt_o, rel=1e-14)
+    used = s.step(Ud, 0.0, want_dt=True)
+    assert used == pytest.approx(dt_o, rel=1e-14)
+    Uo = pb.U0.copy()
+    O.rk3_step(cfg, Uo, used)
+    assert np.max(np.abs(Ud.cpu().numpy() - Uo)) <= 1e-12 * np.max(np.abs(Uo))
+    U2 = torch.from_numpy(pb.U0.copy()).to(DEV)
+    s.step(U2, 1e-3)
+    Uo = pb.U0.copy()
+    O.rk3_step(cfg, Uo, 1e-3)
+    assert np.max(np.abs(U2.cpu().numpy() - Uo)) <= 1e-12 * np.max(np.abs(Uo))
+
+
+def test_periodic_conservation_on_gpu():
+    pb = inputs.taylor_green(32)
+    s = wcns.Solver.for_problem(pb)
+    Ud = torch.from_numpy(pb.U0.copy()).to(DEV)
+    c0 = np.array(s.conserved(Ud))
+    cfg = ora_cfg(pb, wcns.FLUX_ROE)
+    assert np.allclose(c0, O.conserved(cfg, pb.U0), rtol=1e-13, atol=1e-13 * np.abs(c0).max())
+    for _ in range(5):
+        s.step(Ud)
+    c1 = np.array(s.conserved(Ud))
+    scale = O.conserved(cfg, np.abs(pb.U0))
+    scale = np.maximum(scale, scale[1:4].max())
+    assert np.all(np.abs(c1 - c0) <= 1e-13 * scale * 5)
+
+
+# ---------------------------------------------------------------- full-size, sampled
+def _sample(N, count, seed):
+    rng = np.random.default_rng(seed)
+    idx = rng.choice(N, size=min(count, N), replace=False)
+    return np.sort(idx)
+
+
+@pytest.mark.parametrize("which", ["quad1024", "tgv256"])
+def test_full_size_rhs_sampled_against_oracle(which):
+    """At the benchmark sizes (1024^2 four-quadrant, 256^3 Taylor-Green), in the
+    benchmark's launch configuration, sampled nodes match the oracle."""
+    pb = inputs.four_quadrant(1024) if which == "quad1024" else inputs.taylor_green(256)
+    s = wcns.Solver.for_problem(pb)
+    Ud = torch.from_numpy(pb.U0).to(DEV)
+    for _ in range(2):      # move off the initial condition
+        s.step(Ud)
+    U = Ud.cpu().numpy()
+    Ld = torch.empty_like(Ud)
+    s.rhs(Ud, Ld)
+    Lg = Ld.cpu().numpy().reshape(pb.nv, -1)
+    idx = _sample(pb.cells, 4000, 7)
+    # include the corners, edges and the interfaces of the quadrants
+    extra = [0, pb.cells - 1, pb.n[0] - 1, pb.cells // 2, pb.cells // 2 + pb.n[0] // 2]
+    idx = np.unique(np.concatenate([idx, extra]))
+    Lo = O.euler_rhs_at(ora_cfg(pb, wcns.FLUX_ROE), U, idx)
+    S = flux_scale(U, pb)[:, None]
+    err = np.abs(Lg[:, idx] - Lo)
+    assert np.all(err <= RTOL * (np.abs(Lo) + S)), (err / (np.abs(Lo) + S)).max()
+
+
+# ---------------------------------------------------------------- FP32 path
+def test_fp32_rhs_close_to_oracle():
+    """FP32 RHS on a smooth state: normwise relative error of a few 1e-6."""
+    pb = inputs.taylor_green(32)
+    Lo = O.euler_rhs(ora_cfg(pb, wcns.FLUX_ROE), pb.U0)[0]
+    Lg, fl, _ = gpu_rhs(pb, pb.U0, fp32=True)
+    S = flux_scale(pb.U0, pb).reshape(-1, 1, 1, 1)
+    rel = np.max(np.abs(Lg - Lo) / (np.abs(Lo) + S))
+    assert rel < 2e-6, rel
+
+
+def test_fp32_sod_end_state_error_vs_oracle():
+    """FP32 interpolation/flux/difference with FP64 accumulation: relative L1
+    error of the Sod end state against the FP64 oracle."""
+    pb = inputs.shock_tube(400)
+    Uo = pb.U0.copy()
+    O.euler_run(ora_cfg(pb, wcns.FLUX_ROE), Uo, 0.5, 0.2)
+    s = wcns.Solver.for_problem(pb, precision=wcns.FP32)
+    Ud = torch.from_numpy(pb.U0.copy()).to(DEV)
+    t, _ = s.advance(Ud, 0.2)
+    assert t == 0.2
+    rel = np.sum(np.abs(Ud.cpu().numpy() - Uo), axis=1) / np.sum(np.abs(Uo), axis=1)
+    assert np.all(rel < 1e-4), rel
+
+
+def test_nonphysical_state_falls_back_like_the_oracle():
+    """Node-wise random density, pressure and velocity over several decades:
+    interpolated states go negative on about a third of the faces; both
+    implementations fall back to first order on exactly the same faces."""
+    for nd, n in ((1, (300,)), (2, (40, 33))):
+        rng = np.random.default_rng(11 + nd)
+        shape = tuple(reversed(n))
+        rho = 10 ** rng.uniform(-3, 0, shape)
+        p = 10 ** rng.uniform(-4, 0, shape)
+        vel = [rng.uniform(-3, 3, shape) for _ in range(nd)]
+        U = inputs.prim_to_cons(rho, vel, p, 1.4)
+        pb = inputs._finish("noise", nd, n, (0.0,) * nd, (1.0,) * nd, (0,) * nd, 1.4, U, 0.0)
+        cfg = ora_cfg(pb, wcns.FLUX_ROE)
+        _, _, _, np_o, _ = O.euler_rhs(cfg, U, want_flags=True)
+        assert np_o > 50
+        assert_rhs_parity(pb, U, wcns.FLUX_ROE)
