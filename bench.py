@@ -1,0 +1,368 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 TCNS library: RHS cell-updates per second.
+
+Workload (default): inviscid Taylor-Green vortex on a periodic 256^3 grid
+(gamma 1.4, Roe flux, CFL 0.5), advanced by SSP-RK3 steps with the FP32
+bulk path (single-precision interpolation, flux and differencing; FP64
+CFL reduction and state accumulation).  One step = one RK3 step = three
+RHS evaluations; value = nodes x 3 x steps x ranks / max-over-ranks time.
+The FP64 plain path is timed on the same workload and reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload tgv256|quad1024|sod400]
+
+With N > 1 (torchrun) every rank advances its own replica (weak scaling,
+no data-path collective: the instances are independent).
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "WCNS RHS cell-updates/s"
+UNIT = "cell-updates/s"
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12     # SMs x FP64 FMA/clk x FMA x max SM clock
+
+# Flops per face and per node of one sweep direction of the FP32 kernel,
+# counted from its arithmetic (FMA = 2, add/mul/min/max/abs = 1, one MUFU
+# op = 1) with every stencil taking the no-cut branch (smooth flow).
+FACE_FLOPS = {1: 520, 2: 770, 3: 1040}
+NODE_FLOPS = {1: 30, 2: 40, 3: 50}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="tgv256", choices=["tgv256", "quad1024", "sod400"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain-path line")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_1810_07806_gb300 import inputs
+    if name == "tgv256":
+        pb = inputs.taylor_green(256)
+        return pb, dict(workload="taylor_green_3d_256^3_periodic", nodes=pb.cells, nv=5,
+                        precision="fp32 bulk (fp64 reductions + accumulation)", flux="roe", cfl=0.5), True
+    if name == "quad1024":
+        pb = inputs.four_quadrant(1024)
+        return pb, dict(workload="four_quadrant_riemann_2d_1024^2_lax_liu_3", nodes=pb.cells, nv=4,
+                        precision="fp64", flux="roe", cfl=0.5), False
+    pb = inputs.shock_tube(400)
+    return pb, dict(workload="sod_1d_400", nodes=pb.cells, nv=3, precision="fp64", flux="roe",
+                    cfl=0.5), False
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_id):
+        self.dev_id = dev_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.dev_id:
+                cmd += ["-i", self.dev_id]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        mhz = [float(r[1]) for r in rows if re.match(r"^[0-9.]+$", r[1])]
+        mx = [float(r[2]) for r in rows if re.match(r"^[0-9.]+$", r[2])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(mhz) if mhz else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- profiles
+def profile_traffic(kernel_tag):
+    """Per-launch DRAM bytes of the dominant kernel from the committed ncu
+    summary, or None when the kernel source changed since that capture."""
+    path = os.path.join(ROOT, "profiles", "sweep_fp32_tgv.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"traffic_bytes_per_full_launch:\s*([0-9.eE+]+)", txt)
+    h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", txt)
+    if not m or not h or h.group(1) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+def kernel_source_hash():
+    d = os.path.join(ROOT, "paper_1810_07806_gb300", "csrc")
+    sha = hashlib.sha256()
+    for f in ("wcns_device.cuh", "wcns_sweep.cuh", "sweep_fp32.cu"):
+        sha.update(open(os.path.join(d, f), "rb").read())
+    return sha.hexdigest()[:16]
+
+
+# ---------------------------------------------------------------- CPU oracle baseline
+def cpu_oracle_rate(pb, budget_s=12.0):
+    """The FP64 oracle as it stands, on whole grid lines of the same state:
+    grows the sampled fraction of lines until about budget_s of CPU work."""
+    import numpy as np
+    from oracle import oracle as O
+    cfg = O.make_cfg(ndim=pb.ndim, n=pb.n, h=pb.h, periodic=pb.periodic, gamma=pb.gamma)
+    U = pb.U0
+    L = np.zeros_like(U)
+    lines = [pb.cells // pb.n[d] for d in range(pb.ndim)]
+    frac = min(1.0, 2000.0 / max(lines))
+    total_t = 0.0
+    total_cells = 0.0
+    while True:
+        t0 = time.perf_counter()
+        cells = 0.0
+        for d in range(pb.ndim):
+            k = max(1, int(lines[d] * frac))
+            O.euler_rhs_lines(cfg, U, L, d, 0, k)
+            cells += k * pb.n[d] / pb.ndim   # a cell-update = all ndim directions
+        dt = time.perf_counter() - t0
+        total_t += dt
+        total_cells += cells
+        if total_t >= budget_s or frac >= 1.0:
+            break
+        frac = min(1.0, frac * max(2.0, (budget_s - total_t) / max(dt, 1e-3) * 0.9))
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return total_cells / total_t, cores, total_t, total_cells
+
+
+# ---------------------------------------------------------------- main arms
+def dist_setup():
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    return world, rank, local
+
+
+def reference_arm(args, world, rank):
+    """The oracle (plain FP64 CPU code) timed on this host's cores on the same
+    workload; each step a bounded sample of grid lines."""
+    pb, cfg, _ = workload(args.workload)
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle import oracle as O
+    ocfg = O.make_cfg(ndim=pb.ndim, n=pb.n, h=pb.h, periodic=pb.periodic, gamma=pb.gamma)
+    L = np.zeros_like(pb.U0)
+    lines = [pb.cells // pb.n[d] for d in range(pb.ndim)]
+    per_step_budget = max(0.2, 150.0 / max(1, args.steps + args.warmup))
+    # calibrate the fraction of lines per step
+    frac = min(1.0, 512.0 / max(lines))
+    t0 = time.perf_counter()
+    for d in range(pb.ndim):
+        O.euler_rhs_lines(ocfg, pb.U0, L, d, 0, max(1, int(lines[d] * frac)))
+    t1 = time.perf_counter() - t0
+    frac = min(1.0, frac * per_step_budget / max(t1, 1e-4))
+    ks = [max(1, int(lines[d] * frac)) for d in range(pb.ndim)]
+    cells_per_step = sum(ks[d] * pb.n[d] for d in range(pb.ndim)) / pb.ndim
+    for _ in range(args.warmup):
+        for d in range(pb.ndim):
+            O.euler_rhs_lines(ocfg, pb.U0, L, d, 0, ks[d])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for d in range(pb.ndim):
+            O.euler_rhs_lines(ocfg, pb.U0, L, d, 0, ks[d])
+    el = time.perf_counter() - t0
+    value = cells_per_step * args.steps / el
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = "%s: first %s grid lines per direction per step (%.3g cell-updates/step), FP64 oracle" % (
+        cfg["workload"], "/".join(str(k) for k in ks), cells_per_step)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": dict(cfg, precision="fp64 (CPU oracle)"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def time_steps(torch, solver, U, steps):
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(steps):
+        solver.step(U)
+    ev1.record()
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / 1e3
+
+
+def ours_arm(args, world, rank, local):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1810_07806_gb300 import wcns
+
+    torch.cuda.set_device(local)
+    pb, cfg, fp32 = workload(args.workload)
+    dev = torch.device("cuda", local)
+    solver = wcns.Solver.for_problem(pb, precision=wcns.FP32 if fp32 else wcns.FP64, cfl=0.5)
+    U = torch.from_numpy(pb.U0).to(dev)
+    nodes = pb.cells
+    for _ in range(args.warmup):
+        solver.step(U)
+    torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    time.sleep(0.3)
+    solver.profile(True)
+    if world > 1:
+        dist.barrier()
+    el = time_steps(torch, solver, U, args.steps)
+    if world > 1:
+        dist.barrier()
+    sweep_ms, sweep_n = solver.profile_read()
+    solver.profile(False)
+    clk = clocks.stop()
+
+    t = torch.tensor([el], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    el = float(t.item())
+    evals = 3 * args.steps
+    value = nodes * evals * world / el
+
+    # dominant kernel: the fused sweep (all directions)
+    nd = pb.ndim
+    avg_ms = sweep_ms / max(1, sweep_n)
+    flops_launch = nodes * (FACE_FLOPS[nd] * (1.0 + 5.0 / 59.0) + NODE_FLOPS[nd])
+    achieved_tflops = flops_launch / (avg_ms / 1e3) / 1e12
+    peak = FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS
+    traffic = profile_traffic("sweep") if fp32 else None
+    w = 4 if fp32 else 8
+    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved_tflops / peak, "traffic": traffic,
+                "kernel": "sweep_kernel (fused interpolation+flux+MD, one direction)",
+                "peak_source": "derived: 152 SMs x %s x 2 x 2070 MHz" % ("128 FP32 lanes" if fp32 else "2 FP64 FMA/clk"),
+                "avg_launch_ms": avg_ms, "launches": sweep_n,
+                "hbm": {"algorithmic_bytes_per_launch": nodes * pb.nv * w * 2,
+                        "achieved_gbs": nodes * pb.nv * w * 2 / (avg_ms / 1e3) / 1e9,
+                        "peak_gbs": 6782.1, "frac": nodes * pb.nv * w * 2 / (avg_ms / 1e3) / 1e9 / 6782.1}}
+
+    # e2e: public API with host buffers, copies inside the timed region
+    Uh = torch.from_numpy(pb.U0.copy()).pin_memory()
+    e2e_steps = max(1, min(args.steps, 10))
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(e2e_steps):
+        U.copy_(Uh, non_blocking=True)
+        solver.step(U)
+        Uh.copy_(U, non_blocking=True)
+    ev1.record()
+    torch.cuda.synchronize()
+    e2e_el = ev0.elapsed_time(ev1) / 1e3
+    et = torch.tensor([e2e_el], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(et, op=dist.ReduceOp.MAX)
+    e2e_el = float(et.item())
+    nbytes = U.numel() * U.element_size()
+    e2e = {"value": nodes * 3 * e2e_steps * world / e2e_el, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes, "steps": e2e_steps}
+
+    # the FP64 plain path on the same workload
+    fp64_line = None
+    if fp32 and not args.no_fp64:
+        s64 = wcns.Solver.for_problem(pb, precision=wcns.FP64, cfl=0.5)
+        U64 = torch.from_numpy(pb.U0).to(dev)
+        s64.step(U64)
+        k64 = max(1, min(3, args.steps))
+        el64 = time_steps(torch, s64, U64, k64)
+        fp64_line = {"value": nodes * 3 * k64 / el64, "unit": UNIT, "ms_per_step": el64 / k64 * 1e3,
+                     "steps": k64, "dtype": "f64"}
+        del U64
+        s64.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, cores, secs, cells = cpu_oracle_rate(pb)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%s: %.3g cell-updates as whole grid lines of every direction, %.1f s" % (
+                   cfg["workload"], cells, secs)}
+
+    launches = solver.launches_per_step(True) * args.steps
+    if rank == 0:
+        cfg.update({"global_batch": world, "parallelism": "replicas x%d" % world,
+                    "l2": "inputs larger than L2 (state %.0f MB)" % (nbytes / 1e6)})
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp32 else "f64",
+            "data": "synthetic", "config": cfg, "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": e2e, "gpu_launches": launches, "clocks": clk, "fp64_plain": fp64_line,
+        }))
+    solver.close()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        # the reference arm runs on rank 0's host cores only; other ranks exit
+        rank = int(os.environ.get("RANK", "0"))
+        if rank == 0:
+            reference_arm(args, int(os.environ.get("WORLD_SIZE", "1")), 0)
+        return
+    world, rank, local = dist_setup()
+    if True:
+        ours_arm(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -139,6 +139,18 @@ wcns_status wcns_cfl_dt(wcns_handle* h, const void* U, double* dt, void* stream)
  * (synchronises the stream). */
 wcns_status wcns_fallback_count(wcns_handle* h, long long* count, int reset, void* stream);
 
+/* Kernel timing for measurement (no counterpart in the paper).  While
+ * enabled, every sweep launch of this handle is bracketed by a pair of CUDA
+ * events recorded on the launch stream.  wcns_profile_read synchronises
+ * those events and returns the summed duration (ms) and the number of sweep
+ * launches since the last read, then clears them.  Enabling costs two
+ * event records per sweep; disabled by default. */
+wcns_status wcns_profile(wcns_handle* h, int enable);
+wcns_status wcns_profile_read(wcns_handle* h, double* sweep_ms, long long* sweep_launches);
+
+/* Number of kernel launches one wcns_step_rk3 call issues (for accounting). */
+int wcns_launches_per_step(const wcns_handle* h, int cfl_step);
+
 #ifdef __cplusplus
 }
 #endif

@@ -50,6 +50,8 @@ def lib():
         L.ora_euler_rhs.argtypes = [C.POINTER(OraCfg), _dp, _dp, _u8p, _dp, _dp]
         L.ora_euler_rhs_at.restype = C.c_long
         L.ora_euler_rhs_at.argtypes = [C.POINTER(OraCfg), _dp, C.c_long, C.POINTER(C.c_long), _dp]
+        L.ora_euler_rhs_lines.restype = C.c_long
+        L.ora_euler_rhs_lines.argtypes = [C.POINTER(OraCfg), _dp, _dp, C.c_int, C.c_long, C.c_long]
         L.ora_cfl_dt.restype = C.c_double
         L.ora_cfl_dt.argtypes = [C.POINTER(OraCfg), _dp, C.c_double]
         L.ora_rk3_step.restype = C.c_long
@@ -173,6 +175,11 @@ def euler_rhs_at(cfg, U, idx):
     out = np.zeros((cfg.ndim + 2, idx.size))
     lib().ora_euler_rhs_at(C.byref(cfg), _p(U), idx.size, idx.ctypes.data_as(C.POINTER(C.c_long)), _p(out))
     return out
+
+
+def euler_rhs_lines(cfg, U, L, d, line_lo, line_hi):
+    """Add direction-d contributions of lines [line_lo, line_hi) into L (in place)."""
+    return lib().ora_euler_rhs_lines(C.byref(cfg), _p(U), _p(L), d, line_lo, line_hi)
 
 
 def cfl_dt(cfg, U, cfl):

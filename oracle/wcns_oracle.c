@@ -549,6 +549,25 @@ long ora_euler_rhs(const ora_cfg* cfg, const double* U, double* L, uint8_t* flag
     return nonphys;
 }
 
+/* Direction-d contributions of a range of grid lines only (a bounded sample
+ * of the full RHS: the full RHS is the sum over every line of every
+ * direction).  Adds into L; returns fallback faces. */
+long ora_euler_rhs_lines(const ora_cfg* cfg, const double* U, double* L, int d, long line_lo,
+                         long line_hi)
+{
+    const long N = n_nodes(cfg);
+    const long stride = axis_stride(cfg, d);
+    long nonphys = 0;
+    #pragma omp parallel for schedule(static) reduction(+ : nonphys)
+    for (long ln = line_lo; ln < line_hi; ++ln) {
+        ora_stats st = {0, 0.0};
+        long base = line_base(cfg, d, ln);
+        euler_line(cfg, d, U + base, stride, N, L + base, NULL, NULL, 0, &st);
+        nonphys += st.nonphys;
+    }
+    return nonphys;
+}
+
 /* The RHS at selected nodes only (same arithmetic as ora_euler_rhs): for
  * each node index idx[p] (flattened x-fastest), L_out[v * npts + p]. */
 long ora_euler_rhs_at(const ora_cfg* cfg, const double* U, long npts, const long* idx,

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/wcns.h"
 #include "wcns_internal.h"
@@ -31,6 +32,10 @@ struct wcns_handle {
     double* partials = nullptr;
     int nblk_cons = 0;
     size_t bytes = 0;
+    // optional sweep timing
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev;    // pairs (start, end)
+    size_t ev_used = 0;             // events recorded since the last read
 };
 
 static thread_local std::string g_err;
@@ -195,6 +200,7 @@ wcns_status wcns_create(const wcns_grid* g, double gamma, const wcns_scheme_para
 wcns_status wcns_destroy(wcns_handle* h)
 {
     if (!h) return WCNS_OK;
+    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     cudaError_t e = cudaFree(h->L);
     delete h;
     if (e != cudaSuccess) return cuda_fail(e, "cudaFree");
@@ -219,6 +225,17 @@ static size_t flags_offset(const wcns_handle* h, int d)
 }
 
 // Evaluate L = RHS(U) with all directions; U is LT, L is the handle precision.
+static cudaError_t timed_event(wcns_handle* h, cudaStream_t s)
+{
+    if (h->ev_used == h->ev.size()) {
+        cudaEvent_t e;
+        cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) return r;
+        h->ev.push_back(e);
+    }
+    return cudaEventRecord(h->ev[h->ev_used++], s);
+}
+
 static cudaError_t run_rhs(wcns_handle* h, const void* U, bool u_fp64, void* L, uint8_t* flags,
                            const double* dtp, cudaStream_t s)
 {
@@ -239,9 +256,12 @@ static cudaError_t run_rhs(wcns_handle* h, const void* U, bool u_fp64, void* L, 
         a.dt = dtp;
         a.K = h->K;
         a.sqrt_eps_f = h->sqrt_eps_f;
-        cudaError_t e = fp32 ? launch_sweep_fp32(h->ndim, d, h->p.flux, u_fp64, a, s)
-                             : launch_sweep_fp64(h->ndim, d, h->p.flux, a, s);
+        cudaError_t e;
+        if (h->profiling && (e = timed_event(h, s)) != cudaSuccess) return e;
+        e = fp32 ? launch_sweep_fp32(h->ndim, d, h->p.flux, u_fp64, a, s)
+                 : launch_sweep_fp64(h->ndim, d, h->p.flux, a, s);
         if (e != cudaSuccess) return e;
+        if (h->profiling && (e = timed_event(h, s)) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
@@ -295,7 +315,7 @@ wcns_status wcns_step_rk3(wcns_handle* h, void* U, double dt, double* dt_used, v
     CK(cudaGetLastError(), "pending CUDA error");
     CK(reset_clock(h, INFINITY, s), "reset clock");
     if (dt > 0.0) CK(launch_set_dt(dt, 0, h->sc, s), "set dt");
-    else CK(launch_cfl(h->ndim, (const double*)U, h->N, h->inv_h, h->gamma, h->p.cfl, 0, h->sc, s), "cfl");
+    else CK(launch_cfl(h->ndim, (const double*)U, h->N, h->h, h->gamma, h->p.cfl, 0, h->sc, s), "cfl");
     CK(run_stages(h, (double*)U, s), "rk3 stages");
     if (dt_used) {
         CK(cudaMemcpyAsync(dt_used, &h->sc->dt, sizeof(double), cudaMemcpyDeviceToHost, s), "dt copy");
@@ -320,7 +340,7 @@ wcns_status wcns_advance(wcns_handle* h, void* U, double t_end, int max_steps, i
         const long long left = max_steps - issued;
         const int batch = left < check ? (int)left : check;
         for (int k = 0; k < batch; ++k) {
-            CK(launch_cfl(h->ndim, (const double*)U, h->N, h->inv_h, h->gamma, h->p.cfl, 1, h->sc, s), "cfl");
+            CK(launch_cfl(h->ndim, (const double*)U, h->N, h->h, h->gamma, h->p.cfl, 1, h->sc, s), "cfl");
             CK(run_stages(h, (double*)U, s), "rk3 stages");
         }
         issued += batch;
@@ -353,7 +373,7 @@ wcns_status wcns_cfl_dt(wcns_handle* h, const void* U, double* dt, void* stream)
     if (!h || !U || !dt) return fail(WCNS_ERR_INVALID, "wcns_cfl_dt: null argument");
     cudaStream_t s = (cudaStream_t)stream;
     CK(reset_clock(h, INFINITY, s), "reset clock");
-    CK(launch_cfl(h->ndim, (const double*)U, h->N, h->inv_h, h->gamma, h->p.cfl, 0, h->sc, s), "cfl");
+    CK(launch_cfl(h->ndim, (const double*)U, h->N, h->h, h->gamma, h->p.cfl, 0, h->sc, s), "cfl");
     CK(cudaMemcpyAsync(dt, &h->sc->dt, sizeof(double), cudaMemcpyDeviceToHost, s), "dt copy");
     CK(cudaStreamSynchronize(s), "sync");
     return WCNS_OK;
@@ -368,6 +388,38 @@ wcns_status wcns_fallback_count(wcns_handle* h, long long* count, int reset, voi
     if (reset) CK(cudaMemsetAsync(h->fallback, 0, sizeof(long long), s), "reset");
     CK(cudaStreamSynchronize(s), "sync");
     return WCNS_OK;
+}
+
+wcns_status wcns_profile(wcns_handle* h, int enable)
+{
+    g_err.clear();
+    if (!h) return fail(WCNS_ERR_INVALID, "wcns_profile: null handle");
+    h->profiling = enable != 0;
+    return WCNS_OK;
+}
+
+wcns_status wcns_profile_read(wcns_handle* h, double* sweep_ms, long long* sweep_launches)
+{
+    g_err.clear();
+    if (!h || !sweep_ms || !sweep_launches) return fail(WCNS_ERR_INVALID, "wcns_profile_read: null argument");
+    double tot = 0.0;
+    for (size_t i = 0; i + 1 < h->ev_used; i += 2) {
+        CK(cudaEventSynchronize(h->ev[i + 1]), "event sync");
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]), "event time");
+        tot += ms;
+    }
+    *sweep_ms = tot;
+    *sweep_launches = (long long)(h->ev_used / 2);
+    h->ev_used = 0;
+    return WCNS_OK;
+}
+
+int wcns_launches_per_step(const wcns_handle* h, int cfl_step)
+{
+    if (!h) return 0;
+    // clock reset + (CFL reduction and finalize | set dt) + 3 x (sweeps + stage combine)
+    return 1 + (cfl_step ? 2 : 1) + 3 * (h->ndim + 1);
 }
 
 }  // extern "C"

@@ -49,154 +49,21 @@ struct SchemeConst {
     float Cf, CTf, Kf;
 };
 
-// ------------------------------------------------------------------------
-// Exact-order FP64 arithmetic for the parts that decide the stencil flags.
-// These replay one fixed evaluation order with no FMA contraction, so the
-// flags are a deterministic function of the node values.
-// ------------------------------------------------------------------------
-__device__ __forceinline__ double mul_(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ double add_(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ double sub_(double a, double b) { return __dadd_rn(a, -b); }
-__device__ __forceinline__ double div_(double a, double b) { return __ddiv_rn(a, b); }
-
-// p = (gamma-1) (E - (0.5 * sum m_a^2) / rho), sum taken in axis order.
-template <int ND>
-__device__ __forceinline__ double pressure_exact(const double* U, double gm1)
-{
-    double ke = mul_(U[1], U[1]);
-#pragma unroll
-    for (int a = 1; a < ND; ++a) ke = add_(ke, mul_(U[1 + a], U[1 + a]));
-    ke = div_(mul_(0.5, ke), U[0]);
-    return mul_(gm1, sub_(U[ND + 1], ke));
-}
-
-// Roe-averaged left eigenvectors of dF_d/dU between nodes a and b, in the
-// form needed for projection.  Field order: (u_n - c, entropy, shear waves
-// of the tangential axes in axis order, u_n + c).
-template <int ND>
-struct ProjFP64 {
-    double vel[ND];
-    double q2, H, c, un;
-    double l0[ND + 2];   // row of u_n - c
-    double l1[ND + 2];   // entropy row
-    double lN[ND + 2];   // row of u_n + c
-};
-
-template <int ND, int D>
-__device__ __forceinline__ void proj_setup_fp64(const double* Ua, const double* Ub, double gm1,
-                                                ProjFP64<ND>& P)
-{
-    const double ra = __dsqrt_rn(Ua[0]);
-    const double rb = __dsqrt_rn(Ub[0]);
-    const double Ha = div_(add_(Ua[ND + 1], pressure_exact<ND>(Ua, gm1)), Ua[0]);
-    const double Hb = div_(add_(Ub[ND + 1], pressure_exact<ND>(Ub, gm1)), Ub[0]);
-    const double den = add_(ra, rb);
-    double q2 = 0.0;
-#pragma unroll
-    for (int a = 0; a < ND; ++a) {
-        P.vel[a] = div_(add_(mul_(ra, div_(Ua[1 + a], Ua[0])), mul_(rb, div_(Ub[1 + a], Ub[0]))), den);
-        q2 = (a == 0) ? mul_(P.vel[0], P.vel[0]) : add_(q2, mul_(P.vel[a], P.vel[a]));
-    }
-    P.q2 = q2;
-    P.H = div_(add_(mul_(ra, Ha), mul_(rb, Hb)), den);
-    const double c2 = mul_(gm1, sub_(P.H, mul_(0.5, q2)));
-    P.c = __dsqrt_rn(c2);
-    P.un = P.vel[D];
-    const double b1 = div_(gm1, c2);
-    const double b2 = mul_(mul_(0.5, b1), q2);
-    const double unc = div_(P.un, P.c);
-    const double ic = div_(1.0, P.c);
-    P.l0[0] = mul_(0.5, add_(b2, unc));
-    P.lN[0] = mul_(0.5, sub_(b2, unc));
-    P.l1[0] = sub_(1.0, b2);
-#pragma unroll
-    for (int a = 0; a < ND; ++a) {
-        const double t = mul_(-b1, P.vel[a]);
-        P.l0[1 + a] = mul_(0.5, a == D ? sub_(t, ic) : t);
-        P.lN[1 + a] = mul_(0.5, a == D ? add_(t, ic) : t);
-        P.l1[1 + a] = mul_(b1, P.vel[a]);
-    }
-    P.l0[ND + 1] = mul_(0.5, b1);
-    P.lN[ND + 1] = mul_(0.5, b1);
-    P.l1[ND + 1] = -b1;
-}
-
-// Characteristic variables of one node, left-to-right sums.
-template <int ND, int D>
-__device__ __forceinline__ void project_fp64(const ProjFP64<ND>& P, const double* U, double* W)
-{
-    double s0 = mul_(P.l0[0], U[0]), s1 = mul_(P.l1[0], U[0]), sN = mul_(P.lN[0], U[0]);
-#pragma unroll
-    for (int v = 1; v < ND + 2; ++v) {
-        s0 = add_(s0, mul_(P.l0[v], U[v]));
-        s1 = add_(s1, mul_(P.l1[v], U[v]));
-        sN = add_(sN, mul_(P.lN[v], U[v]));
-    }
-    W[0] = s0;
-    W[1] = s1;
-    int k = 2;
-#pragma unroll
-    for (int t = 0; t < ND; ++t) {
-        if (t == D) continue;
-        W[k++] = add_(mul_(-P.vel[t], U[0]), U[1 + t]);
-    }
-    W[ND + 1] = sN;
-}
-
-// Eq. 10, 11, 15 and 16-18 on one stencil s[0..4] = u_{i-2} .. u_{i+2},
-// in one fixed order; chi_k is evaluated as s_k / sum s with
-// s_k = (g_k / max g)^q, which equals Eq. 17 and cannot overflow.
-__device__ __forceinline__ int select_fp64(const double s[5], const SchemeConst& K)
-{
-    double D1[3], D2[3], beta[3];
-    D1[0] = mul_(0.5, add_(sub_(s[0], mul_(4.0, s[1])), mul_(3.0, s[2])));
-    D1[1] = mul_(0.5, sub_(s[3], s[1]));
-    D1[2] = mul_(0.5, sub_(add_(mul_(-3.0, s[2]), mul_(4.0, s[3])), s[4]));
-    D2[0] = add_(sub_(s[0], mul_(2.0, s[1])), s[2]);
-    D2[1] = add_(sub_(s[1], mul_(2.0, s[2])), s[3]);
-    D2[2] = add_(sub_(s[2], mul_(2.0, s[3])), s[4]);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) beta[k] = add_(mul_(D1[k], D1[k]), mul_(D2[k], D2[k]));
-    const double tau = fabs(sub_(beta[0], beta[2]));
-    // No stencil can be cut unless the largest gamma exceeds the smallest by
-    // the factor (3 C_T)^(-1/q); this bound (with a 2% margin) lets smooth
-    // stencils skip the divisions while deciding exactly as the full test.
-    const double bmin = fmin(fmin(beta[0], beta[1]), beta[2]) + K.eps;
-    if (tau < K.keep_all_K * bmin) return 7;
-    double g[3], gmax = 0.0;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        g[k] = add_(K.C, div_(tau, add_(beta[k], K.eps)));
-        if (g[k] > gmax) gmax = g[k];
-    }
-    double sk[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const double r = div_(g[k], gmax);
-        double p = r;
-        for (int e = 1; e < K.q; ++e) p = mul_(p, r);
-        sk[k] = p;
-    }
-    const double ssum = add_(add_(sk[0], sk[1]), sk[2]);
-    int flags = 0;
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-        if (!(div_(sk[k], ssum) < K.CT)) flags |= 1 << k;
-    return flags;
-}
-
 // FP32 selection.  chi_k is invariant under s -> s/sc except through eps, so
 // the stencil is rescaled by sc = max |s_m| (beta, tau become O(1) and cannot
-// underflow), eps becomes max(eps/sc^2, FLT_MIN), tau = 0 keeps every stencil
-// without dividing, and the cutoff chi_k < C_T is tested as
-// s_k < C_T * sum s with s_k = (g_k / max g)^q.
+// underflow) and eps becomes max(eps/sc^2, FLT_MIN).  With b_k = beta_k + eps
+// and m = argmin b (the largest gamma), the ratio g_k / g_m is formed as
+//   (b_m / b_k) * (C b_k + tau) / (C b_m + tau),
+// where every factor is bounded (the literal tau / b_k overflows FP32 when b_k
+// sits at the eps floor), and chi_k < C_T is tested as s_k < C_T sum s with
+// s_k = (g_k / g_m)^q.  tau = 0 keeps every stencil without dividing.
 __device__ __forceinline__ int select_fp32(const float s[5], float inv_sc, float eps_s,
                                            const SchemeConst& K)
 {
     float t[5];
 #pragma unroll
     for (int m = 0; m < 5; ++m) t[m] = s[m] * inv_sc;
-    float D1[3], D2[3], beta[3];
+    float D1[3], D2[3], b[3];
     D1[0] = 0.5f * (t[0] - 4.0f * t[1] + 3.0f * t[2]);
     D1[1] = 0.5f * (t[3] - t[1]);
     D1[2] = 0.5f * (-3.0f * t[2] + 4.0f * t[3] - t[4]);
@@ -204,19 +71,17 @@ __device__ __forceinline__ int select_fp32(const float s[5], float inv_sc, float
     D2[1] = t[1] - 2.0f * t[2] + t[3];
     D2[2] = t[2] - 2.0f * t[3] + t[4];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) beta[k] = D1[k] * D1[k] + D2[k] * D2[k];
-    const float tau = fabsf(beta[0] - beta[2]);
-    const float bmin = fminf(fminf(beta[0], beta[1]), beta[2]) + eps_s;
-    if (!(tau >= K.Kf * bmin)) return 7;           // also catches tau == 0
-    float g[3];
+    for (int k = 0; k < 3; ++k) b[k] = D1[k] * D1[k] + D2[k] * D2[k];
+    const float tau = fabsf(b[0] - b[2]);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) g[k] = K.Cf + tau * __frcp_rn(beta[k] + eps_s);
-    const float gmax = fmaxf(fmaxf(g[0], g[1]), g[2]);
-    const float ig = __frcp_rn(gmax);
+    for (int k = 0; k < 3; ++k) b[k] += eps_s;
+    const float bm = fminf(fminf(b[0], b[1]), b[2]);
+    if (!(tau >= K.Kf * bm)) return 7;           // no cut possible (also tau == 0)
+    const float den = __frcp_rn(fmaf(K.Cf, bm, tau));
     float sk[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const float r = g[k] * ig;
+        const float r = fminf(1.0f, (bm * __frcp_rn(b[k])) * (fmaf(K.Cf, b[k], tau) * den));
         float p = r;
         for (int e = 1; e < K.q; ++e) p *= r;
         sk[k] = p;

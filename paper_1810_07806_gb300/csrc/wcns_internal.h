@@ -23,7 +23,7 @@ struct StepScalars {      // device-resident
     unsigned long long steps;      // steps that advanced time since the last reset
 };
 
-cudaError_t launch_cfl(int nd, const double* U, long long N, const double* inv_h, double gamma,
+cudaError_t launch_cfl(int nd, const double* U, long long N, const double* h, double gamma,
                        double cfl, int clip, StepScalars* sc, cudaStream_t s);
 cudaError_t launch_set_dt(double dt, int clip, StepScalars* sc, cudaStream_t s);
 cudaError_t launch_reset_clock(double t_end, StepScalars* sc, cudaStream_t s);

@@ -4,6 +4,7 @@
 // deterministic FP64 conservation totals.
 #include <math.h>
 
+#include "wcns_fp64.cuh"
 #include "wcns_internal.h"
 
 namespace wcns {
@@ -26,31 +27,27 @@ __device__ __forceinline__ double warp_sum(double x)
     return x;
 }
 
-// lambda = max_i sum_d (|u_d| + c) / h_d over all nodes, FP64.
+// lambda = max_i sum_d (|u_d| + c) / h_d over all nodes, FP64, each node in
+// the fixed order c = sqrt(gamma p / rho), s = sum_d (|m_d / rho| + c) / h_d.
 template <int ND>
 __global__ void __launch_bounds__(256) cfl_reduce_kernel(const double* __restrict__ U, long long N,
-                                                         InvH ih, double gamma,
+                                                         InvH hh, double gamma, double gm1,
                                                          StepScalars* sc, int clip)
 {
-    if (clip && sc->t >= sc->t_end) return;   // finished: nothing to do
+    if (clip && !(sc->t < sc->t_end)) return;   // finished: nothing to do
     double m = 0.0;
-    const double gm1 = gamma - 1.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
          i += (long long)gridDim.x * blockDim.x) {
-        const double rho = U[i];
-        const double ir = 1.0 / rho;
-        double m2 = 0.0, s = 0.0;
-        double vel[ND];
+        double Ui[ND + 2];
+#pragma unroll
+        for (int v = 0; v < ND + 2; ++v) Ui[v] = U[v * N + i];
+        const double c = __dsqrt_rn(div_(mul_(gamma, pressure_exact<ND>(Ui, gm1)), Ui[0]));
+        double s = 0.0;
 #pragma unroll
         for (int a = 0; a < ND; ++a) {
-            const double mv = U[(1 + a) * N + i];
-            m2 = fma(mv, mv, m2);
-            vel[a] = fabs(mv * ir);
+            const double q = div_(add_(fabs(div_(Ui[1 + a], Ui[0])), c), hh.v[a]);
+            s = a == 0 ? q : add_(s, q);
         }
-        const double p = gm1 * (U[(ND + 1) * N + i] - 0.5 * m2 * ir);
-        const double c = sqrt(gamma * p * ir);
-#pragma unroll
-        for (int a = 0; a < ND; ++a) s = fma(vel[a] + c, ih.v[a], s);
         m = fmax(m, s);
     }
     m = warp_max(m);
@@ -71,14 +68,10 @@ __global__ void cfl_finalize_kernel(StepScalars* sc, double cfl, int clip)
     const double t = sc->t;
     const double lam = __longlong_as_double((long long)sc->lam_bits);
     sc->lam_bits = 0ull;   // ready for the next reduction
-    if (clip && t >= sc->t_end) { sc->dt = 0.0; return; }
-    double dt = cfl / lam;
-    if (clip && t + dt > sc->t_end) {
-        dt = sc->t_end - t;
-        sc->t = sc->t_end;
-    } else {
-        sc->t = t + dt;
-    }
+    if (clip && !(t < sc->t_end)) { sc->dt = 0.0; return; }
+    double dt = div_(cfl, lam);
+    if (clip && add_(t, dt) > sc->t_end) dt = sub_(sc->t_end, t);
+    sc->t = add_(t, dt);
     sc->dt = dt;
     sc->steps += 1ull;
 }
@@ -86,9 +79,9 @@ __global__ void cfl_finalize_kernel(StepScalars* sc, double cfl, int clip)
 __global__ void set_dt_kernel(StepScalars* sc, double dt, int clip)
 {
     const double t = sc->t;
-    if (clip && t >= sc->t_end) { sc->dt = 0.0; return; }
-    if (clip && t + dt > sc->t_end) { dt = sc->t_end - t; sc->t = sc->t_end; }
-    else sc->t = t + dt;
+    if (clip && !(t < sc->t_end)) { sc->dt = 0.0; return; }
+    if (clip && add_(t, dt) > sc->t_end) dt = sub_(sc->t_end, t);
+    sc->t = add_(t, dt);
     sc->dt = dt;
     sc->steps += 1ull;
 }
@@ -114,14 +107,15 @@ static int reduce_blocks(long long N)
     return (int)(b < 1216 ? (b < 1 ? 1 : b) : 1216);
 }
 
-cudaError_t launch_cfl(int nd, const double* U, long long N, const double* inv_h, double gamma,
+cudaError_t launch_cfl(int nd, const double* U, long long N, const double* h, double gamma,
                        double cfl, int clip, StepScalars* sc, cudaStream_t s)
 {
-    InvH ih{{inv_h[0], inv_h[1], inv_h[2]}};
+    InvH hh{{h[0], h[1], h[2]}};
+    const double gm1 = gamma - 1.0;
     const int nb = reduce_blocks(N);
-    if (nd == 1) cfl_reduce_kernel<1><<<nb, 256, 0, s>>>(U, N, ih, gamma, sc, clip);
-    else if (nd == 2) cfl_reduce_kernel<2><<<nb, 256, 0, s>>>(U, N, ih, gamma, sc, clip);
-    else cfl_reduce_kernel<3><<<nb, 256, 0, s>>>(U, N, ih, gamma, sc, clip);
+    if (nd == 1) cfl_reduce_kernel<1><<<nb, 256, 0, s>>>(U, N, hh, gamma, gm1, sc, clip);
+    else if (nd == 2) cfl_reduce_kernel<2><<<nb, 256, 0, s>>>(U, N, hh, gamma, gm1, sc, clip);
+    else cfl_reduce_kernel<3><<<nb, 256, 0, s>>>(U, N, hh, gamma, gm1, sc, clip);
     cfl_finalize_kernel<<<1, 1, 0, s>>>(sc, cfl, clip);
     return cudaGetLastError();
 }
@@ -133,7 +127,8 @@ cudaError_t launch_set_dt(double dt, int clip, StepScalars* sc, cudaStream_t s)
 }
 
 // ---------------------------------------------------------------- FP64 stages
-// U1 = U0 + dt L;  U1 = 3/4 U0 + 1/4 (U1 + dt L);  U0 = 1/3 U0 + 2/3 (U1 + dt L)
+// U1 = U0 + dt L;  U1 = 3/4 U0 + 1/4 (U1 + dt L);  U0 = U0 / 3 + 2/3 (U1 + dt L),
+// each sum and product rounded as written.
 template <int STAGE>
 __global__ void __launch_bounds__(256) rk_fp64_kernel(double* __restrict__ U0, double* __restrict__ U1,
                                                       const double* __restrict__ L, long long M,
@@ -145,11 +140,11 @@ __global__ void __launch_bounds__(256) rk_fp64_kernel(double* __restrict__ U0, d
          i += (long long)gridDim.x * blockDim.x) {
         const double l = L[i];
         if (STAGE == 1) {
-            U1[i] = fma(dt, l, U0[i]);
+            U1[i] = add_(U0[i], mul_(dt, l));
         } else if (STAGE == 2) {
-            U1[i] = fma(0.75, U0[i], 0.25 * fma(dt, l, U1[i]));
+            U1[i] = add_(mul_(0.75, U0[i]), mul_(0.25, add_(U1[i], mul_(dt, l))));
         } else {
-            U0[i] = fma(1.0 / 3.0, U0[i], (2.0 / 3.0) * fma(dt, l, U1[i]));
+            U0[i] = add_(div_(U0[i], 3.0), mul_(2.0 / 3.0, add_(U1[i], mul_(dt, l))));
         }
     }
 }

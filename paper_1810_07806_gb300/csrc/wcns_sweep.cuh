@@ -12,7 +12,7 @@
 //  (3) forms -f'_i by the sixth-order MD difference (Eq. 3) and writes or
 //      accumulates it into L (Eq. 2: the directions are summed).
 #pragma once
-#include "wcns_device.cuh"
+#include "wcns_fp64.cuh"
 
 namespace wcns {
 
@@ -58,76 +58,7 @@ template <int ND, int DIR, int FLUX>
 __device__ __forceinline__ void face_flux(double (&u)[6][ND + 2], const SweepArgs& a, double* F,
                                           uint8_t* fl, bool& fell_back)
 {
-    constexpr int NV = ND + 2;
-    const double gm1 = a.K.gm1;
-    ProjFP64<ND> P;
-    proj_setup_fp64<ND, DIR>(u[2], u[3], gm1, P);
-    double Uj[NV], Uj1[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) { Uj[v] = u[2][v]; Uj1[v] = u[3][v]; }
-#pragma unroll
-    for (int m = 0; m < 6; ++m) {
-        double W[NV];
-        project_fp64<ND, DIR>(P, u[m], W);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) u[m][v] = W[v];
-    }
-    double wL[NV], wR[NV];
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        double sl[5], sr[5];
-#pragma unroll
-        for (int m = 0; m < 5; ++m) { sl[m] = u[m][k]; sr[m] = u[5 - m][k]; }
-        const int fL = select_fp64(sl, a.K);
-        const int fR = select_fp64(sr, a.K);
-        wL[k] = interp_row<double>(fL, sl);
-        wR[k] = interp_row<double>(fR, sr);
-        fl[k] = (uint8_t)(fL | (fR << 3));
-    }
-    // back-projection U = R w
-    double UL[NV], UR[NV];
-    {
-        const double c = P.c, un = P.un;
-        const double rl = wL[0] + wL[1] + wL[NV - 1], rr = wR[0] + wR[1] + wR[NV - 1];
-        const double dl = wL[NV - 1] - wL[0], dr = wR[NV - 1] - wR[0];
-        UL[0] = rl;
-        UR[0] = rr;
-        double el = fma(P.H, wL[0] + wL[NV - 1], fma(un * c, dl, 0.5 * P.q2 * wL[1]));
-        double er = fma(P.H, wR[0] + wR[NV - 1], fma(un * c, dr, 0.5 * P.q2 * wR[1]));
-        int k = 2;
-#pragma unroll
-        for (int t = 0; t < ND; ++t) {
-            if (t == DIR) {
-                UL[1 + t] = fma(P.vel[t], rl, c * dl);
-                UR[1 + t] = fma(P.vel[t], rr, c * dr);
-            } else {
-                UL[1 + t] = fma(P.vel[t], rl, wL[k]);
-                UR[1 + t] = fma(P.vel[t], rr, wR[k]);
-                el = fma(P.vel[t], wL[k], el);
-                er = fma(P.vel[t], wR[k], er);
-                ++k;
-            }
-        }
-        UL[NV - 1] = el;
-        UR[NV - 1] = er;
-    }
-    double pL = pressure_of<ND>(UL, gm1), pR = pressure_of<ND>(UR, gm1);
-    if (!(UL[0] > 0.0) || !(UR[0] > 0.0) || !(pL > 0.0) || !(pR > 0.0)) {
-#pragma unroll
-        for (int v = 0; v < NV; ++v) { UL[v] = Uj[v]; UR[v] = Uj1[v]; }
-        pL = pressure_of<ND>(UL, gm1);
-        pR = pressure_of<ND>(UR, gm1);
-        fell_back = true;
-    }
-    if (FLUX == FLUX_ROE) {
-        roe_flux<ND, DIR>(UL, UR, pL, pR, gm1, F);
-    } else {
-        double Fp[NV], Fm[NV];
-        vanleer_half<ND, DIR>(UL, pL, a.K.gamma, gm1, 1.0, Fp);
-        vanleer_half<ND, DIR>(UR, pR, a.K.gamma, gm1, -1.0, Fm);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) F[v] = Fp[v] + Fm[v];
-    }
+    face_fp64<ND, DIR, FLUX>(u, a.K, F, fl, fell_back);
 }
 
 // ---------------------------------------------------------------- FP32 face
@@ -317,10 +248,12 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a)
         uint8_t fl[NV];
         bool fell = false;
         face_flux<ND, DIR, FLUX>(u, a, F, fl, fell);
-        fb += fell ? 1 : 0;
+        // faces shared with the next tile are owned (counted, flagged) by it
+        const bool owned = f < TS || pos0 + TS >= nd;
+        fb += (fell && owned) ? 1 : 0;
 #pragma unroll
         for (int v = 0; v < NV; ++v) sF[sidx<DIR, TL, NF>(v, l, f)] = F[v];
-        if (a.flags != nullptr && (f < TS || pos0 + TS >= nd)) {
+        if (a.flags != nullptr && owned) {
             const long long lines = N / nd;
             const long long j3 = pos0 + f;   // j + 3
 #pragma unroll
@@ -341,14 +274,18 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a)
         const long long g = base0 + l * lstride + (long long)(pos0 + t) * sd;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-            const T* Fv = sF;
-            const T d1 = Fv[sidx<DIR, TL, NF>(v, l, t + 3)] - Fv[sidx<DIR, TL, NF>(v, l, t + 2)];
-            const T d2 = Fv[sidx<DIR, TL, NF>(v, l, t + 4)] - Fv[sidx<DIR, TL, NF>(v, l, t + 1)];
-            const T d3 = Fv[sidx<DIR, TL, NF>(v, l, t + 5)] - Fv[sidx<DIR, TL, NF>(v, l, t + 0)];
-            const T fp = fma(T(MD_A1), d1, fma(T(MD_A2), d2, T(MD_A3) * d3));
-            const T val = -fp * ih;
-            if (a.accumulate) L[v * N + g] += val;
-            else L[v * N + g] = val;
+            const T f0 = sF[sidx<DIR, TL, NF>(v, l, t + 0)], f1 = sF[sidx<DIR, TL, NF>(v, l, t + 1)];
+            const T f2 = sF[sidx<DIR, TL, NF>(v, l, t + 2)], f3 = sF[sidx<DIR, TL, NF>(v, l, t + 3)];
+            const T f4 = sF[sidx<DIR, TL, NF>(v, l, t + 4)], f5 = sF[sidx<DIR, TL, NF>(v, l, t + 5)];
+            if constexpr (sizeof(T) == 8) {
+                const double q = md_fp64(f0, f1, f2, f3, f4, f5, ih);   // L -= f'
+                L[v * N + g] = a.accumulate ? sub_(L[v * N + g], q) : -q;
+            } else {
+                const T fp = fma(T(MD_A1), f3 - f2, fma(T(MD_A2), f4 - f1, T(MD_A3) * (f5 - f0)));
+                const T val = -fp * ih;
+                if (a.accumulate) L[v * N + g] += val;
+                else L[v * N + g] = val;
+            }
         }
     }
 }

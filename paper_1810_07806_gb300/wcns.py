@@ -62,8 +62,13 @@ def lib():
         L.wcns_conserved.argtypes = [vp, vp, C.POINTER(C.c_double), vp]
         L.wcns_cfl_dt.argtypes = [vp, vp, C.POINTER(C.c_double), vp]
         L.wcns_fallback_count.argtypes = [vp, C.POINTER(C.c_longlong), C.c_int, vp]
+        L.wcns_profile.argtypes = [vp, C.c_int]
+        L.wcns_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
+        L.wcns_launches_per_step.argtypes = [vp, C.c_int]
+        L.wcns_launches_per_step.restype = C.c_int
         for f in ("wcns_create", "wcns_destroy", "wcns_rhs", "wcns_step_rk3", "wcns_advance",
-                  "wcns_conserved", "wcns_cfl_dt", "wcns_fallback_count"):
+                  "wcns_conserved", "wcns_cfl_dt", "wcns_fallback_count", "wcns_profile",
+                  "wcns_profile_read"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -173,3 +178,15 @@ class Solver:
         c = C.c_longlong()
         check(lib().wcns_fallback_count(self.h, C.byref(c), int(reset), _stream(stream)))
         return c.value
+
+    def profile(self, enable=True):
+        check(lib().wcns_profile(self.h, int(enable)))
+
+    def profile_read(self):
+        ms = C.c_double()
+        n = C.c_longlong()
+        check(lib().wcns_profile_read(self.h, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+    def launches_per_step(self, cfl_step=True):
+        return lib().wcns_launches_per_step(self.h, int(cfl_step))

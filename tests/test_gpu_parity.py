@@ -244,6 +244,23 @@ def test_fp32_rhs_close_to_oracle():
     assert rel < 2e-6, rel
 
 
+@pytest.mark.parametrize("name,steps", [("sod400", 0), ("sod400", 60), ("quad67x45", 0),
+                                        ("quad67x45", 12), ("lax157", 40)])
+def test_fp32_rhs_at_discontinuities(name, steps):
+    """FP32 RHS next to shocks and contacts: normwise error of a few 1e-7
+    (the cut decisions agree wherever the stencil is not flat to round-off)."""
+    pb = STATES[name]()
+    cfg = ora_cfg(pb, wcns.FLUX_ROE)
+    U = pb.U0.copy()
+    if steps:
+        O.euler_run(cfg, U, 0.5, 10.0, max_steps=steps)
+    Lo = O.euler_rhs(cfg, U)[0]
+    Lg, _, _ = gpu_rhs(pb, U, fp32=True)
+    S = flux_scale(U, pb).reshape((-1,) + (1,) * pb.ndim)
+    rel = np.max(np.abs(Lg - Lo) / (np.abs(Lo) + S))
+    assert rel < 5e-6, rel
+
+
 def test_fp32_sod_end_state_error_vs_oracle():
     """FP32 interpolation/flux/difference with FP64 accumulation: relative L1
     error of the Sod end state against the FP64 oracle."""
