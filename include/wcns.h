@@ -148,6 +148,29 @@ wcns_status wcns_fallback_count(wcns_handle* h, long long* count, int reset, voi
 wcns_status wcns_profile(wcns_handle* h, int enable);
 wcns_status wcns_profile_read(wcns_handle* h, double* sweep_ms, long long* sweep_launches);
 
+/* One FP64 SSP-RK3 step that allocates no device memory.  The paper has no
+ * counterpart: this serves callers that cannot call cudaMalloc, for example
+ * an application whose device memory is all reserved up front by another
+ * allocator, or a time-critical loop that must make no allocation calls.
+ * It needs no handle: grid, gamma and params are as for wcns_create
+ * (params->precision must be WCNS_FP64), U is the caller's FP64 device
+ * state (nv * N doubles, updated in place) and dt / dt_used are as for
+ * wcns_step_rk3, with the same results.  The stage state and right-hand
+ * side live in one library-owned static device buffer of
+ * WCNS_NOALLOC_SCRATCH_BYTES bytes, which every GPU that loads the library
+ * holds until the process exits; grids needing more than
+ * 2 * nv * N * 8 + 512 bytes of it are rejected with WCNS_ERR_INVALID.
+ * The first call on each device performs a one-time set-up there (the
+ * buffer's device address, kernel attributes, a constant table); make that
+ * first call before any stream capture.  All calls on one device share
+ * its buffer, which keeps the last call's contents: calls on the same
+ * device whose GPU work overlaps (different streams or host threads) race
+ * on it and must be serialised by the caller. */
+#define WCNS_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+wcns_status wcns_step_rk3_noalloc(const wcns_grid* grid, double gamma,
+                                  const wcns_scheme_params* params, void* U, double dt,
+                                  double* dt_used, void* stream);
+
 /* Number of kernel launches one wcns_step_rk3 call issues (for accounting). */
 int wcns_launches_per_step(const wcns_handle* h, int cfl_step);
 

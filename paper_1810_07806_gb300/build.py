@@ -19,7 +19,7 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
 # The FP32 sweep may use approximate division/sqrt and flush denormals; the
 # FP64 units keep IEEE division and square root (always the case for double).
 EXTRA = {"sweep_fp32.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]}
-SOURCES = ["wcns_api.cu", "wcns_rk.cu", "sweep_fp64.cu", "sweep_fp32.cu"]
+SOURCES = ["wcns_api.cu", "wcns_rk.cu", "sweep_fp64.cu", "sweep_fp32.cu", "wcns_noalloc.cu"]
 
 
 def nvcc():

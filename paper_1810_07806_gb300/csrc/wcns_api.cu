@@ -423,3 +423,12 @@ int wcns_launches_per_step(const wcns_handle* h, int cfl_step)
 }
 
 }  // extern "C"
+
+namespace wcns {
+// Message for wcns_last_error() from entry points defined in other files.
+void set_last_error(const char* msg)
+{
+    if (msg) g_err = msg;
+    else g_err.clear();
+}
+}  // namespace wcns

@@ -37,4 +37,7 @@ cudaError_t launch_conserved(int nv, const double* U, long long N, double vol, d
                              int nblocks, cudaStream_t s);
 int conserved_blocks(long long N);
 
+// Sets the thread-local message returned by wcns_last_error().
+void set_last_error(const char* msg);
+
 }  // namespace wcns

@@ -190,3 +190,17 @@ class Solver:
 
     def launches_per_step(self, cfl_step=True):
         return lib().wcns_launches_per_step(self.h, int(cfl_step))
+
+
+def step_rk3_noalloc(grid, gamma, params, U, dt=0.0, want_dt=False, stream=None):
+    """wcns_step_rk3_noalloc: one FP64 RK3 step using the library's static
+    device buffer instead of a handle (for callers that cannot allocate)."""
+    L = lib()
+    fn = L.wcns_step_rk3_noalloc
+    fn.argtypes = [C.POINTER(Grid), C.c_double, C.POINTER(SchemeParams), C.c_void_p, C.c_double,
+                   C.POINTER(C.c_double), C.c_void_p]
+    fn.restype = C.c_int
+    d = C.c_double()
+    check(fn(C.byref(grid), float(gamma), C.byref(params), _ptr(U), float(dt),
+             C.byref(d) if want_dt else None, _stream(stream)))
+    return d.value if want_dt else None
