@@ -1,6 +1,5 @@
 // sweep_fp32.cu -- FP32 instances of the fused sweep (rescaled smoothness
-// indicators).  The input state is either the FP64 base state (first RK
-// stage, rounded on load) or the FP32 stage state.
+// indicators).  The input state is single precision.
 #include "wcns_internal.h"
 
 namespace wcns {
@@ -35,12 +34,8 @@ static cudaError_t dispatch(int nd, int dir, const SweepArgs& a, cudaStream_t s,
     return go<LT, 3, 2, FLUX>(a, s, prep);
 }
 
-cudaError_t launch_sweep_fp32(int nd, int dir, int flux, bool load_fp64, const SweepArgs& a,
-                              cudaStream_t s)
+cudaError_t launch_sweep_fp32(int nd, int dir, int flux, const SweepArgs& a, cudaStream_t s)
 {
-    if (load_fp64)
-        return flux == FLUX_ROE ? dispatch<double, FLUX_ROE>(nd, dir, a, s, false)
-                                : dispatch<double, FLUX_VANLEER>(nd, dir, a, s, false);
     return flux == FLUX_ROE ? dispatch<float, FLUX_ROE>(nd, dir, a, s, false)
                             : dispatch<float, FLUX_VANLEER>(nd, dir, a, s, false);
 }
@@ -50,14 +45,9 @@ cudaError_t prepare_sweeps_fp32()
     SweepArgs a{};
     for (int nd = 1; nd <= 3; ++nd)
         for (int d = 0; d < nd; ++d)
-            for (int f = 0; f < 4; ++f) {
-                cudaError_t e;
-                switch (f) {
-                    case 0: e = dispatch<double, FLUX_ROE>(nd, d, a, 0, true); break;
-                    case 1: e = dispatch<double, FLUX_VANLEER>(nd, d, a, 0, true); break;
-                    case 2: e = dispatch<float, FLUX_ROE>(nd, d, a, 0, true); break;
-                    default: e = dispatch<float, FLUX_VANLEER>(nd, d, a, 0, true); break;
-                }
+            for (int f = 0; f < 2; ++f) {
+                cudaError_t e = f == 0 ? dispatch<float, FLUX_ROE>(nd, d, a, 0, true)
+                                       : dispatch<float, FLUX_VANLEER>(nd, d, a, 0, true);
                 if (e != cudaSuccess) return e;
             }
     return cudaSuccess;

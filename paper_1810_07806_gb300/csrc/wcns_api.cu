@@ -236,7 +236,7 @@ static cudaError_t timed_event(wcns_handle* h, cudaStream_t s)
     return cudaEventRecord(h->ev[h->ev_used++], s);
 }
 
-static cudaError_t run_rhs(wcns_handle* h, const void* U, bool u_fp64, void* L, uint8_t* flags,
+static cudaError_t run_rhs(wcns_handle* h, const void* U, void* L, uint8_t* flags,
                            const double* dtp, cudaStream_t s)
 {
     const bool fp32 = h->p.precision == WCNS_FP32;
@@ -258,7 +258,7 @@ static cudaError_t run_rhs(wcns_handle* h, const void* U, bool u_fp64, void* L, 
         a.sqrt_eps_f = h->sqrt_eps_f;
         cudaError_t e;
         if (h->profiling && (e = timed_event(h, s)) != cudaSuccess) return e;
-        e = fp32 ? launch_sweep_fp32(h->ndim, d, h->p.flux, u_fp64, a, s)
+        e = fp32 ? launch_sweep_fp32(h->ndim, d, h->p.flux, a, s)
                  : launch_sweep_fp64(h->ndim, d, h->p.flux, a, s);
         if (e != cudaSuccess) return e;
         if (h->profiling && (e = timed_event(h, s)) != cudaSuccess) return e;
@@ -271,13 +271,16 @@ wcns_status wcns_rhs(wcns_handle* h, const void* U, void* L, uint8_t* flags, voi
     g_err.clear();
     if (!h || !U || !L) return fail(WCNS_ERR_INVALID, "wcns_rhs: null argument");
     CK(cudaGetLastError(), "pending CUDA error");
-    CK(run_rhs(h, U, h->p.precision == WCNS_FP64, L, flags, nullptr, (cudaStream_t)stream),
+    CK(run_rhs(h, U, L, flags, nullptr, (cudaStream_t)stream),
        "wcns_rhs launch");
     return WCNS_OK;
 }
 
-// The three stages of one step after dt has been placed in h->sc.
-static cudaError_t run_stages(wcns_handle* h, double* U, cudaStream_t s)
+// The three stages of one step after dt has been placed in h->sc.  In FP32
+// mode the first stage reads float(U) from the stage buffer: converted here
+// unless the caller knows the previous step of this handle left it there
+// (s_current, only inside wcns_advance where U is not touched between steps).
+static cudaError_t run_stages(wcns_handle* h, double* U, cudaStream_t s, bool s_current = false)
 {
     const long long M = (long long)h->nv * h->N;
     const double* dtp = &h->sc->dt;
@@ -285,21 +288,32 @@ static cudaError_t run_stages(wcns_handle* h, double* U, cudaStream_t s)
     if (h->p.precision == WCNS_FP64) {
         double* U1 = (double*)h->U1;
         double* L = (double*)h->L;
-        if ((e = run_rhs(h, U, true, L, nullptr, dtp, s)) != cudaSuccess) return e;
+        if ((e = run_rhs(h, U, L, nullptr, dtp, s)) != cudaSuccess) return e;
         if ((e = launch_rk_fp64(1, U, U1, L, M, h->sc, s)) != cudaSuccess) return e;
-        if ((e = run_rhs(h, U1, true, L, nullptr, dtp, s)) != cudaSuccess) return e;
+        if ((e = run_rhs(h, U1, L, nullptr, dtp, s)) != cudaSuccess) return e;
         if ((e = launch_rk_fp64(2, U, U1, L, M, h->sc, s)) != cudaSuccess) return e;
-        if ((e = run_rhs(h, U1, true, L, nullptr, dtp, s)) != cudaSuccess) return e;
+        if ((e = run_rhs(h, U1, L, nullptr, dtp, s)) != cudaSuccess) return e;
         return launch_rk_fp64(3, U, U1, L, M, h->sc, s);
     }
     float* S = (float*)h->U1;
     float* L = (float*)h->L;
-    if ((e = run_rhs(h, U, true, L, nullptr, dtp, s)) != cudaSuccess) return e;
+    if (!s_current && (e = launch_to_fp32(U, S, M, h->sc, s)) != cudaSuccess) return e;
+    if ((e = run_rhs(h, S, L, nullptr, dtp, s)) != cudaSuccess) return e;
     if ((e = launch_rk_fp32(1, U, S, h->D, L, M, h->sc, s)) != cudaSuccess) return e;
-    if ((e = run_rhs(h, S, false, L, nullptr, dtp, s)) != cudaSuccess) return e;
+    if ((e = run_rhs(h, S, L, nullptr, dtp, s)) != cudaSuccess) return e;
     if ((e = launch_rk_fp32(2, U, S, h->D, L, M, h->sc, s)) != cudaSuccess) return e;
-    if ((e = run_rhs(h, S, false, L, nullptr, dtp, s)) != cudaSuccess) return e;
+    if ((e = run_rhs(h, S, L, nullptr, dtp, s)) != cudaSuccess) return e;
     return launch_rk_fp32(3, U, S, h->D, L, M, h->sc, s);
+}
+
+// The time step of a step: the fixed-order FP64 rule for the FP64 path (bit
+// reproducible with the oracle), the FP32-evaluated speeds with an FP64 max
+// for the FP32 path.
+static cudaError_t step_cfl(wcns_handle* h, const double* U, int clip, cudaStream_t s)
+{
+    if (h->p.precision == WCNS_FP32)
+        return launch_cfl_fast(h->ndim, U, h->N, h->h, h->gamma, h->p.cfl, clip, h->sc, s);
+    return launch_cfl(h->ndim, U, h->N, h->h, h->gamma, h->p.cfl, clip, h->sc, s);
 }
 
 static cudaError_t reset_clock(wcns_handle* h, double t_end, cudaStream_t s)
@@ -315,7 +329,7 @@ wcns_status wcns_step_rk3(wcns_handle* h, void* U, double dt, double* dt_used, v
     CK(cudaGetLastError(), "pending CUDA error");
     CK(reset_clock(h, INFINITY, s), "reset clock");
     if (dt > 0.0) CK(launch_set_dt(dt, 0, h->sc, s), "set dt");
-    else CK(launch_cfl(h->ndim, (const double*)U, h->N, h->h, h->gamma, h->p.cfl, 0, h->sc, s), "cfl");
+    else CK(step_cfl(h, (const double*)U, 0, s), "cfl");
     CK(run_stages(h, (double*)U, s), "rk3 stages");
     if (dt_used) {
         CK(cudaMemcpyAsync(dt_used, &h->sc->dt, sizeof(double), cudaMemcpyDeviceToHost, s), "dt copy");
@@ -340,8 +354,8 @@ wcns_status wcns_advance(wcns_handle* h, void* U, double t_end, int max_steps, i
         const long long left = max_steps - issued;
         const int batch = left < check ? (int)left : check;
         for (int k = 0; k < batch; ++k) {
-            CK(launch_cfl(h->ndim, (const double*)U, h->N, h->h, h->gamma, h->p.cfl, 1, h->sc, s), "cfl");
-            CK(run_stages(h, (double*)U, s), "rk3 stages");
+            CK(step_cfl(h, (const double*)U, 1, s), "cfl");
+            CK(run_stages(h, (double*)U, s, issued + k > 0), "rk3 stages");
         }
         issued += batch;
         CK(cudaMemcpyAsync(&cur, h->sc, sizeof cur, cudaMemcpyDeviceToHost, s), "clock copy");
@@ -419,7 +433,8 @@ int wcns_launches_per_step(const wcns_handle* h, int cfl_step)
 {
     if (!h) return 0;
     // clock reset + (CFL reduction and finalize | set dt) + 3 x (sweeps + stage combine)
-    return 1 + (cfl_step ? 2 : 1) + 3 * (h->ndim + 1);
+    // + the FP32 path's conversion of the state for the first stage
+    return 1 + (cfl_step ? 2 : 1) + 3 * (h->ndim + 1) + (h->p.precision == WCNS_FP32 ? 1 : 0);
 }
 
 }  // extern "C"

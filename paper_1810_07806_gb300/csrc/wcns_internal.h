@@ -5,11 +5,10 @@
 
 namespace wcns {
 
-// Launch one sweep of direction dir.  T = double (fp64) or float (fp32);
-// load_fp64 selects a double input state for the float sweep.
+// Launch one sweep of direction dir, FP64 or FP32 (input and output in the
+// sweep's precision).
 cudaError_t launch_sweep_fp64(int nd, int dir, int flux, const SweepArgs& a, cudaStream_t s);
-cudaError_t launch_sweep_fp32(int nd, int dir, int flux, bool load_fp64, const SweepArgs& a,
-                              cudaStream_t s);
+cudaError_t launch_sweep_fp32(int nd, int dir, int flux, const SweepArgs& a, cudaStream_t s);
 // Raise the dynamic shared-memory limit of every sweep instance (once per device).
 cudaError_t prepare_sweeps_fp64();
 cudaError_t prepare_sweeps_fp32();
@@ -25,6 +24,9 @@ struct StepScalars {      // device-resident
 
 cudaError_t launch_cfl(int nd, const double* U, long long N, const double* h, double gamma,
                        double cfl, int clip, StepScalars* sc, cudaStream_t s);
+// FP32-path variant: per-node speeds in FP32 (rounded upward), FP64 max and dt.
+cudaError_t launch_cfl_fast(int nd, const double* U, long long N, const double* h, double gamma,
+                            double cfl, int clip, StepScalars* sc, cudaStream_t s);
 cudaError_t launch_set_dt(double dt, int clip, StepScalars* sc, cudaStream_t s);
 cudaError_t launch_reset_clock(double t_end, StepScalars* sc, cudaStream_t s);
 // FP64 stage combinations (Shu-Osher SSP-RK3) over M = nv*N values.
@@ -33,6 +35,8 @@ cudaError_t launch_rk_fp64(int stage, double* U0, double* U1, const double* L, l
 // FP32 stages: increments relative to the FP64 base state U0.
 cudaError_t launch_rk_fp32(int stage, double* U0, float* S, float* D, const float* L, long long M,
                            const StepScalars* sc, cudaStream_t s);
+// S = float(U) (skipped when *dt == 0, i.e. the run has finished).
+cudaError_t launch_to_fp32(const double* U, float* S, long long M, const StepScalars* sc, cudaStream_t s);
 cudaError_t launch_conserved(int nv, const double* U, long long N, double vol, double* partials,
                              int nblocks, cudaStream_t s);
 int conserved_blocks(long long N);

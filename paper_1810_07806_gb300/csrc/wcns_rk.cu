@@ -62,6 +62,52 @@ __global__ void __launch_bounds__(256) cfl_reduce_kernel(const double* __restric
     }
 }
 
+// The same lambda for the FP32 path: each node's wave-speed sum is evaluated
+// in FP32 from the FP64 state and multiplied by (1 + 2^-16), an upper bound of
+// its rounding error, so the step never exceeds the FP64 CFL bound; the
+// maximum and dt stay FP64.  One pass over the state, no FP64 divisions.
+template <int ND>
+__global__ void __launch_bounds__(256) cfl_reduce_fast_kernel(const double* __restrict__ U, long long N,
+                                                              InvH hh, float gamma, StepScalars* sc,
+                                                              int clip)
+{
+    if (clip && !(sc->t < sc->t_end)) return;
+    float m = 0.f;
+    const float gm1 = gamma - 1.f;
+    float ih[ND];
+#pragma unroll
+    for (int a = 0; a < ND; ++a) ih[a] = (float)(1.0 / hh.v[a]);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float rho = (float)U[i];
+        const float ir = __frcp_rn(rho);
+        float m2 = 0.f, s = 0.f, c = 0.f;
+        float vel[ND];
+#pragma unroll
+        for (int a = 0; a < ND; ++a) {
+            const float mv = (float)U[(1 + a) * N + i];
+            m2 = fmaf(mv, mv, m2);
+            vel[a] = fabsf(mv) * ir;
+        }
+        const float p = gm1 * ((float)U[(ND + 1) * N + i] - 0.5f * m2 * ir);
+        c = sqrtf(gamma * p * ir);
+#pragma unroll
+        for (int a = 0; a < ND; ++a) s = fmaf(vel[a] + c, ih[a], s);
+        m = fmaxf(m, s);
+    }
+    double md = (double)m * (1.0 + 1.0 / 65536.0);
+    md = warp_max(md);
+    __shared__ double red[8];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = md;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        md = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        md = warp_max(md);
+        if (threadIdx.x == 0)
+            atomicMax(&sc->lam_bits, (unsigned long long)__double_as_longlong(md));
+    }
+}
+
 // dt = CFL / lambda, clipped so the step lands on t_end.
 __global__ void cfl_finalize_kernel(StepScalars* sc, double cfl, int clip)
 {
@@ -120,6 +166,18 @@ cudaError_t launch_cfl(int nd, const double* U, long long N, const double* h, do
     return cudaGetLastError();
 }
 
+cudaError_t launch_cfl_fast(int nd, const double* U, long long N, const double* h, double gamma,
+                            double cfl, int clip, StepScalars* sc, cudaStream_t s)
+{
+    InvH hh{{h[0], h[1], h[2]}};
+    const int nb = reduce_blocks(N);
+    if (nd == 1) cfl_reduce_fast_kernel<1><<<nb, 256, 0, s>>>(U, N, hh, (float)gamma, sc, clip);
+    else if (nd == 2) cfl_reduce_fast_kernel<2><<<nb, 256, 0, s>>>(U, N, hh, (float)gamma, sc, clip);
+    else cfl_reduce_fast_kernel<3><<<nb, 256, 0, s>>>(U, N, hh, (float)gamma, sc, clip);
+    cfl_finalize_kernel<<<1, 1, 0, s>>>(sc, cfl, clip);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_set_dt(double dt, int clip, StepScalars* sc, cudaStream_t s)
 {
     set_dt_kernel<<<1, 1, 0, s>>>(sc, dt, clip);
@@ -170,6 +228,7 @@ cudaError_t launch_rk_fp64(int stage, double* U0, double* U1, const double* L, l
 // the FP32 increment D carries the stage update, so nothing of the update is
 // lost to the size of U.  S = float(U0) + D is the next sweep's input.
 //   D1 = dt L,  D2 = (D1 + dt L)/4,  U0 += 2/3 (D2 + dt L)   (FP64 accumulation)
+// The last stage also leaves float(U0) in S for the next step's first stage.
 template <int STAGE>
 __global__ void __launch_bounds__(256) rk_fp32_kernel(double* __restrict__ U0, float* __restrict__ S,
                                                       float* __restrict__ D, const float* __restrict__ L,
@@ -191,7 +250,9 @@ __global__ void __launch_bounds__(256) rk_fp32_kernel(double* __restrict__ U0, f
             S[i] = __double2float_rn(U0[i]) + d;
         } else {
             const float d = (2.0f / 3.0f) * fmaf(dt, l, D[i]);
-            U0[i] += (double)d;
+            const double u = U0[i] + (double)d;
+            U0[i] = u;
+            S[i] = __double2float_rn(u);   // the next step's first-stage input
         }
     }
 }
@@ -203,6 +264,22 @@ cudaError_t launch_rk_fp32(int stage, double* U0, float* S, float* D, const floa
     if (stage == 1) rk_fp32_kernel<1><<<nb, 256, 0, s>>>(U0, S, D, L, M, sc);
     else if (stage == 2) rk_fp32_kernel<2><<<nb, 256, 0, s>>>(U0, S, D, L, M, sc);
     else rk_fp32_kernel<3><<<nb, 256, 0, s>>>(U0, S, D, L, M, sc);
+    return cudaGetLastError();
+}
+
+// S = float(U): the single-precision input of a step's first stage.
+__global__ void __launch_bounds__(256) to_fp32_kernel(const double* __restrict__ U, float* __restrict__ S,
+                                                      long long M, const StepScalars* sc)
+{
+    if (sc != nullptr && sc->dt == 0.0) return;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M;
+         i += (long long)gridDim.x * blockDim.x)
+        S[i] = __double2float_rn(U[i]);
+}
+
+cudaError_t launch_to_fp32(const double* U, float* S, long long M, const StepScalars* sc, cudaStream_t s)
+{
+    to_fp32_kernel<<<stream_blocks(M), 256, 0, s>>>(U, S, M, sc);
     return cudaGetLastError();
 }
 

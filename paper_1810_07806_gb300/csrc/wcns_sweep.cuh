@@ -33,6 +33,18 @@ struct SweepArgs {
     float sqrt_eps_f;         // sqrt(eps) in float, for the FP32 rescaled eps
 };
 
+// 4-byte asynchronous global->shared copies (cp.async): the staging loads
+// and the prefetch of the RHS being accumulated proceed while the CTA
+// computes, instead of stalling the issuing warps.
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int NW>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(NW) : "memory"); }
+
 template <typename T, int ND, int DIR>
 struct TileGeom {
     static constexpr int TL = (ND == 1) ? 1 : (DIR == 0 ? 4 : 16);   // lines per tile
@@ -40,9 +52,14 @@ struct TileGeom {
     static constexpr int P = TS + 2 * GHOST;                          // staged nodes
     static constexpr int NF = TS + 5;                                 // faces
     static constexpr int THREADS = 256;
+    // FP32: at most 64 registers so four CTAs share an SM; FP64 is bound by
+    // its pipe and keeps the compiler's choice.
+    static constexpr int MIN_CTAS = sizeof(T) == 4 ? 4 : 1;
+    // FP32 sweeps that accumulate prefetch the TS nodes of L they update
+    static constexpr bool PREFETCH_L = sizeof(T) == 4;
     static constexpr size_t smem_bytes()
     {
-        return sizeof(T) * (size_t)(ND + 2) * TL * (P + NF);
+        return sizeof(T) * (size_t)(ND + 2) * TL * (P + NF + (PREFETCH_L ? TS : 0));
     }
 };
 
@@ -180,15 +197,19 @@ __device__ __forceinline__ void face_flux(float (&u)[6][ND + 2], const SweepArgs
 
 // ---------------------------------------------------------------- kernel
 template <typename T, typename LT, int ND, int DIR, int FLUX>
-__global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a)
+__global__ void __launch_bounds__(256, TileGeom<T, ND, DIR>::MIN_CTAS) sweep_kernel(const SweepArgs a)
 {
     constexpr int NV = ND + 2;
     using G = TileGeom<T, ND, DIR>;
     constexpr int TL = G::TL, TS = G::TS, P = G::P, NF = G::NF;
+    constexpr bool kAsyncStage = sizeof(LT) == sizeof(T) && sizeof(T) == 4;
+    constexpr bool kPre = G::PREFETCH_L;
+    constexpr bool kAsync = kAsyncStage || kPre;
     if (a.dt != nullptr && *a.dt == 0.0) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sS = reinterpret_cast<T*>(smem_raw);
     T* sF = sS + NV * TL * P;
+    T* sL = sF + NV * TL * NF;   // prefetched L (FP32 accumulating sweeps)
 
     const int nx = a.n[0], ny = a.n[1];
     const int nd = a.n[DIR];
@@ -229,7 +250,27 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a)
         int p = pos0 - GHOST + s;
         if (a.periodic) { p %= nd; if (p < 0) p += nd; }
         else p = min(max(p, 0), nd - 1);
-        sS[sidx<DIR, TL, P>(v, l, s)] = (T)U[v * N + base0 + l * lstride + (long long)p * sd];
+        const LT* src = &U[v * N + base0 + l * lstride + (long long)p * sd];
+        if constexpr (kAsyncStage) cp_async4(&sS[sidx<DIR, TL, P>(v, l, s)], src);
+        else sS[sidx<DIR, TL, P>(v, l, s)] = (T)*src;
+    }
+    if constexpr (kAsync) cp_async_commit();   // group: staged nodes
+    if constexpr (kPre) {
+        if (a.accumulate) {                    // group: the L values this tile adds to
+            const T* Lg = reinterpret_cast<const T*>(a.L);
+            for (int e = threadIdx.x; e < NV * TL * TS; e += blockDim.x) {
+                int v, l, t;
+                if (DIR == 0) { t = e % TS; const int r = e / TS; l = r % TL; v = r / TL; }
+                else { l = e % TL; const int r = e / TL; t = r % TS; v = r / TS; }
+                if (l >= lcount || t >= tcount) continue;
+                cp_async4(&sL[sidx<DIR, TL, TS>(v, l, t)],
+                          &Lg[v * N + base0 + l * lstride + (long long)(pos0 + t) * sd]);
+            }
+        }
+        cp_async_commit();
+        cp_async_wait<1>();                    // staged nodes have landed
+    } else if constexpr (kAsync) {
+        cp_async_wait<0>();
     }
     __syncthreads();
 
@@ -262,6 +303,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a)
         }
     }
     if (fb) atomicAdd((unsigned long long*)a.fallback, (unsigned long long)fb);
+    if constexpr (kPre) cp_async_wait<0>();    // prefetched L has landed
     __syncthreads();
 
     // (3) Eq. 3 at nodes pos0 .. pos0 + tcount - 1
@@ -283,8 +325,9 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a)
             } else {
                 const T fp = fma(T(MD_A1), f3 - f2, fma(T(MD_A2), f4 - f1, T(MD_A3) * (f5 - f0)));
                 const T val = -fp * ih;
-                if (a.accumulate) L[v * N + g] += val;
-                else L[v * N + g] = val;
+                if (!a.accumulate) L[v * N + g] = val;
+                else if constexpr (kPre) L[v * N + g] = sL[sidx<DIR, TL, TS>(v, l, t)] + val;
+                else L[v * N + g] += val;
             }
         }
     }
