@@ -153,6 +153,8 @@ wcns_status wcns_create(const wcns_grid* g, double gamma, const wcns_scheme_para
     h->K.Cf = (float)prm->C;
     h->K.CTf = (float)prm->CT;
     h->K.Kf = (float)h->K.keep_all_K;
+    h->K.gammaf = (float)gamma;
+    h->K.gm1f = (float)(gamma - 1.0);
     h->sqrt_eps_f = (float)sqrt(prm->eps);
 
     cudaError_t e = cudaGetDevice(&h->device);
@@ -250,6 +252,7 @@ static cudaError_t run_rhs(wcns_handle* h, const void* U, void* L, uint8_t* flag
         a.n[2] = h->n[2];
         a.periodic = h->periodic[d];
         a.inv_h = h->inv_h[d];
+        a.inv_hf = (float)h->inv_h[d];
         a.accumulate = d > 0;
         a.flags = flags ? flags + flags_offset(h, d) : nullptr;
         a.fallback = h->fallback;

@@ -47,6 +47,7 @@ struct SchemeConst {
     int q;
     double keep_all_K;   // tau < K * (min beta + eps) guarantees no cut (exact test)
     float Cf, CTf, Kf;
+    float gammaf, gm1f;  // gamma, gamma - 1 in float
 };
 
 // FP32 selection.  chi_k is invariant under s -> s/sc except through eps, so

@@ -31,6 +31,7 @@ struct SweepArgs {
     const double* dt;         // nullable: skip all work when *dt == 0 (finished)
     SchemeConst K;
     float sqrt_eps_f;         // sqrt(eps) in float, for the FP32 rescaled eps
+    float inv_hf;             // 1 / h_DIR in float
 };
 
 // 4-byte asynchronous global->shared copies (cp.async): the staging loads
@@ -84,7 +85,7 @@ __device__ __forceinline__ void face_flux(float (&u)[6][ND + 2], const SweepArgs
                                           uint8_t* fl, bool& fell_back)
 {
     constexpr int NV = ND + 2;
-    const float gm1 = (float)a.K.gm1;
+    const float gm1 = a.K.gm1f;
     // Roe average of nodes j, j+1 and the closed form of L U:
     //   P = b1 (E - vel.m + q2 rho / 2), Q = (u_n rho - m_n) / c,
     //   w_0 = (P + Q)/2, w_1 = rho - P, w_t = m_t - vel_t rho, w_N = (P - Q)/2.
@@ -188,8 +189,8 @@ __device__ __forceinline__ void face_flux(float (&u)[6][ND + 2], const SweepArgs
         roe_flux<ND, DIR>(UL, UR, pL, pR, gm1, F);
     } else {
         float Fp[NV], Fm[NV];
-        vanleer_half<ND, DIR>(UL, pL, (float)a.K.gamma, gm1, 1.f, Fp);
-        vanleer_half<ND, DIR>(UR, pR, (float)a.K.gamma, gm1, -1.f, Fm);
+        vanleer_half<ND, DIR>(UL, pL, a.K.gammaf, gm1, 1.f, Fp);
+        vanleer_half<ND, DIR>(UR, pR, a.K.gammaf, gm1, -1.f, Fm);
 #pragma unroll
         for (int v = 0; v < NV; ++v) F[v] = Fp[v] + Fm[v];
     }
@@ -205,7 +206,11 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR>::MIN_CTAS) sweep_ker
     constexpr bool kAsyncStage = sizeof(LT) == sizeof(T) && sizeof(T) == 4;
     constexpr bool kPre = G::PREFETCH_L;
     constexpr bool kAsync = kAsyncStage || kPre;
-    if (a.dt != nullptr && *a.dt == 0.0) return;
+    // A finished run (dt == 0) skips the work.  The FP32 sweep reads the flag
+    // after its staging copies are in flight, so the read costs no latency.
+    if constexpr (!kAsyncStage) {
+        if (a.dt != nullptr && *a.dt == 0.0) return;
+    }
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sS = reinterpret_cast<T*>(smem_raw);
     T* sF = sS + NV * TL * P;
@@ -240,31 +245,47 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR>::MIN_CTAS) sweep_ker
     const int tcount = min(TS, nd - pos0);
     const int nfaces = tcount + 5;
 
-    // (1) stage nodes pos0-5 .. pos0+TS+4 of each line
+    // (1) stage nodes pos0-5 .. pos0+TS+4 of each line: one boundary-mapped
+    // position per (line, node) pair, then its NV variables.  Positions lie in
+    // [pos0 - 5, pos0 + TS + 5), so one conditional wrap suffices unless the
+    // periodic axis is shorter than the staged window.
     const LT* U = reinterpret_cast<const LT*>(a.U);
-    for (int e = threadIdx.x; e < NV * TL * P; e += blockDim.x) {
-        int v, l, s;
-        if (DIR == 0) { s = e % P; const int r = e / P; l = r % TL; v = r / TL; }
-        else { l = e % TL; const int r = e / TL; s = r % P; v = r / P; }
+    const bool wrap_mod = a.periodic && nd < P;
+    for (int e = threadIdx.x; e < TL * P; e += blockDim.x) {
+        int l, s;
+        if (DIR == 0) { s = e % P; l = e / P; } else { l = e % TL; s = e / TL; }
         if (l >= lcount) continue;
         int p = pos0 - GHOST + s;
-        if (a.periodic) { p %= nd; if (p < 0) p += nd; }
-        else p = min(max(p, 0), nd - 1);
-        const LT* src = &U[v * N + base0 + l * lstride + (long long)p * sd];
-        if constexpr (kAsyncStage) cp_async4(&sS[sidx<DIR, TL, P>(v, l, s)], src);
-        else sS[sidx<DIR, TL, P>(v, l, s)] = (T)*src;
+        if (a.periodic) {
+            if (wrap_mod) { p %= nd; if (p < 0) p += nd; }
+            else p = p < 0 ? p + nd : (p >= nd ? p - nd : p);
+        } else {
+            p = min(max(p, 0), nd - 1);
+        }
+        const LT* src = U + base0 + l * lstride + (long long)p * sd;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            if constexpr (kAsyncStage) cp_async4(&sS[sidx<DIR, TL, P>(v, l, s)], src + v * N);
+            else sS[sidx<DIR, TL, P>(v, l, s)] = (T)src[v * N];
+        }
     }
     if constexpr (kAsync) cp_async_commit();   // group: staged nodes
+    if constexpr (kAsyncStage) {
+        if (a.dt != nullptr && *a.dt == 0.0) {
+            cp_async_wait<0>();
+            return;
+        }
+    }
     if constexpr (kPre) {
         if (a.accumulate) {                    // group: the L values this tile adds to
             const T* Lg = reinterpret_cast<const T*>(a.L);
-            for (int e = threadIdx.x; e < NV * TL * TS; e += blockDim.x) {
-                int v, l, t;
-                if (DIR == 0) { t = e % TS; const int r = e / TS; l = r % TL; v = r / TL; }
-                else { l = e % TL; const int r = e / TL; t = r % TS; v = r / TS; }
+            for (int e = threadIdx.x; e < TL * TS; e += blockDim.x) {
+                int l, t;
+                if (DIR == 0) { t = e % TS; l = e / TS; } else { l = e % TL; t = e / TL; }
                 if (l >= lcount || t >= tcount) continue;
-                cp_async4(&sL[sidx<DIR, TL, TS>(v, l, t)],
-                          &Lg[v * N + base0 + l * lstride + (long long)(pos0 + t) * sd]);
+                const T* src = Lg + base0 + l * lstride + (long long)(pos0 + t) * sd;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) cp_async4(&sL[sidx<DIR, TL, TS>(v, l, t)], src + v * N);
             }
         }
         cp_async_commit();
@@ -308,7 +329,9 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR>::MIN_CTAS) sweep_ker
 
     // (3) Eq. 3 at nodes pos0 .. pos0 + tcount - 1
     T* L = reinterpret_cast<T*>(a.L);
-    const T ih = (T)a.inv_h;
+    T ih;
+    if constexpr (sizeof(T) == 8) ih = a.inv_h;
+    else ih = a.inv_hf;
     for (int e = threadIdx.x; e < TL * TS; e += blockDim.x) {
         int l, t;
         if (DIR == 0) { t = e % TS; l = e / TS; } else { l = e % TL; t = e / TL; }
