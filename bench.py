@@ -47,7 +47,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="tgv256", choices=["tgv256", "quad1024", "sod400"])
+    ap.add_argument("--workload", default="tgv256",
+                    choices=["tgv256", "quad1024", "sod400", "batch1d", "serve"])
+    ap.add_argument("--requests", type=int, default=32, help="serve: requests replayed from the trace")
+    ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrival rate (1/s)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain-path line")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     return ap.parse_args()
@@ -348,8 +351,102 @@ def ours_arm(args, world, rank, local):
     solver.close()
 
 
+def batch_arm(args):
+    """Batched 1D Euler: 4096 Shu-Osher-type instances (N log-uniform in
+    [200, 4000]); one step = one SSP-RK3 step of every instance."""
+    import torch
+    from paper_1810_07806_gb300 import inputs, wcns
+    pbs = inputs.shu_osher_batch(4096)
+    nodes = sum(p.cells for p in pbs)
+    out = {}
+    for name, prec, k in (("fp32", wcns.FP32, args.steps), ("fp64", wcns.FP64, max(1, min(args.steps, 5)))):
+        b = wcns.Batch(1, max_nodes=nodes, max_instances=len(pbs), precision=prec)
+        for pb in pbs:
+            b.add(pb)
+        b.step(max(1, args.warmup))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.step(k)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / k
+        out[name] = {"value": nodes * 3 / ms * 1e3, "ms_per_step": ms, "steps": k}
+        b.close()
+    # the plain path: one instance per launch sequence, FP64, on a subset
+    sub = pbs[:64]
+    sol = [wcns.Solver.for_problem(pb) for pb in sub]
+    Us = [torch.from_numpy(pb.U0.copy()).cuda() for pb in sub]
+    for s_, U in zip(sol, Us):
+        s_.step(U)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        for s_, U in zip(sol, Us):
+            s_.step(U)
+    torch.cuda.synchronize()
+    el = (time.perf_counter() - t0) / 3
+    out["plain_fp64"] = {"value": sum(p.cells for p in sub) * 3 / el, "ms_per_step_64_instances": el * 1e3}
+    print(json.dumps({
+        "metric": METRIC, "value": out["fp32"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": out["fp32"]["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batched_shu_osher_1d_4096_instances", "nodes": nodes, "seed": 1810,
+                   "precision": "fp32 bulk", "launch": "one graph per RK3 step, one launch per stage kernel"},
+        "batched_fp64": out["fp64"], "plain_fp64_one_instance_per_launch": out["plain_fp64"]}))
+
+
+def serve_arm(args):
+    """Serving: a seeded Poisson trace of four-quadrant Riemann requests (side
+    log-uniform 128..1024, t_end U[0.1, 0.3], half FP32 / half FP64) replayed
+    in real time against one server; latency = result ready - arrival."""
+    import numpy as np
+    from paper_1810_07806_gb300 import inputs, wcns
+    trace = inputs.serving_trace(args.requests, rate=args.rate)
+    sv = wcns.Server(hbm_budget_bytes=64 << 30, max_instances_per_class=64, steps_per_tick=16)
+    t0 = time.perf_counter()
+    arrivals = {}
+    work = {}
+    got = {}
+    k = 0
+    qdepth = []
+    while len(got) < len(trace):
+        now = time.perf_counter() - t0
+        while k < len(trace) and trace[k].arrival_s <= now:
+            r = trace[k]
+            pb = r.problem()
+            sv.submit(pb, tag=k, precision=wcns.FP32 if r.fp32 else wcns.FP64)
+            arrivals[k] = time.perf_counter() - t0
+            work[k] = pb.cells
+            k += 1
+        for res in sv.poll(64, timeout_us=2000):
+            res["ready"] = time.perf_counter() - t0
+            got[res["tag"]] = res
+        qdepth.append(sv.stats()["queued"])
+    total = time.perf_counter() - t0
+    lat = np.array([got[i]["ready"] - arrivals[i] for i in range(len(trace))])
+    cells = sum(work[i] * 3 * got[i]["steps"] for i in range(len(trace)))
+    st = sv.stats()
+    sv.close()
+    print(json.dumps({
+        "metric": METRIC, "value": cells / total, "unit": UNIT, "n_gpus": 1, "steps": int(st["steps"]),
+        "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "serving_four_quadrant_2d_trace", "requests": len(trace), "rate_per_s": args.rate,
+                   "seed": 7806, "side": "log-uniform 128..1024", "t_end": "U[0.1,0.3]", "fp32_share": 0.5},
+        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                      "max": float(lat.max())},
+        "wall_s": total, "max_queue": int(max(qdepth) if qdepth else 0), "max_running": st["max_running"],
+        "all_ok": all(got[i]["status"] == 0 for i in range(len(trace)))}))
+
+
 def main():
     args = parse()
+    if args.workload == "batch1d" and args.impl == "ours":
+        return batch_arm(args)
+    if args.workload == "serve" and args.impl == "ours":
+        return serve_arm(args)
     if args.impl == "reference":
         # the reference arm runs on rank 0's host cores only; other ranks exit
         rank = int(os.environ.get("RANK", "0"))

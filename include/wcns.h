@@ -171,6 +171,110 @@ wcns_status wcns_step_rk3_noalloc(const wcns_grid* grid, double gamma,
                                   const wcns_scheme_params* params, void* U, double dt,
                                   double* dt_used, void* stream);
 
+/* ---------------------------------------------------------------------
+ * Batches (no counterpart in the paper; the method is applied unchanged to
+ * every instance).  A batch advances many independent grids of one
+ * dimension, precision and scheme together: each instance has its own node
+ * counts, boundary rules, CFL time step and end time.  One launch per sweep
+ * direction covers the tiles of all instances; one SSP-RK3 step of the
+ * whole batch is captured as a CUDA graph and replayed.  An instance gives
+ * the same result in a batch as alone (bit for bit in FP64).
+ * --------------------------------------------------------------------- */
+typedef struct wcns_batch wcns_batch;
+
+/* Create a batch for up to max_instances instances holding max_nodes nodes
+ * in total (device arenas are allocated here: state, stage and RHS arrays,
+ * plus per-instance clocks).  params as for wcns_create. */
+wcns_status wcns_batch_create(int ndim, double gamma, const wcns_scheme_params* params,
+                              long long max_nodes, int max_instances, wcns_batch** out);
+wcns_status wcns_batch_destroy(wcns_batch* b);
+size_t wcns_batch_bytes(const wcns_batch* b);
+
+/* Add an instance with FP64 initial state U0 (nv * N doubles, SoA; a host
+ * pointer, or a device pointer when u0_on_device) to be advanced from t = 0
+ * to t_end.  Returns its slot.  WCNS_ERR_BUSY: no free slot; WCNS_ERR_NOMEM:
+ * not enough free arena.  The copy is queued on `stream`; it joins at the
+ * next wcns_batch_step. */
+wcns_status wcns_batch_add(wcns_batch* b, const wcns_grid* grid, const double* U0, int u0_on_device,
+                           double t_end, int* slot, void* stream);
+
+/* Free an instance's slot and arena range (after its result was read). */
+wcns_status wcns_batch_remove(wcns_batch* b, int slot);
+
+/* Advance every instance by nsteps RK3 steps (finished instances do no
+ * work).  If active is non-NULL, synchronises and returns how many
+ * instances advanced in the last step (0: all have reached t_end). */
+wcns_status wcns_batch_step(wcns_batch* b, int nsteps, int* active, void* stream);
+
+/* Step until every instance has finished or max_steps, checking every
+ * `check` steps.  Returns the steps taken.  Synchronises. */
+wcns_status wcns_batch_run(wcns_batch* b, int max_steps, int check, int* steps, void* stream);
+
+/* Copy an instance's FP64 state (host pointer, or device when out_on_device;
+ * nullable) and return its time and step count.  Synchronises the stream. */
+wcns_status wcns_batch_read(wcns_batch* b, int slot, double* U_out, int out_on_device, double* t,
+                            int* steps, void* stream);
+
+/* ---------------------------------------------------------------------
+ * Serving (no counterpart in the paper).  A server accepts solve requests
+ * at any time and runs them with continuous batching: a worker thread
+ * admits queued requests (in arrival order) into resident batches, one per
+ * scheme class, as the HBM budget, a slot and arena space allow; everything
+ * admitted advances together, a fixed number of RK3 steps per tick;
+ * requests join and leave at step boundaries; finished states are copied
+ * to the host and returned by wcns_serve_poll.  A result equals the same
+ * problem solved alone (bit for bit).  The server uses the CUDA device that
+ * is current when it is created.
+ * --------------------------------------------------------------------- */
+typedef struct wcns_server wcns_server;
+
+typedef struct {
+    size_t hbm_budget_bytes;      /* device memory the server may reserve      */
+    int max_instances_per_class;  /* slots of each class's batch               */
+    long long max_nodes_per_class;/* arena cap per class (0: budget share)     */
+    int steps_per_tick;           /* RK3 steps between admission/retirement    */
+} wcns_server_config;
+
+typedef struct {
+    wcns_grid grid;
+    double gamma;
+    wcns_scheme_params params;    /* precision selects the FP32 or FP64 path   */
+    const double* U0;             /* host FP64 initial state, copied on submit */
+    double t_end;
+    uint64_t tag;                 /* returned unchanged in the result          */
+} wcns_request;
+
+typedef struct {
+    uint64_t ticket, tag;
+    wcns_status status;           /* WCNS_OK, or why the request failed         */
+    int ndim, n[3], precision;
+    double t;                     /* time reached (t_end)                      */
+    int steps;                    /* RK3 steps taken                           */
+    double* U;                    /* host FP64 final state, owned by the result */
+    double t_submit, t_admit, t_done;   /* seconds since server creation       */
+} wcns_result;
+
+typedef struct {
+    int queued, max_queue, max_running;
+    long long admitted, completed, ticks, steps;
+    size_t bytes_reserved;
+} wcns_server_stats_t;
+
+void wcns_server_default_config(wcns_server_config* cfg);
+wcns_status wcns_server_create(const wcns_server_config* cfg, wcns_server** out);
+/* Stops the worker; requests still queued complete with WCNS_ERR_BUSY. */
+wcns_status wcns_server_destroy(wcns_server* sv);
+
+/* Queue a request (thread-safe; copies U0).  Returns a ticket. */
+wcns_status wcns_batch_submit(wcns_server* sv, const wcns_request* req, uint64_t* ticket);
+
+/* Up to `max` finished results, waiting up to timeout_us for the first
+ * (0: no wait).  WCNS_ERR_TIMEOUT if none arrived in time.  Each result's U
+ * must be released with wcns_result_free. */
+wcns_status wcns_serve_poll(wcns_server* sv, wcns_result* out, int max, int* n_out, int timeout_us);
+void wcns_result_free(wcns_result* r);
+wcns_status wcns_server_stats(wcns_server* sv, wcns_server_stats_t* stats);
+
 /* Number of kernel launches one wcns_step_rk3 call issues (for accounting). */
 int wcns_launches_per_step(const wcns_handle* h, int cfl_step);
 

@@ -18,8 +18,10 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
           "--expt-relaxed-constexpr"]
 # The FP32 sweep may use approximate division/sqrt and flush denormals; the
 # FP64 units keep IEEE division and square root (always the case for double).
-EXTRA = {"sweep_fp32.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]}
-SOURCES = ["wcns_api.cu", "wcns_rk.cu", "sweep_fp64.cu", "sweep_fp32.cu", "wcns_noalloc.cu"]
+FP32_FLAGS = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
+EXTRA = {"sweep_fp32.cu": FP32_FLAGS, "sweep_batch_fp32.cu": FP32_FLAGS}
+SOURCES = ["wcns_api.cu", "wcns_rk.cu", "sweep_fp64.cu", "sweep_fp32.cu", "wcns_noalloc.cu",
+           "wcns_batch.cu", "sweep_batch_fp64.cu", "sweep_batch_fp32.cu", "wcns_serve.cu"]
 
 
 def nvcc():

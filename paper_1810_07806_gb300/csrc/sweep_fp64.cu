@@ -43,14 +43,7 @@ cudaError_t launch_sweep_fp64(int nd, int dir, int flux, const SweepArgs& a, cud
 cudaError_t prepare_sweeps_fp64()
 {
     // omega_k^(T) = delta_k d_k / sum_j delta_j d_j (Eq. 19), sum in k order
-    const double d[3] = {1.0 / 16.0, 10.0 / 16.0, 5.0 / 16.0};
-    double w[8][3];
-    for (int f = 0; f < 8; ++f) {
-        double ds = 0.0;
-        for (int k = 0; k < 3; ++k) ds += ((f >> k) & 1) ? d[k] : 0.0;
-        for (int k = 0; k < 3; ++k) w[f][k] = f == 0 ? d[k] : (((f >> k) & 1) ? d[k] : 0.0) / ds;
-    }
-    cudaError_t e0 = cudaMemcpyToSymbol(c_omega, w, sizeof w);
+    cudaError_t e0 = fill_omega_table();
     if (e0 != cudaSuccess) return e0;
     SweepArgs a{};
     for (int nd = 1; nd <= 3; ++nd)

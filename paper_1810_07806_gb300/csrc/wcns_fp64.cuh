@@ -153,6 +153,19 @@ __device__ __forceinline__ int select_fp64(const double s[5], const SchemeConst&
 // from the host (the same IEEE divisions) before the first launch.
 static __constant__ double c_omega[8][3];
 
+// Fills this translation unit's copy of c_omega (host side, before launches).
+static inline cudaError_t fill_omega_table()
+{
+    const double d[3] = {1.0 / 16.0, 10.0 / 16.0, 5.0 / 16.0};
+    double w[8][3];
+    for (int f = 0; f < 8; ++f) {
+        double ds = 0.0;
+        for (int k = 0; k < 3; ++k) ds += ((f >> k) & 1) ? d[k] : 0.0;
+        for (int k = 0; k < 3; ++k) w[f][k] = f == 0 ? d[k] : (((f >> k) & 1) ? d[k] : 0.0) / ds;
+    }
+    return cudaMemcpyToSymbol(c_omega, w, sizeof w);
+}
+
 // Eq. 9 and Eq. 12: u = sum_k omega_k (u_i + D1_k / 2 + D2_k / 8).
 __device__ __forceinline__ double interp_fp64(int flags, const double s[5], const double D1[3],
                                               const double D2[3])

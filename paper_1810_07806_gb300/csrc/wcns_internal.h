@@ -9,6 +9,13 @@ namespace wcns {
 // sweep's precision).
 cudaError_t launch_sweep_fp64(int nd, int dir, int flux, const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_sweep_fp32(int nd, int dir, int flux, const SweepArgs& a, cudaStream_t s);
+// Batched sweeps over a tile table (wcns_batch.cu); ntiles CTAs.
+cudaError_t launch_sweep_batch_fp64(int nd, int dir, int flux, const SweepArgs& a, long long ntiles,
+                                    cudaStream_t s);
+cudaError_t launch_sweep_batch_fp32(int nd, int dir, int flux, const SweepArgs& a, long long ntiles,
+                                    cudaStream_t s);
+cudaError_t prepare_sweeps_batch_fp64();
+cudaError_t prepare_sweeps_batch_fp32();
 // Raise the dynamic shared-memory limit of every sweep instance (once per device).
 cudaError_t prepare_sweeps_fp64();
 cudaError_t prepare_sweeps_fp32();
@@ -40,6 +47,16 @@ cudaError_t launch_to_fp32(const double* U, float* S, long long M, const StepSca
 cudaError_t launch_conserved(int nv, const double* U, long long N, double vol, double* partials,
                              int nblocks, cudaStream_t s);
 int conserved_blocks(long long N);
+
+}  // namespace wcns
+#include <vector>
+struct wcns_batch;
+namespace wcns {
+// Batch helpers for the serving loop (wcns_batch.cu).
+cudaError_t batch_finished_slots(wcns_batch* b, std::vector<int>& out, cudaStream_t s);
+int batch_active_count(const wcns_batch* b);
+bool batch_fits(const wcns_batch* b, long long nodes);
+long long batch_capacity_nodes(const wcns_batch* b);
 
 // Sets the thread-local message returned by wcns_last_error().
 void set_last_error(const char* msg);

@@ -18,6 +18,29 @@ namespace wcns {
 
 enum { FLUX_ROE = 0, FLUX_VANLEER = 1 };
 
+// Batched sweeps run over many independent grids ("instances") of one
+// dimension at once: each CTA takes one tile from a table and reads its
+// instance's geometry.  Instance i's state is an SoA block [var][nodes_i] at
+// element offset `off` of the batch arrays.
+struct BatchInst {
+    long long off;            // element offset of the instance's block
+    long long N;              // nodes of the instance
+    int n[3];                 // nodes per axis
+    int periodic[3];          // boundary rule per axis
+    double h[3];              // node spacing per axis
+    double inv_h[3];          // 1 / h per axis
+    float inv_hf[3];
+};
+
+struct BatchTile {
+    int inst;                 // instance index
+    int pos0;                 // first node along the sweep direction
+    int lfirst;               // first line of the tile (x sweep: row; y/z: x column)
+    int outer;                // y/z sweeps: the remaining axis index
+};
+
+struct StepScalars;
+
 struct SweepArgs {
     const void* U;            // input state, LT, SoA
     void* L;                  // output RHS, T, SoA
@@ -32,6 +55,11 @@ struct SweepArgs {
     SchemeConst K;
     float sqrt_eps_f;         // sqrt(eps) in float, for the FP32 rescaled eps
     float inv_hf;             // 1 / h_DIR in float
+    // batched mode only
+    const BatchInst* insts;
+    const BatchTile* tiles;
+    const double* inst_dt;    // dt of instance i at inst_dt[i * dt_stride]
+    int dt_stride;            // in doubles
 };
 
 // 4-byte asynchronous global->shared copies (cp.async): the staging loads
@@ -197,7 +225,7 @@ __device__ __forceinline__ void face_flux(float (&u)[6][ND + 2], const SweepArgs
 }
 
 // ---------------------------------------------------------------- kernel
-template <typename T, typename LT, int ND, int DIR, int FLUX>
+template <typename T, typename LT, int ND, int DIR, int FLUX, bool BATCH = false>
 __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR>::MIN_CTAS) sweep_kernel(const SweepArgs a)
 {
     constexpr int NV = ND + 2;
@@ -206,38 +234,70 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR>::MIN_CTAS) sweep_ker
     constexpr bool kAsyncStage = sizeof(LT) == sizeof(T) && sizeof(T) == 4;
     constexpr bool kPre = G::PREFETCH_L;
     constexpr bool kAsync = kAsyncStage || kPre;
+
+    // The grid (one instance, or the tile's instance in batched mode).
+    const LT* Ub;
+    T* Lb;
+    long long N;
+    int nx, ny, nd, periodic, pos0, lfirst;
+    long long outer;
+    const double* dtp;
+    T ih;
+    if constexpr (BATCH) {
+        const BatchTile bt = a.tiles[blockIdx.x];
+        const BatchInst& I = a.insts[bt.inst];
+        Ub = reinterpret_cast<const LT*>(a.U) + I.off;
+        Lb = reinterpret_cast<T*>(a.L) + I.off;
+        N = I.N;
+        nx = I.n[0];
+        ny = I.n[1];
+        nd = I.n[DIR];
+        periodic = I.periodic[DIR];
+        if constexpr (sizeof(T) == 8) ih = I.inv_h[DIR];
+        else ih = I.inv_hf[DIR];
+        pos0 = bt.pos0;
+        lfirst = bt.lfirst;
+        outer = bt.outer;
+        dtp = a.inst_dt + (long long)bt.inst * a.dt_stride;
+    } else {
+        Ub = reinterpret_cast<const LT*>(a.U);
+        Lb = reinterpret_cast<T*>(a.L);
+        N = a.N;
+        nx = a.n[0];
+        ny = a.n[1];
+        nd = a.n[DIR];
+        periodic = a.periodic;
+        if constexpr (sizeof(T) == 8) ih = a.inv_h;
+        else ih = a.inv_hf;
+        pos0 = blockIdx.y * TS;
+        lfirst = blockIdx.x * TL;
+        outer = blockIdx.z;
+        dtp = a.dt;
+    }
     // A finished run (dt == 0) skips the work.  The FP32 sweep reads the flag
     // after its staging copies are in flight, so the read costs no latency.
     if constexpr (!kAsyncStage) {
-        if (a.dt != nullptr && *a.dt == 0.0) return;
+        if (dtp != nullptr && *dtp == 0.0) return;
     }
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sS = reinterpret_cast<T*>(smem_raw);
     T* sF = sS + NV * TL * P;
     T* sL = sF + NV * TL * NF;   // prefetched L (FP32 accumulating sweeps)
 
-    const int nx = a.n[0], ny = a.n[1];
-    const int nd = a.n[DIR];
-    const long long N = a.N;
     long long sd;
-    int pos0, lfirst, lcount;
+    int lcount;
     long long base0, lstride;   // base offset of local line l = base0 + l * lstride
     long long line0;            // global line index of local line 0 (for flags)
     if (DIR == 0) {
         const int rows = (int)(N / nx);
         sd = 1;
-        pos0 = blockIdx.y * TS;
-        lfirst = blockIdx.x * TL;
         lcount = min(TL, rows - lfirst);
         base0 = (long long)lfirst * nx;
         lstride = nx;
         line0 = lfirst;
     } else {
         sd = (DIR == 1) ? (long long)nx : (long long)nx * ny;
-        pos0 = blockIdx.y * TS;
-        lfirst = blockIdx.x * TL;
         lcount = min(TL, nx - lfirst);
-        const long long outer = blockIdx.z;   // z for DIR 1, y for DIR 2
         base0 = (DIR == 1 ? outer * nx * ny : outer * nx) + lfirst;
         lstride = 1;
         line0 = outer * nx + lfirst;
@@ -249,14 +309,14 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR>::MIN_CTAS) sweep_ker
     // position per (line, node) pair, then its NV variables.  Positions lie in
     // [pos0 - 5, pos0 + TS + 5), so one conditional wrap suffices unless the
     // periodic axis is shorter than the staged window.
-    const LT* U = reinterpret_cast<const LT*>(a.U);
-    const bool wrap_mod = a.periodic && nd < P;
+    const LT* U = Ub;
+    const bool wrap_mod = periodic && nd < P;
     for (int e = threadIdx.x; e < TL * P; e += blockDim.x) {
         int l, s;
         if (DIR == 0) { s = e % P; l = e / P; } else { l = e % TL; s = e / TL; }
         if (l >= lcount) continue;
         int p = pos0 - GHOST + s;
-        if (a.periodic) {
+        if (periodic) {
             if (wrap_mod) { p %= nd; if (p < 0) p += nd; }
             else p = p < 0 ? p + nd : (p >= nd ? p - nd : p);
         } else {
@@ -271,14 +331,14 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR>::MIN_CTAS) sweep_ker
     }
     if constexpr (kAsync) cp_async_commit();   // group: staged nodes
     if constexpr (kAsyncStage) {
-        if (a.dt != nullptr && *a.dt == 0.0) {
+        if (dtp != nullptr && *dtp == 0.0) {
             cp_async_wait<0>();
             return;
         }
     }
     if constexpr (kPre) {
         if (a.accumulate) {                    // group: the L values this tile adds to
-            const T* Lg = reinterpret_cast<const T*>(a.L);
+            const T* Lg = Lb;
             for (int e = threadIdx.x; e < TL * TS; e += blockDim.x) {
                 int l, t;
                 if (DIR == 0) { t = e % TS; l = e / TS; } else { l = e % TL; t = e / TL; }
@@ -328,10 +388,7 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR>::MIN_CTAS) sweep_ker
     __syncthreads();
 
     // (3) Eq. 3 at nodes pos0 .. pos0 + tcount - 1
-    T* L = reinterpret_cast<T*>(a.L);
-    T ih;
-    if constexpr (sizeof(T) == 8) ih = a.inv_h;
-    else ih = a.inv_hf;
+    T* L = Lb;
     for (int e = threadIdx.x; e < TL * TS; e += blockDim.x) {
         int l, t;
         if (DIR == 0) { t = e % TS; l = e / TS; } else { l = e % TL; t = e / TL; }

@@ -204,3 +204,195 @@ def step_rk3_noalloc(grid, gamma, params, U, dt=0.0, want_dt=False, stream=None)
     check(fn(C.byref(grid), float(gamma), C.byref(params), _ptr(U), float(dt),
              C.byref(d) if want_dt else None, _stream(stream)))
     return d.value if want_dt else None
+
+
+class Batch:
+    """A wcns_batch: many independent grids of one dimension and precision
+    advanced together (per-instance sizes, boundary rules, time steps and
+    end times)."""
+
+    def __init__(self, ndim, max_nodes, max_instances, gamma=1.4, **params):
+        L = lib()
+        L.wcns_batch_create.argtypes = [C.c_int, C.c_double, C.POINTER(SchemeParams), C.c_longlong, C.c_int,
+                                        C.POINTER(C.c_void_p)]
+        L.wcns_batch_destroy.argtypes = [C.c_void_p]
+        L.wcns_batch_bytes.argtypes = [C.c_void_p]
+        L.wcns_batch_bytes.restype = C.c_size_t
+        L.wcns_batch_add.argtypes = [C.c_void_p, C.POINTER(Grid), C.c_void_p, C.c_int, C.c_double,
+                                     C.POINTER(C.c_int), C.c_void_p]
+        L.wcns_batch_remove.argtypes = [C.c_void_p, C.c_int]
+        L.wcns_batch_step.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_void_p]
+        L.wcns_batch_run.argtypes = [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int), C.c_void_p]
+        L.wcns_batch_read.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_double),
+                                      C.POINTER(C.c_int), C.c_void_p]
+        for f in ("wcns_batch_create", "wcns_batch_destroy", "wcns_batch_add", "wcns_batch_remove",
+                  "wcns_batch_step", "wcns_batch_run", "wcns_batch_read"):
+            getattr(L, f).restype = C.c_int
+        self.ndim = ndim
+        self.nv = ndim + 2
+        self.params = default_params(**params)
+        h = C.c_void_p()
+        check(L.wcns_batch_create(ndim, gamma, C.byref(self.params), int(max_nodes), int(max_instances), C.byref(h)))
+        self.h = h
+        self.grids = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            check(lib().wcns_batch_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def nbytes(self):
+        return lib().wcns_batch_bytes(self.h)
+
+    def add(self, pb, U0=None, t_end=None, stream=None):
+        """Add a Problem (inputs.Problem); U0: a CUDA tensor or a numpy array
+        (defaults to pb.U0).  Returns the slot."""
+        import numpy as np
+        g = make_grid(pb.ndim, pb.n, pb.lo, pb.hi, pb.periodic)
+        U0 = pb.U0 if U0 is None else U0
+        slot = C.c_int()
+        if isinstance(U0, np.ndarray):
+            U0 = np.ascontiguousarray(U0, dtype=np.float64)
+            check(lib().wcns_batch_add(self.h, C.byref(g), U0.ctypes.data_as(C.c_void_p), 0,
+                                       float(pb.t_end if t_end is None else t_end), C.byref(slot), _stream(stream)))
+        else:
+            check(lib().wcns_batch_add(self.h, C.byref(g), _ptr(U0), 1,
+                                       float(pb.t_end if t_end is None else t_end), C.byref(slot), _stream(stream)))
+        self.grids[slot.value] = (pb.ndim, tuple(pb.n))
+        return slot.value
+
+    def remove(self, slot):
+        check(lib().wcns_batch_remove(self.h, int(slot)))
+        self.grids.pop(slot, None)
+
+    def step(self, nsteps=1, stream=None):
+        a = C.c_int()
+        check(lib().wcns_batch_step(self.h, int(nsteps), C.byref(a), _stream(stream)))
+        return a.value
+
+    def run(self, max_steps=10 ** 9, check_every=32, stream=None):
+        s = C.c_int()
+        check(lib().wcns_batch_run(self.h, int(min(max_steps, 2 ** 31 - 1)), int(check_every), C.byref(s),
+                                   _stream(stream)))
+        return s.value
+
+    def read(self, slot, out=None, stream=None):
+        """Returns (U as a numpy array or the given CUDA tensor, t, steps)."""
+        import numpy as np
+        t = C.c_double()
+        st = C.c_int()
+        nd, n = self.grids[slot]
+        shape = (nd + 2,) + tuple(reversed(n))
+        if out is None:
+            host = np.empty(shape, dtype=np.float64)
+            check(lib().wcns_batch_read(self.h, int(slot), host.ctypes.data_as(C.c_void_p), 0, C.byref(t),
+                                        C.byref(st), _stream(stream)))
+            return host, t.value, st.value
+        check(lib().wcns_batch_read(self.h, int(slot), _ptr(out), 1, C.byref(t), C.byref(st), _stream(stream)))
+        return out, t.value, st.value
+
+
+class Request(C.Structure):
+    _fields_ = [("grid", Grid), ("gamma", C.c_double), ("params", SchemeParams),
+                ("U0", C.POINTER(C.c_double)), ("t_end", C.c_double), ("tag", C.c_uint64)]
+
+
+class Result(C.Structure):
+    _fields_ = [("ticket", C.c_uint64), ("tag", C.c_uint64), ("status", C.c_int), ("ndim", C.c_int),
+                ("n", C.c_int * 3), ("precision", C.c_int), ("t", C.c_double), ("steps", C.c_int),
+                ("U", C.POINTER(C.c_double)), ("t_submit", C.c_double), ("t_admit", C.c_double),
+                ("t_done", C.c_double)]
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_instances_per_class", C.c_int),
+                ("max_nodes_per_class", C.c_longlong), ("steps_per_tick", C.c_int)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("queued", C.c_int), ("max_queue", C.c_int), ("max_running", C.c_int),
+                ("admitted", C.c_longlong), ("completed", C.c_longlong), ("ticks", C.c_longlong),
+                ("steps", C.c_longlong), ("bytes_reserved", C.c_size_t)]
+
+
+class Server:
+    """A wcns_server: continuous batching of solve requests on the current
+    CUDA device.  submit() queues a problem; poll() returns finished ones as
+    dicts with the final state (numpy), time, steps and timestamps."""
+
+    def __init__(self, hbm_budget_bytes=8 << 30, max_instances_per_class=256, max_nodes_per_class=0,
+                 steps_per_tick=16):
+        L = lib()
+        L.wcns_server_default_config.argtypes = [C.POINTER(ServerConfig)]
+        L.wcns_server_create.argtypes = [C.POINTER(ServerConfig), C.POINTER(C.c_void_p)]
+        L.wcns_server_destroy.argtypes = [C.c_void_p]
+        L.wcns_batch_submit.argtypes = [C.c_void_p, C.POINTER(Request), C.POINTER(C.c_uint64)]
+        L.wcns_serve_poll.argtypes = [C.c_void_p, C.POINTER(Result), C.c_int, C.POINTER(C.c_int), C.c_int]
+        L.wcns_result_free.argtypes = [C.POINTER(Result)]
+        L.wcns_server_stats.argtypes = [C.c_void_p, C.POINTER(ServerStats)]
+        for f in ("wcns_server_create", "wcns_server_destroy", "wcns_batch_submit", "wcns_serve_poll",
+                  "wcns_server_stats"):
+            getattr(L, f).restype = C.c_int
+        cfg = ServerConfig(int(hbm_budget_bytes), int(max_instances_per_class), int(max_nodes_per_class),
+                           int(steps_per_tick))
+        h = C.c_void_p()
+        check(L.wcns_server_create(C.byref(cfg), C.byref(h)))
+        self.h = h
+        self.shapes = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            check(lib().wcns_server_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, pb, tag=0, t_end=None, **params):
+        import numpy as np
+        U0 = np.ascontiguousarray(pb.U0, dtype=np.float64)
+        req = Request()
+        req.grid = make_grid(pb.ndim, pb.n, pb.lo, pb.hi, pb.periodic)
+        req.gamma = pb.gamma
+        req.params = default_params(**params)
+        req.U0 = U0.ctypes.data_as(C.POINTER(C.c_double))
+        req.t_end = float(pb.t_end if t_end is None else t_end)
+        req.tag = int(tag)
+        ticket = C.c_uint64()
+        check(lib().wcns_batch_submit(self.h, C.byref(req), C.byref(ticket)))
+        self.shapes[ticket.value] = (pb.ndim + 2,) + tuple(reversed(pb.n[:pb.ndim]))
+        return ticket.value
+
+    def poll(self, max_results=64, timeout_us=0):
+        import numpy as np
+        arr = (Result * max_results)()
+        n = C.c_int()
+        st = lib().wcns_serve_poll(self.h, arr, max_results, C.byref(n), int(timeout_us))
+        if st not in (OK, ERR_TIMEOUT):
+            check(st)
+        out = []
+        for k in range(n.value):
+            r = arr[k]
+            shape = self.shapes.pop(r.ticket, None)
+            U = None
+            if r.U and shape is not None:
+                U = np.ctypeslib.as_array(r.U, shape=(int(np.prod(shape)),)).reshape(shape).copy()
+            out.append(dict(ticket=r.ticket, tag=r.tag, status=r.status, t=r.t, steps=r.steps, U=U,
+                            t_submit=r.t_submit, t_admit=r.t_admit, t_done=r.t_done, precision=r.precision))
+            lib().wcns_result_free(C.byref(arr[k]))
+        return out
+
+    def stats(self):
+        s = ServerStats()
+        check(lib().wcns_server_stats(self.h, C.byref(s)))
+        return {f: getattr(s, f) for f, _ in ServerStats._fields_}
