@@ -327,7 +327,20 @@ def ours_arm(args, world, rank, local):
         el64 = time_steps(torch, s64, U64, k64)
         fp64_line = {"value": nodes * 3 * k64 / el64, "unit": UNIT, "ms_per_step": el64 / k64 * 1e3,
                      "steps": k64, "dtype": "f64"}
-        del U64
+        # FP32 bulk vs FP64 (which reproduces the FP64 oracle bit for bit):
+        # three steps of the same fixed size from the initial state
+        Ua = torch.from_numpy(pb.U0).to(dev)
+        Ub = torch.from_numpy(pb.U0).to(dev)
+        dt = s64.cfl_dt(Ua)
+        for _ in range(3):
+            s64.step(Ua, dt)
+            solver.step(Ub, dt)
+        torch.cuda.synchronize()
+        d = (Ub - Ua).abs().reshape(pb.nv, -1).sum(dim=1)
+        tot = Ua.abs().reshape(pb.nv, -1).sum(dim=1)
+        tot[1:-1] = tot[1:-1].max()      # momenta against the largest momentum total
+        fp64_line["fp32_l1_rel_error_3_steps"] = float((d / tot).max())
+        del U64, Ua, Ub
         s64.close()
 
     cpu = None
@@ -388,12 +401,29 @@ def batch_arm(args):
     torch.cuda.synchronize()
     el = (time.perf_counter() - t0) / 3
     out["plain_fp64"] = {"value": sum(p.cells for p in sub) * 3 / el, "ms_per_step_64_instances": el * 1e3}
+    # FP32 vs FP64 (= the oracle bit for bit) for 64 instances run to t = 0.2
+    import numpy as np
+    sub = pbs[:64]
+    res = {}
+    for prec in (wcns.FP32, wcns.FP64):
+        b = wcns.Batch(1, max_nodes=sum(p.cells for p in sub), max_instances=len(sub), precision=prec)
+        sl = [b.add(pb, t_end=0.2) for pb in sub]
+        b.run(check_every=64)
+        res[prec] = [b.read(k)[0] for k in sl]
+        b.close()
+    def rel(a, c):
+        tot = np.sum(np.abs(c), axis=1)
+        tot[1:-1] = tot[1:-1].max()
+        return float(np.max(np.sum(np.abs(a - c), axis=1) / tot))
+    l1 = max(rel(a, c) for a, c in zip(res[wcns.FP32], res[wcns.FP64]))
+    out["fp32"]["l1_rel_error_vs_fp64_t0.2_64_instances"] = l1
     print(json.dumps({
         "metric": METRIC, "value": out["fp32"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": out["fp32"]["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "batched_shu_osher_1d_4096_instances", "nodes": nodes, "seed": 1810,
                    "precision": "fp32 bulk", "launch": "one graph per RK3 step, one launch per stage kernel"},
+        "fp32_l1_rel_error_vs_fp64": out["fp32"]["l1_rel_error_vs_fp64_t0.2_64_instances"],
         "batched_fp64": out["fp64"], "plain_fp64_one_instance_per_launch": out["plain_fp64"]}))
 
 
