@@ -95,6 +95,70 @@ __device__ __forceinline__ int select_fp32(const float s[5], float inv_sc, float
     return flags;
 }
 
+// Cutoff decision from the three (rescaled) indicators of one stencil; the
+// same arithmetic as select_fp32 after its beta_k.
+__device__ __forceinline__ int cut_fp32(float b0, float b1, float b2, float eps_s, const SchemeConst& K)
+{
+    const float tau = fabsf(b0 - b2);
+    const float bm = fminf(fminf(b0, b1), b2) + eps_s;
+    if (!(tau >= K.Kf * bm)) return 7;           // no cut possible (also tau == 0)
+    b0 += eps_s;
+    b1 += eps_s;
+    b2 += eps_s;
+    const float den = __frcp_rn(fmaf(K.Cf, bm, tau));
+    const float bb[3] = {b0, b1, b2};
+    float sk[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float r = fminf(1.0f, (bm * __frcp_rn(bb[k])) * (fmaf(K.Cf, bb[k], tau) * den));
+        float p = r;
+        for (int e = 1; e < K.q; ++e) p *= r;
+        sk[k] = p;
+    }
+    const float lim = K.CTf * (sk[0] + sk[1] + sk[2]);
+    int flags = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        if (!(sk[k] < lim)) flags |= 1 << k;
+    return flags;
+}
+
+// Both biased selections of one characteristic field of a face from its six
+// values s[0..5] = w_{j-2} .. w_{j+3}: the left-biased stencil is s[0..4], the
+// right-biased one the mirror s[5..1].  The values are rescaled once by
+// 1/sc, sc = max |s| (floored at FLT_MIN so an all-zero field keeps every
+// stencil without a branch), and the two second differences the mirrored
+// stencils share are formed once.
+__device__ __forceinline__ void select_pair_fp32(const float s[6], float sqrt_eps, const SchemeConst& K,
+                                                 int& fL, int& fR)
+{
+    float sc = 0.f;
+#pragma unroll
+    for (int m = 0; m < 6; ++m) sc = fmaxf(sc, fabsf(s[m]));
+    sc = fmaxf(sc, 1.17549435e-38f);
+    const float inv = __frcp_rn(sc);
+    const float e = sqrt_eps * inv;
+    const float eps_s = fmaxf(e * e, 1.17549435e-38f);
+    float t[6];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) t[m] = s[m] * inv;
+    // second differences: (t0 t1 t2), (t1 t2 t3), (t2 t3 t4), (t3 t4 t5)
+    const float a2 = t[0] - 2.0f * t[1] + t[2];
+    const float b2 = t[1] - 2.0f * t[2] + t[3];
+    const float c2 = t[2] - 2.0f * t[3] + t[4];
+    const float d2 = t[3] - 2.0f * t[4] + t[5];
+    // left-biased: centre t2
+    const float l0 = 0.5f * (t[0] - 4.0f * t[1] + 3.0f * t[2]);
+    const float l1 = 0.5f * (t[3] - t[1]);
+    const float l2 = 0.5f * (-3.0f * t[2] + 4.0f * t[3] - t[4]);
+    // right-biased (mirror): centre t3
+    const float r0 = 0.5f * (t[5] - 4.0f * t[4] + 3.0f * t[3]);
+    const float r1 = 0.5f * (t[2] - t[4]);
+    const float r2 = 0.5f * (-3.0f * t[3] + 4.0f * t[2] - t[1]);
+    fL = cut_fp32(l0 * l0 + a2 * a2, l1 * l1 + b2 * b2, l2 * l2 + c2 * c2, eps_s, K);
+    fR = cut_fp32(r0 * r0 + d2 * d2, r1 * r1 + c2 * c2, r2 * r2 + b2 * b2, eps_s, K);
+}
+
 // Eq. 12 with the weights of Eq. 19, as the equivalent Table-1 stencil.
 // The all-retained row (Eq. 7) is inlined; reduced rows come from constant
 // memory (only cut faces take that branch).

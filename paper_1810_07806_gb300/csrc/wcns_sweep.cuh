@@ -162,20 +162,13 @@ __device__ __forceinline__ void face_flux(float (&u)[6][ND + 2], const SweepArgs
     float wL[NV], wR[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-        float sl[5], sr[5];
-        float sc = 0.f;
+        float sl[5], sr[5], s6[6];
 #pragma unroll
-        for (int m = 0; m < 6; ++m) sc = fmaxf(sc, fabsf(u[m][k]));
+        for (int m = 0; m < 6; ++m) s6[m] = u[m][k];
 #pragma unroll
         for (int m = 0; m < 5; ++m) { sl[m] = u[m][k]; sr[m] = u[5 - m][k]; }
-        int fL = 7, fR = 7;
-        if (sc > 0.f) {
-            const float inv = __frcp_rn(sc);
-            const float e = a.sqrt_eps_f * inv;
-            const float eps_s = fmaxf(e * e, 1.17549435e-38f);
-            fL = select_fp32(sl, inv, eps_s, a.K);
-            fR = select_fp32(sr, inv, eps_s, a.K);
-        }
+        int fL, fR;
+        select_pair_fp32(s6, a.sqrt_eps_f, a.K, fL, fR);
         wL[k] = interp_row<float>(fL, sl);
         wR[k] = interp_row<float>(fR, sr);
         fl[k] = (uint8_t)(fL | (fR << 3));
