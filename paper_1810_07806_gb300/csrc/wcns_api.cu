@@ -25,7 +25,8 @@ struct wcns_handle {
     int device = 0;
     // device scratch
     void* L = nullptr;          // RHS, handle precision
-    void* U1 = nullptr;         // FP64: stage state; FP32: stage sweep input (float)
+    void* U1 = nullptr;         // FP64: stage state; FP32: stage sweep input A (float)
+    float* S2 = nullptr;        // FP32: second stage input buffer B
     float* D = nullptr;         // FP32: stage increment
     StepScalars* sc = nullptr;
     long long* fallback = nullptr;
@@ -174,10 +175,10 @@ wcns_status wcns_create(const wcns_grid* g, double gamma, const wcns_scheme_para
     const size_t M = (size_t)h->nv * h->N;
     const size_t w = fp32 ? 4 : 8;
     h->nblk_cons = conserved_blocks(h->N);
-    size_t bytes = M * w * 2 + (fp32 ? M * 4 : 0) + sizeof(StepScalars) + 64 +
+    size_t bytes = M * w * 2 + (fp32 ? M * 8 : 0) + sizeof(StepScalars) + 64 +
                    sizeof(double) * (h->nblk_cons + 1) * h->nv;
     char* base = nullptr;
-    e = cudaMalloc((void**)&base, bytes + 2048);
+    e = cudaMalloc((void**)&base, bytes + 4096);
     if (e != cudaSuccess) {
         delete h;
         cudaGetLastError();
@@ -188,10 +189,11 @@ wcns_status wcns_create(const wcns_grid* g, double gamma, const wcns_scheme_para
     h->L = carve(M * w);
     h->U1 = carve(M * w);
     if (fp32) h->D = (float*)carve(M * 4);
+    if (fp32) h->S2 = (float*)carve(M * 4);
     h->sc = (StepScalars*)carve(sizeof(StepScalars));
     h->fallback = (long long*)carve(64);
     h->partials = (double*)carve(sizeof(double) * (h->nblk_cons + 1) * h->nv);
-    h->bytes = bytes + 2048;
+    h->bytes = bytes + 4096;
     e = cudaMemset(h->sc, 0, sizeof(StepScalars));
     if (e == cudaSuccess) e = cudaMemset(h->fallback, 0, 64);
     if (e != cudaSuccess) { cudaFree(base); delete h; return cuda_fail(e, "cudaMemset"); }
@@ -226,7 +228,6 @@ static size_t flags_offset(const wcns_handle* h, int d)
     return s;
 }
 
-// Evaluate L = RHS(U) with all directions; U is LT, L is the handle precision.
 static cudaError_t timed_event(wcns_handle* h, cudaStream_t s)
 {
     if (h->ev_used == h->ev.size()) {
@@ -238,11 +239,17 @@ static cudaError_t timed_event(wcns_handle* h, cudaStream_t s)
     return cudaEventRecord(h->ev[h->ev_used++], s);
 }
 
+// Evaluate L = RHS(U) with all directions; U and L in the handle precision.
+// FP32 steps sweep the directions in reverse (z, y, x) and let the x sweep
+// apply the SSP-RK3 stage combination (fuse_stage 1..3): U0 is the FP64
+// state, D the FP32 increment, S_out the next stage's input.
 static cudaError_t run_rhs(wcns_handle* h, const void* U, void* L, uint8_t* flags,
-                           const double* dtp, cudaStream_t s)
+                           const double* dtp, cudaStream_t s, int fuse_stage = 0,
+                           double* U0 = nullptr, float* S_out = nullptr)
 {
     const bool fp32 = h->p.precision == WCNS_FP32;
-    for (int d = 0; d < h->ndim; ++d) {
+    for (int k = 0; k < h->ndim; ++k) {
+        const int d = fuse_stage ? h->ndim - 1 - k : k;
         SweepArgs a{};
         a.U = U;
         a.L = L;
@@ -253,12 +260,18 @@ static cudaError_t run_rhs(wcns_handle* h, const void* U, void* L, uint8_t* flag
         a.periodic = h->periodic[d];
         a.inv_h = h->inv_h[d];
         a.inv_hf = (float)h->inv_h[d];
-        a.accumulate = d > 0;
+        a.accumulate = k > 0;
         a.flags = flags ? flags + flags_offset(h, d) : nullptr;
         a.fallback = h->fallback;
         a.dt = dtp;
         a.K = h->K;
         a.sqrt_eps_f = h->sqrt_eps_f;
+        if (fuse_stage && d == 0) {
+            a.fuse_stage = fuse_stage;
+            a.U0 = U0;
+            a.D = h->D;
+            a.S_out = S_out;
+        }
         cudaError_t e;
         if (h->profiling && (e = timed_event(h, s)) != cudaSuccess) return e;
         e = fp32 ? launch_sweep_fp32(h->ndim, d, h->p.flux, a, s)
@@ -280,10 +293,8 @@ wcns_status wcns_rhs(wcns_handle* h, const void* U, void* L, uint8_t* flags, voi
 }
 
 // The three stages of one step after dt has been placed in h->sc.  In FP32
-// mode the first stage reads float(U) from the stage buffer: converted here
-// unless the caller knows the previous step of this handle left it there
-// (s_current, only inside wcns_advance where U is not touched between steps).
-static cudaError_t run_stages(wcns_handle* h, double* U, cudaStream_t s, bool s_current = false)
+// mode the first stage reads float(U), converted here.
+static cudaError_t run_stages(wcns_handle* h, double* U, cudaStream_t s)
 {
     const long long M = (long long)h->nv * h->N;
     const double* dtp = &h->sc->dt;
@@ -298,15 +309,15 @@ static cudaError_t run_stages(wcns_handle* h, double* U, cudaStream_t s, bool s_
         if ((e = run_rhs(h, U1, L, nullptr, dtp, s)) != cudaSuccess) return e;
         return launch_rk_fp64(3, U, U1, L, M, h->sc, s);
     }
-    float* S = (float*)h->U1;
+    // FP32: stage inputs alternate A -> B -> A; the x sweep of each stage
+    // writes the next one (and, in stage 3, the FP64 state)
+    float* A = (float*)h->U1;
+    float* B = h->S2;
     float* L = (float*)h->L;
-    if (!s_current && (e = launch_to_fp32(U, S, M, h->sc, s)) != cudaSuccess) return e;
-    if ((e = run_rhs(h, S, L, nullptr, dtp, s)) != cudaSuccess) return e;
-    if ((e = launch_rk_fp32(1, U, S, h->D, L, M, h->sc, s)) != cudaSuccess) return e;
-    if ((e = run_rhs(h, S, L, nullptr, dtp, s)) != cudaSuccess) return e;
-    if ((e = launch_rk_fp32(2, U, S, h->D, L, M, h->sc, s)) != cudaSuccess) return e;
-    if ((e = run_rhs(h, S, L, nullptr, dtp, s)) != cudaSuccess) return e;
-    return launch_rk_fp32(3, U, S, h->D, L, M, h->sc, s);
+    if ((e = launch_to_fp32(U, A, M, h->sc, s)) != cudaSuccess) return e;
+    if ((e = run_rhs(h, A, L, nullptr, dtp, s, 1, U, B)) != cudaSuccess) return e;
+    if ((e = run_rhs(h, B, L, nullptr, dtp, s, 2, U, A)) != cudaSuccess) return e;
+    return run_rhs(h, A, L, nullptr, dtp, s, 3, U, B);
 }
 
 // The time step of a step: the fixed-order FP64 rule for the FP64 path (bit
@@ -358,7 +369,7 @@ wcns_status wcns_advance(wcns_handle* h, void* U, double t_end, int max_steps, i
         const int batch = left < check ? (int)left : check;
         for (int k = 0; k < batch; ++k) {
             CK(step_cfl(h, (const double*)U, 1, s), "cfl");
-            CK(run_stages(h, (double*)U, s, issued + k > 0), "rk3 stages");
+            CK(run_stages(h, (double*)U, s), "rk3 stages");
         }
         issued += batch;
         CK(cudaMemcpyAsync(&cur, h->sc, sizeof cur, cudaMemcpyDeviceToHost, s), "clock copy");
@@ -435,9 +446,11 @@ wcns_status wcns_profile_read(wcns_handle* h, double* sweep_ms, long long* sweep
 int wcns_launches_per_step(const wcns_handle* h, int cfl_step)
 {
     if (!h) return 0;
-    // clock reset + (CFL reduction and finalize | set dt) + 3 x (sweeps + stage combine)
-    // + the FP32 path's conversion of the state for the first stage
-    return 1 + (cfl_step ? 2 : 1) + 3 * (h->ndim + 1) + (h->p.precision == WCNS_FP32 ? 1 : 0);
+    // clock reset + (CFL reduction and finalize | set dt) + stages: FP64 3 x
+    // (sweeps + stage combine); FP32 one state conversion + 3 x sweeps (the
+    // last sweep of each stage applies the combination)
+    const int stages = h->p.precision == WCNS_FP32 ? 1 + 3 * h->ndim : 3 * (h->ndim + 1);
+    return 1 + (cfl_step ? 2 : 1) + stages;
 }
 
 }  // extern "C"

@@ -144,36 +144,6 @@ __global__ void __launch_bounds__(256) batch_rk_fp64_kernel(double* __restrict__
     }
 }
 
-template <int STAGE>
-__global__ void __launch_bounds__(256) batch_rk_fp32_kernel(double* __restrict__ U0, float* __restrict__ S,
-                                                            float* __restrict__ D, const float* __restrict__ L,
-                                                            const ElemChunk* __restrict__ chunks,
-                                                            const StepScalars* __restrict__ sc)
-{
-    const ElemChunk ch = chunks[blockIdx.x];
-    const double dtd = sc[ch.inst].dt;
-    if (dtd == 0.0) return;
-    const float dt = (float)dtd;
-    for (int k = threadIdx.x; k < ch.count; k += blockDim.x) {
-        const long long i = ch.begin + k;
-        const float l = L[i];
-        if (STAGE == 1) {
-            const float d = dt * l;
-            D[i] = d;
-            S[i] = __double2float_rn(U0[i]) + d;
-        } else if (STAGE == 2) {
-            const float d = 0.25f * fmaf(dt, l, D[i]);
-            D[i] = d;
-            S[i] = __double2float_rn(U0[i]) + d;
-        } else {
-            const float d = (2.0f / 3.0f) * fmaf(dt, l, D[i]);
-            const double u = U0[i] + (double)d;
-            U0[i] = u;
-            S[i] = __double2float_rn(u);
-        }
-    }
-}
-
 __global__ void __launch_bounds__(256) batch_to_fp32_kernel(const double* __restrict__ U, float* __restrict__ S,
                                                             const ElemChunk* __restrict__ chunks,
                                                             const StepScalars* __restrict__ sc)
@@ -217,7 +187,8 @@ struct wcns_batch {
     int cap_slots = 0;
     // arenas and per-instance clocks
     double* U = nullptr;
-    void* S = nullptr;      // FP64: stage state; FP32: stage input (float)
+    void* S = nullptr;      // FP64: stage state; FP32: stage input A (float)
+    float* S2 = nullptr;    // FP32: stage input B
     void* L = nullptr;
     float* D = nullptr;
     StepScalars* sc = nullptr;
@@ -365,14 +336,18 @@ wcns_status rebuild(wcns_batch* b)
     return WCNS_OK;
 }
 
-cudaError_t sweeps(wcns_batch* b, const void* Uin, void* L, cudaStream_t s)
+cudaError_t sweeps(wcns_batch* b, const void* Uin, void* L, cudaStream_t s, int fuse_stage = 0,
+                   float* S_out = nullptr)
 {
     const bool fp32 = b->precision == WCNS_FP32;
-    for (int d = 0; d < b->ndim; ++d) {
+    for (int k = 0; k < b->ndim; ++k) {
+        // FP32: z, y, x with the stage combination in the x sweep (as the
+        // single-grid FP32 step); FP64: x, y, z, the oracle's order
+        const int d = fuse_stage ? b->ndim - 1 - k : k;
         SweepArgs a{};
         a.U = Uin;
         a.L = L;
-        a.accumulate = d > 0;
+        a.accumulate = k > 0;
         a.fallback = b->fallback;
         a.K = b->K;
         a.sqrt_eps_f = b->sqrt_eps_f;
@@ -380,6 +355,12 @@ cudaError_t sweeps(wcns_batch* b, const void* Uin, void* L, cudaStream_t s)
         a.tiles = b->d_tiles[d];
         a.inst_dt = &b->sc[0].dt;
         a.dt_stride = kDtStride;
+        if (fuse_stage && d == 0) {
+            a.fuse_stage = fuse_stage;
+            a.U0 = b->U;
+            a.D = b->D;
+            a.S_out = S_out;
+        }
         cudaError_t e = fp32 ? launch_sweep_batch_fp32(b->ndim, d, b->flux, a, b->ntiles[d], s)
                              : launch_sweep_batch_fp64(b->ndim, d, b->flux, a, b->ntiles[d], s);
         if (e != cudaSuccess) return e;
@@ -420,15 +401,15 @@ cudaError_t step_sequence(wcns_batch* b, cudaStream_t s)
         if ((e = sweeps(b, U1, L, s)) != cudaSuccess) return e;
         batch_rk_fp64_kernel<3><<<b->nech, 256, 0, s>>>(b->U, U1, L, b->d_ech, b->sc);
     } else {
-        float* S = (float*)b->S;
+        // stage inputs A -> B -> A; the x sweep of each stage applies the
+        // stage combination (stage 3 also updates the FP64 state)
+        float* A = (float*)b->S;
+        float* B = b->S2;
         float* L = (float*)b->L;
-        batch_to_fp32_kernel<<<b->nech, 256, 0, s>>>(b->U, S, b->d_ech, b->sc);
-        if ((e = sweeps(b, S, L, s)) != cudaSuccess) return e;
-        batch_rk_fp32_kernel<1><<<b->nech, 256, 0, s>>>(b->U, S, b->D, L, b->d_ech, b->sc);
-        if ((e = sweeps(b, S, L, s)) != cudaSuccess) return e;
-        batch_rk_fp32_kernel<2><<<b->nech, 256, 0, s>>>(b->U, S, b->D, L, b->d_ech, b->sc);
-        if ((e = sweeps(b, S, L, s)) != cudaSuccess) return e;
-        batch_rk_fp32_kernel<3><<<b->nech, 256, 0, s>>>(b->U, S, b->D, L, b->d_ech, b->sc);
+        batch_to_fp32_kernel<<<b->nech, 256, 0, s>>>(b->U, A, b->d_ech, b->sc);
+        if ((e = sweeps(b, A, L, s, 1, B)) != cudaSuccess) return e;
+        if ((e = sweeps(b, B, L, s, 2, A)) != cudaSuccess) return e;
+        if ((e = sweeps(b, A, L, s, 3, B)) != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }
@@ -496,12 +477,13 @@ wcns_status wcns_batch_create(int ndim, double gamma, const wcns_scheme_params* 
     }
     const size_t w = fp32 ? 4 : 8;
     const size_t M = (size_t)b->cap_elems;
-    b->bytes = M * 8 + M * w * 2 + (fp32 ? M * 4 : 0) + sizeof(StepScalars) * max_instances +
+    b->bytes = M * 8 + M * w * 2 + (fp32 ? M * 8 : 0) + sizeof(StepScalars) * max_instances +
                (sizeof(BatchInst) + sizeof(int)) * max_instances + 64;
     e = cudaMalloc((void**)&b->U, M * 8);
     if (e == cudaSuccess) e = cudaMalloc(&b->S, M * w);
     if (e == cudaSuccess) e = cudaMalloc(&b->L, M * w);
     if (e == cudaSuccess && fp32) e = cudaMalloc((void**)&b->D, M * 4);
+    if (e == cudaSuccess && fp32) e = cudaMalloc((void**)&b->S2, M * 4);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->sc, sizeof(StepScalars) * max_instances);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->active, 64);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->fallback, 64);
@@ -530,6 +512,7 @@ wcns_status wcns_batch_destroy(wcns_batch* b)
     cudaFree(b->S);
     cudaFree(b->L);
     cudaFree(b->D);
+    cudaFree(b->S2);
     cudaFree(b->sc);
     cudaFree(b->active);
     cudaFree(b->fallback);

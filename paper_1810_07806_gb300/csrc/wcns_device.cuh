@@ -50,53 +50,14 @@ struct SchemeConst {
     float gammaf, gm1f;  // gamma, gamma - 1 in float
 };
 
-// FP32 selection.  chi_k is invariant under s -> s/sc except through eps, so
-// the stencil is rescaled by sc = max |s_m| (beta, tau become O(1) and cannot
-// underflow) and eps becomes max(eps/sc^2, FLT_MIN).  With b_k = beta_k + eps
-// and m = argmin b (the largest gamma), the ratio g_k / g_m is formed as
-//   (b_m / b_k) * (C b_k + tau) / (C b_m + tau),
+// FP32 cutoff decision from the three rescaled indicators of one stencil.
+// chi_k is invariant under s -> s/sc except through eps, so the stencil is
+// rescaled (beta, tau become O(1) and cannot underflow) and eps becomes
+// max(eps/sc^2, FLT_MIN).  With b_k = beta_k + eps and m = argmin b (the
+// largest gamma), g_k / g_m is formed as (b_m / b_k)(C b_k + tau)/(C b_m + tau),
 // where every factor is bounded (the literal tau / b_k overflows FP32 when b_k
 // sits at the eps floor), and chi_k < C_T is tested as s_k < C_T sum s with
 // s_k = (g_k / g_m)^q.  tau = 0 keeps every stencil without dividing.
-__device__ __forceinline__ int select_fp32(const float s[5], float inv_sc, float eps_s,
-                                           const SchemeConst& K)
-{
-    float t[5];
-#pragma unroll
-    for (int m = 0; m < 5; ++m) t[m] = s[m] * inv_sc;
-    float D1[3], D2[3], b[3];
-    D1[0] = 0.5f * (t[0] - 4.0f * t[1] + 3.0f * t[2]);
-    D1[1] = 0.5f * (t[3] - t[1]);
-    D1[2] = 0.5f * (-3.0f * t[2] + 4.0f * t[3] - t[4]);
-    D2[0] = t[0] - 2.0f * t[1] + t[2];
-    D2[1] = t[1] - 2.0f * t[2] + t[3];
-    D2[2] = t[2] - 2.0f * t[3] + t[4];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) b[k] = D1[k] * D1[k] + D2[k] * D2[k];
-    const float tau = fabsf(b[0] - b[2]);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) b[k] += eps_s;
-    const float bm = fminf(fminf(b[0], b[1]), b[2]);
-    if (!(tau >= K.Kf * bm)) return 7;           // no cut possible (also tau == 0)
-    const float den = __frcp_rn(fmaf(K.Cf, bm, tau));
-    float sk[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const float r = fminf(1.0f, (bm * __frcp_rn(b[k])) * (fmaf(K.Cf, b[k], tau) * den));
-        float p = r;
-        for (int e = 1; e < K.q; ++e) p *= r;
-        sk[k] = p;
-    }
-    const float lim = K.CTf * (sk[0] + sk[1] + sk[2]);
-    int flags = 0;
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-        if (!(sk[k] < lim)) flags |= 1 << k;
-    return flags;
-}
-
-// Cutoff decision from the three (rescaled) indicators of one stencil; the
-// same arithmetic as select_fp32 after its beta_k.
 __device__ __forceinline__ int cut_fp32(float b0, float b1, float b2, float eps_s, const SchemeConst& K)
 {
     const float tau = fabsf(b0 - b2);
@@ -111,8 +72,14 @@ __device__ __forceinline__ int cut_fp32(float b0, float b1, float b2, float eps_
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const float r = fminf(1.0f, (bm * __frcp_rn(bb[k])) * (fmaf(K.Cf, bb[k], tau) * den));
-        float p = r;
-        for (int e = 1; e < K.q; ++e) p *= r;
+        float p;
+        if (K.q == 6) {              // the paper's q: three multiplies, no loop
+            const float r2 = r * r;
+            p = r2 * r2 * r2;
+        } else {
+            p = r;
+            for (int e = 1; e < K.q; ++e) p *= r;
+        }
         sk[k] = p;
     }
     const float lim = K.CTf * (sk[0] + sk[1] + sk[2]);

@@ -39,9 +39,6 @@ cudaError_t launch_reset_clock(double t_end, StepScalars* sc, cudaStream_t s);
 // FP64 stage combinations (Shu-Osher SSP-RK3) over M = nv*N values.
 cudaError_t launch_rk_fp64(int stage, double* U0, double* U1, const double* L, long long M,
                            const StepScalars* sc, cudaStream_t s);
-// FP32 stages: increments relative to the FP64 base state U0.
-cudaError_t launch_rk_fp32(int stage, double* U0, float* S, float* D, const float* L, long long M,
-                           const StepScalars* sc, cudaStream_t s);
 // S = float(U) (skipped when *dt == 0, i.e. the run has finished).
 cudaError_t launch_to_fp32(const double* U, float* S, long long M, const StepScalars* sc, cudaStream_t s);
 cudaError_t launch_conserved(int nv, const double* U, long long N, double vol, double* partials,

@@ -223,50 +223,6 @@ cudaError_t launch_rk_fp64(int stage, double* U0, double* U1, const double* L, l
     return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- FP32 stages
-// Stage values are U^(s) = U0 + D^(s): the FP64 base carries the magnitude,
-// the FP32 increment D carries the stage update, so nothing of the update is
-// lost to the size of U.  S = float(U0) + D is the next sweep's input.
-//   D1 = dt L,  D2 = (D1 + dt L)/4,  U0 += 2/3 (D2 + dt L)   (FP64 accumulation)
-// The last stage also leaves float(U0) in S for the next step's first stage.
-template <int STAGE>
-__global__ void __launch_bounds__(256) rk_fp32_kernel(double* __restrict__ U0, float* __restrict__ S,
-                                                      float* __restrict__ D, const float* __restrict__ L,
-                                                      long long M, const StepScalars* sc)
-{
-    const double dtd = sc->dt;
-    if (dtd == 0.0) return;
-    const float dt = (float)dtd;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M;
-         i += (long long)gridDim.x * blockDim.x) {
-        const float l = L[i];
-        if (STAGE == 1) {
-            const float d = dt * l;
-            D[i] = d;
-            S[i] = __double2float_rn(U0[i]) + d;
-        } else if (STAGE == 2) {
-            const float d = 0.25f * fmaf(dt, l, D[i]);
-            D[i] = d;
-            S[i] = __double2float_rn(U0[i]) + d;
-        } else {
-            const float d = (2.0f / 3.0f) * fmaf(dt, l, D[i]);
-            const double u = U0[i] + (double)d;
-            U0[i] = u;
-            S[i] = __double2float_rn(u);   // the next step's first-stage input
-        }
-    }
-}
-
-cudaError_t launch_rk_fp32(int stage, double* U0, float* S, float* D, const float* L, long long M,
-                           const StepScalars* sc, cudaStream_t s)
-{
-    const int nb = stream_blocks(M);
-    if (stage == 1) rk_fp32_kernel<1><<<nb, 256, 0, s>>>(U0, S, D, L, M, sc);
-    else if (stage == 2) rk_fp32_kernel<2><<<nb, 256, 0, s>>>(U0, S, D, L, M, sc);
-    else rk_fp32_kernel<3><<<nb, 256, 0, s>>>(U0, S, D, L, M, sc);
-    return cudaGetLastError();
-}
-
 // S = float(U): the single-precision input of a step's first stage.
 __global__ void __launch_bounds__(256) to_fp32_kernel(const double* __restrict__ U, float* __restrict__ S,
                                                       long long M, const StepScalars* sc)

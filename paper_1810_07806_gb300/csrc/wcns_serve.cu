@@ -65,7 +65,7 @@ ClassKey key_of(const wcns_request& r)
 size_t bytes_per_node(int ndim, int precision)
 {
     const size_t nv = ndim + 2;
-    return nv * (8 + (precision == WCNS_FP32 ? 4 + 4 + 4 : 8 + 8));
+    return nv * (8 + (precision == WCNS_FP32 ? 4 + 4 + 4 + 4 : 8 + 8));
 }
 
 }  // namespace

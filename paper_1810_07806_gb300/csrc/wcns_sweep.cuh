@@ -55,6 +55,14 @@ struct SweepArgs {
     SchemeConst K;
     float sqrt_eps_f;         // sqrt(eps) in float, for the FP32 rescaled eps
     float inv_hf;             // 1 / h_DIR in float
+    // FP32 steps: the last sweep of a stage also applies the SSP-RK3 stage
+    // combination (stage 1..3; 0 = plain RHS).  U0 is the FP64 base state, D
+    // the FP32 increment, S_out the next stage's FP32 input (batch arrays in
+    // batched mode).
+    int fuse_stage;
+    double* U0;
+    float* D;
+    float* S_out;
     // batched mode only
     const BatchInst* insts;
     const BatchTile* tiles;
@@ -69,6 +77,11 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem)
 {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int NW>
@@ -86,9 +99,13 @@ struct TileGeom {
     static constexpr int MIN_CTAS = sizeof(T) == 4 ? 4 : 1;
     // FP32 sweeps that accumulate prefetch the TS nodes of L they update
     static constexpr bool PREFETCH_L = sizeof(T) == 4;
+    // The FP32 x sweep (the last of a step's stage) can fuse the stage
+    // combination: it prefetches the FP64 base state and the FP32 increment.
+    static constexpr bool FUSE = sizeof(T) == 4 && DIR == 0;
     static constexpr size_t smem_bytes()
     {
-        return sizeof(T) * (size_t)(ND + 2) * TL * (P + NF + (PREFETCH_L ? TS : 0));
+        return sizeof(T) * (size_t)(ND + 2) * TL * (P + NF + (PREFETCH_L ? TS : 0)) +
+               (FUSE ? (size_t)(ND + 2) * TL * TS * (sizeof(double) + sizeof(float)) : 0);
     }
 };
 
@@ -236,11 +253,19 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR>::MIN_CTAS) sweep_ker
     long long outer;
     const double* dtp;
     T ih;
+    double* U0b = a.U0;
+    float* Db = a.D;
+    float* Sob = a.S_out;
     if constexpr (BATCH) {
         const BatchTile bt = a.tiles[blockIdx.x];
         const BatchInst& I = a.insts[bt.inst];
         Ub = reinterpret_cast<const LT*>(a.U) + I.off;
         Lb = reinterpret_cast<T*>(a.L) + I.off;
+        if (a.fuse_stage) {
+            U0b += I.off;
+            Db += I.off;
+            Sob += I.off;
+        }
         N = I.N;
         nx = I.n[0];
         ny = I.n[1];
@@ -276,6 +301,9 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR>::MIN_CTAS) sweep_ker
     T* sS = reinterpret_cast<T*>(smem_raw);
     T* sF = sS + NV * TL * P;
     T* sL = sF + NV * TL * NF;   // prefetched L (FP32 accumulating sweeps)
+    // fused stage combination (FP32 x sweep): prefetched base state and increment
+    double* sU0 = reinterpret_cast<double*>(sL + (G::PREFETCH_L ? NV * TL * TS : 0));
+    float* sD = reinterpret_cast<float*>(sU0 + (G::FUSE ? NV * TL * TS : 0));
 
     long long sd;
     int lcount;
@@ -341,6 +369,20 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR>::MIN_CTAS) sweep_ker
                 for (int v = 0; v < NV; ++v) cp_async4(&sL[sidx<DIR, TL, TS>(v, l, t)], src + v * N);
             }
         }
+        if constexpr (G::FUSE) {
+            if (a.fuse_stage) {
+                for (int e = threadIdx.x; e < TL * TS; e += blockDim.x) {
+                    const int t = e % TS, l = e / TS;
+                    if (l >= lcount || t >= tcount) continue;
+                    const long long g = base0 + l * lstride + (long long)(pos0 + t) * sd;
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        cp_async8(&sU0[sidx<DIR, TL, TS>(v, l, t)], U0b + v * N + g);
+                        if (a.fuse_stage > 1) cp_async4(&sD[sidx<DIR, TL, TS>(v, l, t)], Db + v * N + g);
+                    }
+                }
+            }
+        }
         cp_async_commit();
         cp_async_wait<1>();                    // staged nodes have landed
     } else if constexpr (kAsync) {
@@ -398,9 +440,36 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR>::MIN_CTAS) sweep_ker
             } else {
                 const T fp = fma(T(MD_A1), f3 - f2, fma(T(MD_A2), f4 - f1, T(MD_A3) * (f5 - f0)));
                 const T val = -fp * ih;
-                if (!a.accumulate) L[v * N + g] = val;
-                else if constexpr (kPre) L[v * N + g] = sL[sidx<DIR, TL, TS>(v, l, t)] + val;
-                else L[v * N + g] += val;
+                T lv = val;
+                if (a.accumulate) {
+                    if constexpr (kPre) lv = sL[sidx<DIR, TL, TS>(v, l, t)] + val;
+                    else lv = L[v * N + g] + val;
+                }
+                if constexpr (G::FUSE) {
+                    if (a.fuse_stage) {
+                        // SSP-RK3 stage on U = U0 + D (FP64 base, FP32 increment):
+                        //   D1 = dt L;  D2 = (D1 + dt L)/4;  U0 += 2/3 (D2 + dt L)
+                        const float dt = (float)*dtp;
+                        const double u0 = sU0[sidx<DIR, TL, TS>(v, l, t)];
+                        const long long gi = v * N + g;
+                        if (a.fuse_stage == 1) {
+                            const float dd = dt * lv;
+                            Db[gi] = dd;
+                            Sob[gi] = __double2float_rn(u0) + dd;
+                        } else if (a.fuse_stage == 2) {
+                            const float dd = 0.25f * fmaf(dt, lv, sD[sidx<DIR, TL, TS>(v, l, t)]);
+                            Db[gi] = dd;
+                            Sob[gi] = __double2float_rn(u0) + dd;
+                        } else {
+                            const float dd = (2.0f / 3.0f) * fmaf(dt, lv, sD[sidx<DIR, TL, TS>(v, l, t)]);
+                            const double un = u0 + (double)dd;
+                            U0b[gi] = un;
+                            Sob[gi] = __double2float_rn(un);
+                        }
+                        continue;
+                    }
+                }
+                L[v * N + g] = lv;
             }
         }
     }
