@@ -139,6 +139,20 @@ wcns_status wcns_cfl_dt(wcns_handle* h, const void* U, double* dt, void* stream)
  * (synchronises the stream). */
 wcns_status wcns_fallback_count(wcns_handle* h, long long* count, int reset, void* stream);
 
+/* Tile-shape autotuner (no counterpart in the paper).  For FP32 handles of
+ * 2D/3D grids, times every compiled pencil-tile configuration of each
+ * direction's sweep (lines per tile x nodes per line; the halo depth is fixed
+ * at 5 by the stencil) on the FP64 device state U, and keeps the fastest for
+ * this handle.  chosen (nullable) receives the configuration per direction
+ * (0 = default).  FP64 and 1D handles keep configuration 0.  Results do not
+ * depend on the configuration.  Synchronises the stream. */
+wcns_status wcns_autotune(wcns_handle* h, const void* U, int* chosen, void* stream);
+
+/* Set (set non-NULL: one configuration 0..2 per direction; ignored by FP64
+ * and 1D handles) and/or read (get non-NULL, 3 ints) the handle's tile
+ * configurations.  No device work. */
+wcns_status wcns_tile_config(wcns_handle* h, const int* set, int* get);
+
 /* Kernel timing for measurement (no counterpart in the paper).  While
  * enabled, every sweep launch of this handle is bracketed by a pair of CUDA
  * events recorded on the launch stream.  wcns_profile_read synchronises

@@ -1,14 +1,21 @@
 // sweep_fp32.cu -- FP32 instances of the fused sweep (rescaled smoothness
-// indicators).  The input state is single precision.
+// indicators) for tile configuration SWEEP_CFG (0, 1 or 2; one translation
+// unit per configuration so they compile in parallel).  The input state is
+// single precision.
 #include "wcns_internal.h"
+
+#ifndef SWEEP_CFG
+#define SWEEP_CFG 0
+#endif
 
 namespace wcns {
 
-template <typename LT, int ND, int DIR, int FLUX>
+template <int ND, int DIR, int FLUX>
 static cudaError_t go(const SweepArgs& a, cudaStream_t s, bool prepare)
 {
-    using G = TileGeom<float, ND, DIR>;
-    auto k = sweep_kernel<float, LT, ND, DIR, FLUX>;
+    constexpr int CFG = ND == 1 ? 0 : SWEEP_CFG;
+    using G = TileGeom<float, ND, DIR, CFG>;
+    auto k = sweep_kernel<float, float, ND, DIR, FLUX, false, CFG>;
     const size_t smem = G::smem_bytes();
     if (prepare) return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid;
@@ -24,33 +31,54 @@ static cudaError_t go(const SweepArgs& a, cudaStream_t s, bool prepare)
     return cudaGetLastError();
 }
 
-template <typename LT, int FLUX>
+template <int FLUX>
 static cudaError_t dispatch(int nd, int dir, const SweepArgs& a, cudaStream_t s, bool prep)
 {
-    if (nd == 1) return go<LT, 1, 0, FLUX>(a, s, prep);
-    if (nd == 2) return dir == 0 ? go<LT, 2, 0, FLUX>(a, s, prep) : go<LT, 2, 1, FLUX>(a, s, prep);
-    if (dir == 0) return go<LT, 3, 0, FLUX>(a, s, prep);
-    if (dir == 1) return go<LT, 3, 1, FLUX>(a, s, prep);
-    return go<LT, 3, 2, FLUX>(a, s, prep);
+    if (nd == 1) return SWEEP_CFG == 0 ? go<1, 0, FLUX>(a, s, prep) : cudaErrorInvalidValue;
+    if (nd == 2) return dir == 0 ? go<2, 0, FLUX>(a, s, prep) : go<2, 1, FLUX>(a, s, prep);
+    if (dir == 0) return go<3, 0, FLUX>(a, s, prep);
+    if (dir == 1) return go<3, 1, FLUX>(a, s, prep);
+    return go<3, 2, FLUX>(a, s, prep);
 }
 
-cudaError_t launch_sweep_fp32(int nd, int dir, int flux, const SweepArgs& a, cudaStream_t s)
+#define WCNS_CAT2(a, b) a##b
+#define WCNS_CAT(a, b) WCNS_CAT2(a, b)
+
+cudaError_t WCNS_CAT(launch_sweep_fp32_cfg, SWEEP_CFG)(int nd, int dir, int flux, const SweepArgs& a,
+                                                        cudaStream_t s)
 {
-    return flux == FLUX_ROE ? dispatch<float, FLUX_ROE>(nd, dir, a, s, false)
-                            : dispatch<float, FLUX_VANLEER>(nd, dir, a, s, false);
+    return flux == FLUX_ROE ? dispatch<FLUX_ROE>(nd, dir, a, s, false)
+                            : dispatch<FLUX_VANLEER>(nd, dir, a, s, false);
 }
 
-cudaError_t prepare_sweeps_fp32()
+cudaError_t WCNS_CAT(prepare_sweeps_fp32_cfg, SWEEP_CFG)()
 {
     SweepArgs a{};
-    for (int nd = 1; nd <= 3; ++nd)
+    for (int nd = SWEEP_CFG == 0 ? 1 : 2; nd <= 3; ++nd)
         for (int d = 0; d < nd; ++d)
             for (int f = 0; f < 2; ++f) {
-                cudaError_t e = f == 0 ? dispatch<float, FLUX_ROE>(nd, d, a, 0, true)
-                                       : dispatch<float, FLUX_VANLEER>(nd, d, a, 0, true);
+                cudaError_t e = f == 0 ? dispatch<FLUX_ROE>(nd, d, a, 0, true)
+                                       : dispatch<FLUX_VANLEER>(nd, d, a, 0, true);
                 if (e != cudaSuccess) return e;
             }
     return cudaSuccess;
 }
+
+#if SWEEP_CFG == 0
+cudaError_t launch_sweep_fp32(int nd, int dir, int flux, int cfg, const SweepArgs& a, cudaStream_t s)
+{
+    if (nd == 1 || cfg == 0) return launch_sweep_fp32_cfg0(nd, dir, flux, a, s);
+    if (cfg == 1) return launch_sweep_fp32_cfg1(nd, dir, flux, a, s);
+    return launch_sweep_fp32_cfg2(nd, dir, flux, a, s);
+}
+
+cudaError_t prepare_sweeps_fp32()
+{
+    cudaError_t e = prepare_sweeps_fp32_cfg0();
+    if (e == cudaSuccess) e = prepare_sweeps_fp32_cfg1();
+    if (e == cudaSuccess) e = prepare_sweeps_fp32_cfg2();
+    return e;
+}
+#endif
 
 }  // namespace wcns

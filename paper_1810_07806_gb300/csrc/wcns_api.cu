@@ -33,6 +33,8 @@ struct wcns_handle {
     double* partials = nullptr;
     int nblk_cons = 0;
     size_t bytes = 0;
+    // tile configuration of each direction's FP32 sweep (set by wcns_autotune)
+    int tile_cfg[3] = {0, 0, 0};
     // optional sweep timing
     bool profiling = false;
     std::vector<cudaEvent_t> ev;    // pairs (start, end)
@@ -274,7 +276,7 @@ static cudaError_t run_rhs(wcns_handle* h, const void* U, void* L, uint8_t* flag
         }
         cudaError_t e;
         if (h->profiling && (e = timed_event(h, s)) != cudaSuccess) return e;
-        e = fp32 ? launch_sweep_fp32(h->ndim, d, h->p.flux, a, s)
+        e = fp32 ? launch_sweep_fp32(h->ndim, d, h->p.flux, h->tile_cfg[d], a, s)
                  : launch_sweep_fp64(h->ndim, d, h->p.flux, a, s);
         if (e != cudaSuccess) return e;
         if (h->profiling && (e = timed_event(h, s)) != cudaSuccess) return e;
@@ -463,3 +465,68 @@ void set_last_error(const char* msg)
     else g_err.clear();
 }
 }  // namespace wcns
+
+extern "C" wcns_status wcns_autotune(wcns_handle* h, const void* U, int* chosen, void* stream)
+{
+    using namespace wcns;
+    set_last_error(nullptr);
+    if (!h || !U) return fail(WCNS_ERR_INVALID, "wcns_autotune: null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->p.precision == WCNS_FP32 && h->ndim >= 2) {
+        const long long M = (long long)h->nv * h->N;
+        float* A = (float*)h->U1;
+        CK(launch_to_fp32((const double*)U, A, M, nullptr, s), "autotune state");
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0), "event");
+        CK(cudaEventCreate(&e1), "event");
+        for (int d = 0; d < h->ndim; ++d) {
+            float best = 1e30f;
+            int pick = 0;
+            for (int cfg = 0; cfg < 3; ++cfg) {
+                SweepArgs a{};
+                a.U = A;
+                a.L = h->L;
+                a.N = h->N;
+                for (int k = 0; k < 3; ++k) a.n[k] = h->n[k];
+                a.periodic = h->periodic[d];
+                a.inv_h = h->inv_h[d];
+                a.inv_hf = (float)h->inv_h[d];
+                a.accumulate = d != h->ndim - 1;   // as in a step: the first sweep writes L
+                a.fallback = h->fallback;
+                a.K = h->K;
+                a.sqrt_eps_f = h->sqrt_eps_f;
+                CK(launch_sweep_fp32(h->ndim, d, h->p.flux, cfg, a, s), "autotune warm-up");
+                CK(cudaEventRecord(e0, s), "event");
+                for (int r = 0; r < 3; ++r) CK(launch_sweep_fp32(h->ndim, d, h->p.flux, cfg, a, s), "autotune");
+                CK(cudaEventRecord(e1, s), "event");
+                CK(cudaEventSynchronize(e1), "event");
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, e0, e1), "event");
+                if (ms < best) { best = ms; pick = cfg; }
+            }
+            h->tile_cfg[d] = pick;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        CK(cudaMemsetAsync(h->fallback, 0, sizeof(long long), s), "counter reset");
+    }
+    if (chosen)
+        for (int d = 0; d < 3; ++d) chosen[d] = d < h->ndim ? h->tile_cfg[d] : 0;
+    return WCNS_OK;
+}
+
+extern "C" wcns_status wcns_tile_config(wcns_handle* h, const int* set, int* get)
+{
+    using namespace wcns;
+    set_last_error(nullptr);
+    if (!h) return fail(WCNS_ERR_INVALID, "wcns_tile_config: null handle");
+    if (set) {
+        for (int d = 0; d < h->ndim; ++d)
+            if (set[d] < 0 || set[d] > 2) return fail(WCNS_ERR_INVALID, "tile configuration must be 0, 1 or 2");
+        if (h->p.precision == WCNS_FP32 && h->ndim >= 2)
+            for (int d = 0; d < h->ndim; ++d) h->tile_cfg[d] = set[d];
+    }
+    if (get)
+        for (int d = 0; d < 3; ++d) get[d] = d < h->ndim ? h->tile_cfg[d] : 0;
+    return WCNS_OK;
+}

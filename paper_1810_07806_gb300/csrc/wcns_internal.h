@@ -8,7 +8,13 @@ namespace wcns {
 // Launch one sweep of direction dir, FP64 or FP32 (input and output in the
 // sweep's precision).
 cudaError_t launch_sweep_fp64(int nd, int dir, int flux, const SweepArgs& a, cudaStream_t s);
-cudaError_t launch_sweep_fp32(int nd, int dir, int flux, const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_sweep_fp32(int nd, int dir, int flux, int cfg, const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_sweep_fp32_cfg0(int nd, int dir, int flux, const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_sweep_fp32_cfg1(int nd, int dir, int flux, const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_sweep_fp32_cfg2(int nd, int dir, int flux, const SweepArgs& a, cudaStream_t s);
+cudaError_t prepare_sweeps_fp32_cfg0();
+cudaError_t prepare_sweeps_fp32_cfg1();
+cudaError_t prepare_sweeps_fp32_cfg2();
 // Batched sweeps over a tile table (wcns_batch.cu); ntiles CTAs.
 cudaError_t launch_sweep_batch_fp64(int nd, int dir, int flux, const SweepArgs& a, long long ntiles,
                                     cudaStream_t s);

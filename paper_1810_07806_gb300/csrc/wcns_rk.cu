@@ -227,7 +227,7 @@ cudaError_t launch_rk_fp64(int stage, double* U0, double* U1, const double* L, l
 __global__ void __launch_bounds__(256) to_fp32_kernel(const double* __restrict__ U, float* __restrict__ S,
                                                       long long M, const StepScalars* sc)
 {
-    if (sc != nullptr && sc->dt == 0.0) return;
+    if (sc != nullptr && sc->dt == 0.0) return;   // a finished run (sc may be null: always convert)
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M;
          i += (long long)gridDim.x * blockDim.x)
         S[i] = __double2float_rn(U[i]);

@@ -87,10 +87,23 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int NW>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(NW) : "memory"); }
 
-template <typename T, int ND, int DIR>
+// Tile shapes: lines per tile (TL) x nodes per line (TS); TL * (TS + 5) faces
+// is a multiple of the 256 threads.  Configuration 0 is the default; the
+// autotuner (FP32, 2D/3D) may pick 1 (longer pencils: fewer recomputed halo
+// faces) or 2 (whole-line x pencils, narrower y/z tiles) per direction.
+constexpr int tile_lines(int nd, int dir, int cfg)
+{
+    return nd == 1 ? 1 : (dir == 0 ? (cfg == 0 ? 4 : (cfg == 1 ? 2 : 1)) : (cfg == 0 ? 16 : 8));
+}
+constexpr int tile_nodes(int nd, int dir, int cfg)
+{
+    return nd == 1 ? 251 : (dir == 0 ? (cfg == 0 ? 59 : (cfg == 1 ? 123 : 251)) : (cfg == 1 ? 123 : 59));
+}
+
+template <typename T, int ND, int DIR, int CFG = 0>
 struct TileGeom {
-    static constexpr int TL = (ND == 1) ? 1 : (DIR == 0 ? 4 : 16);   // lines per tile
-    static constexpr int TS = (ND == 1) ? 251 : 59;                   // nodes per line
+    static constexpr int TL = tile_lines(ND, DIR, CFG);   // lines per tile
+    static constexpr int TS = tile_nodes(ND, DIR, CFG);   // nodes per line
     static constexpr int P = TS + 2 * GHOST;                          // staged nodes
     static constexpr int NF = TS + 5;                                 // faces
     static constexpr int THREADS = 256;
@@ -235,11 +248,11 @@ __device__ __forceinline__ void face_flux(float (&u)[6][ND + 2], const SweepArgs
 }
 
 // ---------------------------------------------------------------- kernel
-template <typename T, typename LT, int ND, int DIR, int FLUX, bool BATCH = false>
-__global__ void __launch_bounds__(256, TileGeom<T, ND, DIR>::MIN_CTAS) sweep_kernel(const SweepArgs a)
+template <typename T, typename LT, int ND, int DIR, int FLUX, bool BATCH = false, int CFG = 0>
+__global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) sweep_kernel(const SweepArgs a)
 {
     constexpr int NV = ND + 2;
-    using G = TileGeom<T, ND, DIR>;
+    using G = TileGeom<T, ND, DIR, CFG>;
     constexpr int TL = G::TL, TS = G::TS, P = G::P, NF = G::NF;
     constexpr bool kAsyncStage = sizeof(LT) == sizeof(T) && sizeof(T) == 4;
     constexpr bool kPre = G::PREFETCH_L;

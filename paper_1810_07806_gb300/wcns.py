@@ -188,6 +188,25 @@ class Solver:
         check(lib().wcns_profile_read(self.h, C.byref(ms), C.byref(n)))
         return ms.value, n.value
 
+    def autotune(self, U, stream=None):
+        """Pick the fastest tile configuration of each direction's FP32 sweep
+        for this grid (returns the configuration per direction)."""
+        L = lib()
+        L.wcns_autotune.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(C.c_int), C.c_void_p]
+        L.wcns_autotune.restype = C.c_int
+        out = (C.c_int * 3)()
+        check(L.wcns_autotune(self.h, _ptr(U), out, _stream(stream)))
+        return list(out)[: self.ndim]
+
+    def tile_config(self, cfg=None):
+        L = lib()
+        L.wcns_tile_config.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.wcns_tile_config.restype = C.c_int
+        get = (C.c_int * 3)()
+        st = (C.c_int * 3)(*(list(cfg) + [0, 0, 0])[:3]) if cfg is not None else None
+        check(L.wcns_tile_config(self.h, st, get))
+        return list(get)[: self.ndim]
+
     def launches_per_step(self, cfl_step=True):
         return lib().wcns_launches_per_step(self.h, int(cfl_step))
 

@@ -312,3 +312,28 @@ def test_fp32_error_on_smooth_flow_is_small():
     # the w-momentum stays (round-off) zero; measure it against the others
     rel[3] = np.sum(np.abs(b[3] - a[3])) / np.sum(np.abs(a[1]))
     assert np.all(rel < 3e-6), rel
+
+
+@pytest.mark.parametrize("which", ["tgv40", "quad130x71"])
+def test_tile_configurations_give_identical_results(which):
+    """Every pencil-tile configuration the autotuner can pick computes the
+    same faces with the same arithmetic: RHS and steps are bit-identical."""
+    pb = inputs.taylor_green(40) if which == "tgv40" else inputs.four_quadrant(130, ny=71)
+    s = wcns.Solver.for_problem(pb, precision=wcns.FP32)
+    U32 = torch.from_numpy(pb.U0).to(DEV).float()
+    outs, steps = [], []
+    for cfg in range(3):
+        s.tile_config([cfg] * pb.ndim)
+        L = torch.empty_like(U32)
+        s.rhs(U32, L)
+        outs.append(L.cpu().numpy())
+        U = torch.from_numpy(pb.U0.copy()).to(DEV)
+        for _ in range(3):
+            s.step(U, 1e-4)
+        steps.append(U.cpu().numpy())
+    for k in (1, 2):
+        assert np.array_equal(outs[k], outs[0])
+        assert np.array_equal(steps[k], steps[0])
+    chosen = s.autotune(torch.from_numpy(pb.U0).to(DEV))
+    assert len(chosen) == pb.ndim and all(0 <= c <= 2 for c in chosen)
+    s.close()
