@@ -10,7 +10,7 @@ import numpy as np
 from . import build as _build
 
 FLUX_ROE, FLUX_VANLEER = 0, 1
-W_TENO, W_JS, W_LINEAR = 0, 1, 2
+W_TENO, W_JS, W_LINEAR, W_Z = 0, 1, 2, 3
 
 _dp = C.POINTER(C.c_double)
 _u8p = C.POINTER(C.c_uint8)

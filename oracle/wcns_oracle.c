@@ -19,6 +19,8 @@
  *   Eq. 8-11 three 3-point sub-stencils and their Taylor interpolants
  *   Eq. 12-13 convex combination, optimal weights d = (1, 10, 5)/16
  *   Eq. 14-15 Jiang-Shu weights and the WCNS smoothness indicator beta_k
+ *   WCNS-Z   the comparison scheme of Sec. 3, weights of Borges et al.
+ *            (cited, not printed): alpha_k = d_k (1 + tau_5 / (beta_k + eps))
  *   Eq. 16-19 TENO scale separation gamma_k, normalisation chi_k, sharp
  *            cutoff delta_k, and the final weights omega_k^(T)
  *   Sec. 3   characteristic-variable interpolation, ideal gas, van Leer or
@@ -53,7 +55,7 @@
 
 /* Scheme switches (the oracle's own numbering). */
 enum { ORA_FLUX_ROE = 0, ORA_FLUX_VANLEER = 1 };
-enum { ORA_W_TENO = 0, ORA_W_JS = 1, ORA_W_LINEAR = 2 };
+enum { ORA_W_TENO = 0, ORA_W_JS = 1, ORA_W_LINEAR = 2, ORA_W_Z = 3 };
 
 typedef struct {
     int ndim;             /* 1, 2 or 3                                   */
@@ -151,7 +153,14 @@ static double interp_left(const ora_cfg* cfg, const double s[5], int force_flags
             }
         }
     }
-    if (force_flags < 0 && cfg->weights == ORA_W_JS) {
+    if (force_flags < 0 && cfg->weights == ORA_W_Z) {
+        double tau = fabs(beta[0] - beta[2]), a[3], asum = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            a[k] = d[k] * (1.0 + tau / (beta[k] + cfg->eps));
+            asum += a[k];
+        }
+        for (int k = 0; k < 3; ++k) w[k] = a[k] / asum;
+    } else if (force_flags < 0 && cfg->weights == ORA_W_JS) {
         double a[3], asum = 0.0;                               /* Eq. 14 */
         for (int k = 0; k < 3; ++k) {
             double b = beta[k] + cfg->eps_js;

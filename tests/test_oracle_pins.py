@@ -234,11 +234,14 @@ def test_table2_gaussian_advection(N):
     u0 = np.exp(-300 * (x - 0.5) ** 2)
     steps = int(math.ceil(1.0 / (0.02 * h)))
     got = {}
-    for key, w in (("tcns", O.W_TENO), ("linear", O.W_LINEAR), ("js", O.W_JS)):
+    for key, w in (("tcns", O.W_TENO), ("linear", O.W_LINEAR), ("js", O.W_JS), ("z", O.W_Z)):
         u = O.scalar_run(O.make_cfg(weights=w), 0, u0, h, 1.0, steps)
         got[key] = np.max(np.abs(u - u0))
     assert abs(got["linear"] / tab["linear"] - 1) < 0.012, got
     assert abs(got["js"] / tab["js"] - 1) < 0.03, got
+    # WCNS-Z (weights of Borges et al., cited by the paper, not printed):
+    # alpha_k = d_k (1 + tau_5 / (beta_k + eps)) reproduces the printed column
+    assert abs(got["z"] / tab["z"] - 1) < 0.012, got
     # N = 51 is under-resolved: the TCNS cut pattern, hence the third digit,
     # moves with dt (5.21e-2 .. 5.25e-2 for CFL 0.005 .. 0.1)
     assert abs(got["tcns"] / tab["tcns"] - 1) < (0.012 if N > 51 else 0.015), got
@@ -258,7 +261,7 @@ def test_table3_burgers(N):
     du0 = lambda z: np.pi * np.cos(np.pi * z)
     ue = burgers_exact(x, 0.2, u0f, du0)
     steps = int(math.ceil(0.2 / (0.05 * h / 1.5)))
-    for key, w in (("tcns", O.W_TENO), ("js", O.W_JS)):
+    for key, w in (("tcns", O.W_TENO), ("js", O.W_JS), ("z", O.W_Z)):
         u = O.scalar_run(O.make_cfg(weights=w), 1, u0f(x), h, 0.2, steps)
         err = np.max(np.abs(u - ue))
         assert abs(err / tab[key] - 1) < 0.015, (key, err, tab[key])
