@@ -42,7 +42,12 @@ typedef enum {
 enum { WCNS_BC_TRANSMISSIVE = 0, WCNS_BC_PERIODIC = 1 };
 enum { WCNS_FLUX_ROE = 0, WCNS_FLUX_VANLEER = 1 };
 enum { WCNS_DIFF_MD6 = 0 };
-enum { WCNS_W_TENO = 0 };
+/* Interpolation weights: TENO selection (Eq. 16-19, the paper's scheme),
+ * WCNS-JS (Eq. 14), linear (the optimal weights d_k of Eq. 13, i.e. Eq. 7)
+ * and WCNS-Z (the weights of Borges et al. that the paper compares with,
+ * alpha_k = d_k (1 + tau_5 / (beta_k + eps)) with the tau_5 of Eq. 16).
+ * JS, linear and Z are available in FP64 only. */
+enum { WCNS_W_TENO = 0, WCNS_W_JS = 1, WCNS_W_LINEAR = 2, WCNS_W_Z = 3 };
 enum { WCNS_FP64 = 0, WCNS_FP32 = 1 };
 
 /* Uniform grid.  Axis a has n[a] nodes on [lo[a], hi[a]].  A transmissive
@@ -64,13 +69,14 @@ typedef struct {
 typedef struct {
     int flux;            /* WCNS_FLUX_ROE | WCNS_FLUX_VANLEER                 */
     int diff;            /* WCNS_DIFF_MD6                                     */
-    int weights;         /* WCNS_W_TENO                                       */
-    double C, eps, CT;   /* Eq. 16 and Eq. 18 constants                       */
+    int weights;         /* WCNS_W_TENO | _JS | _LINEAR | _Z                  */
+    double C, eps, CT;   /* Eq. 16 and Eq. 18 constants (eps also serves Z)   */
     int q;               /* Eq. 16 power, 1..16                               */
     int characteristic;  /* must be 1: interpolate characteristic variables   */
     int precision;       /* WCNS_FP64 | WCNS_FP32                             */
     double cfl;          /* CFL number of the time-step rule                  */
     int entropy_fix;     /* must be 0 (the paper uses none)                   */
+    double eps_js;       /* epsilon of Eq. 14 (WCNS-JS), default 1e-6         */
 } wcns_scheme_params;
 
 typedef struct wcns_handle wcns_handle;
@@ -288,6 +294,37 @@ wcns_status wcns_batch_submit(wcns_server* sv, const wcns_request* req, uint64_t
 wcns_status wcns_serve_poll(wcns_server* sv, wcns_result* out, int max, int* n_out, int timeout_us);
 void wcns_result_free(wcns_result* r);
 wcns_status wcns_server_stats(wcns_server* sv, wcns_server_stats_t* stats);
+
+/* ---------------------------------------------------------------------
+ * Scalar conservation laws u_t + f(u)_x = 0 on periodic 1D grids, the
+ * paper's accuracy tests (Sec. 3.2: linear advection, f = u; Sec. 3.3:
+ * inviscid Burgers, f = u^2 / 2).  The midpoint flux is Eq. 6 with the
+ * approximate eigenvalue a = 1 (advection) or a = (u_L + u_R) / 2
+ * (Burgers); u_L and u_R come from the node-to-midpoint interpolation of
+ * Sec. 2.2 with the weights params->weights selects (no characteristic
+ * projection: there is one field); the derivative is Eq. 3.  FP64 only.
+ *
+ * `count` independent lines of n unique nodes each (periodic: node n is
+ * node 0; h is the node spacing) sit in device memory at u + i * ld,
+ * i = 0 .. count-1, ld >= n doubles.  Each line is solved by one
+ * thread-block cluster that keeps it resident in distributed shared memory
+ * for the whole call.  1 <= n <= wcns_scalar_max_nodes(); count >= 1.
+ * Stream-ordered; no allocation; no host synchronisation.
+ * --------------------------------------------------------------------- */
+enum { WCNS_SCALAR_ADVECTION = 0, WCNS_SCALAR_BURGERS = 1 };
+
+/* Largest n the scalar solver accepts on the current device. */
+int wcns_scalar_max_nodes(void);
+
+/* L = -f'(u) by Eq. 3 for every line (L has the same layout as u). */
+wcns_status wcns_scalar_rhs(int kind, const wcns_scheme_params* params, int n, double h, int count,
+                            const double* u, long long ld, double* L, void* stream);
+
+/* nsteps SSP-RK3 steps of equal size dt = t_end / nsteps, in place, in one
+ * kernel launch (the lines stay on chip between steps). */
+wcns_status wcns_scalar_run(int kind, const wcns_scheme_params* params, int n, double h,
+                            double t_end, int nsteps, int count, double* u, long long ld,
+                            void* stream);
 
 /* Number of kernel launches one wcns_step_rk3 call issues (for accounting). */
 int wcns_launches_per_step(const wcns_handle* h, int cfl_step);

@@ -85,6 +85,7 @@ void wcns_default_params(wcns_scheme_params* p)
     p->precision = WCNS_FP64;
     p->cfl = 0.5;
     p->entropy_fix = 0;
+    p->eps_js = 1e-6;
 }
 
 static bool prepared_fp64[64], prepared_fp32[64];
@@ -97,18 +98,7 @@ wcns_status wcns_create(const wcns_grid* g, double gamma, const wcns_scheme_para
     *out = nullptr;
     if (g->ndim < 1 || g->ndim > 3) return fail(WCNS_ERR_INVALID, "ndim must be 1, 2 or 3");
     if (!(gamma > 1.0)) return fail(WCNS_ERR_INVALID, "gamma must exceed 1");
-    if (prm->flux != WCNS_FLUX_ROE && prm->flux != WCNS_FLUX_VANLEER)
-        return fail(WCNS_ERR_INVALID, "unsupported flux %d", prm->flux);
-    if (prm->diff != WCNS_DIFF_MD6) return fail(WCNS_ERR_INVALID, "unsupported difference scheme");
-    if (prm->weights != WCNS_W_TENO) return fail(WCNS_ERR_INVALID, "unsupported weights");
-    if (prm->characteristic != 1) return fail(WCNS_ERR_INVALID, "characteristic must be 1");
-    if (prm->entropy_fix != 0) return fail(WCNS_ERR_INVALID, "entropy_fix must be 0");
-    if (!(prm->C > 0.0) || !(prm->eps > 0.0) || !(prm->CT > 0.0) || !(prm->CT < 1.0 / 3.0))
-        return fail(WCNS_ERR_INVALID, "need C > 0, eps > 0, 0 < C_T < 1/3");
-    if (prm->q < 1 || prm->q > 16) return fail(WCNS_ERR_INVALID, "q must be in 1..16");
-    if (prm->precision != WCNS_FP64 && prm->precision != WCNS_FP32)
-        return fail(WCNS_ERR_INVALID, "precision must be WCNS_FP64 or WCNS_FP32");
-    if (!(prm->cfl > 0.0)) return fail(WCNS_ERR_INVALID, "cfl must be positive");
+    if (const char* why = scheme_params_error(prm)) return fail(WCNS_ERR_INVALID, "%s", why);
 
     wcns_handle* h = new wcns_handle();
     h->ndim = g->ndim;
@@ -142,22 +132,7 @@ wcns_status wcns_create(const wcns_grid* g, double gamma, const wcns_scheme_para
     }
     h->gamma = gamma;
     h->p = *prm;
-    h->K.gamma = gamma;
-    h->K.gm1 = gamma - 1.0;
-    h->K.C = prm->C;
-    h->K.eps = prm->eps;
-    h->K.CT = prm->CT;
-    h->K.q = prm->q;
-    // A stencil can only be cut if max g / min g exceeds (3 C_T)^(-1/q); since
-    // max g / min g <= 1 + tau / (C (min beta + eps)), tau below
-    // 0.98 (ratio - 1) C (min beta + eps) keeps all three.
-    const double ratio = pow(3.0 * prm->CT, -1.0 / prm->q);
-    h->K.keep_all_K = 0.98 * (ratio - 1.0) * prm->C;
-    h->K.Cf = (float)prm->C;
-    h->K.CTf = (float)prm->CT;
-    h->K.Kf = (float)h->K.keep_all_K;
-    h->K.gammaf = (float)gamma;
-    h->K.gm1f = (float)(gamma - 1.0);
+    h->K = make_scheme_const(prm, gamma);
     h->sqrt_eps_f = (float)sqrt(prm->eps);
 
     cudaError_t e = cudaGetDevice(&h->device);

@@ -428,16 +428,7 @@ wcns_status wcns_batch_create(int ndim, double gamma, const wcns_scheme_params* 
     *out = nullptr;
     if (ndim < 1 || ndim > 3) return bfail(WCNS_ERR_INVALID, "ndim must be 1, 2 or 3");
     if (!(gamma > 1.0)) return bfail(WCNS_ERR_INVALID, "gamma must exceed 1");
-    if (prm->flux != WCNS_FLUX_ROE && prm->flux != WCNS_FLUX_VANLEER)
-        return bfail(WCNS_ERR_INVALID, "unsupported flux");
-    if (prm->diff != WCNS_DIFF_MD6 || prm->weights != WCNS_W_TENO || prm->characteristic != 1 ||
-        prm->entropy_fix != 0)
-        return bfail(WCNS_ERR_INVALID, "unsupported scheme option");
-    if (!(prm->C > 0.0) || !(prm->eps > 0.0) || !(prm->CT > 0.0) || !(prm->CT < 1.0 / 3.0) || prm->q < 1 ||
-        prm->q > 16 || !(prm->cfl > 0.0))
-        return bfail(WCNS_ERR_INVALID, "bad scheme constants");
-    if (prm->precision != WCNS_FP64 && prm->precision != WCNS_FP32)
-        return bfail(WCNS_ERR_INVALID, "precision must be WCNS_FP64 or WCNS_FP32");
+    if (const char* why = scheme_params_error(prm)) return bfail(WCNS_ERR_INVALID, "%s", why);
     if (max_nodes < 1 || max_instances < 1) return bfail(WCNS_ERR_INVALID, "capacities must be positive");
 
     wcns_batch* b = new wcns_batch();
@@ -447,18 +438,7 @@ wcns_status wcns_batch_create(int ndim, double gamma, const wcns_scheme_params* 
     b->flux = prm->flux;
     b->gamma = gamma;
     b->cfl = prm->cfl;
-    b->K.gamma = gamma;
-    b->K.gm1 = gamma - 1.0;
-    b->K.C = prm->C;
-    b->K.eps = prm->eps;
-    b->K.CT = prm->CT;
-    b->K.q = prm->q;
-    b->K.keep_all_K = 0.98 * (pow(3.0 * prm->CT, -1.0 / prm->q) - 1.0) * prm->C;
-    b->K.Cf = (float)prm->C;
-    b->K.CTf = (float)prm->CT;
-    b->K.Kf = (float)b->K.keep_all_K;
-    b->K.gammaf = (float)gamma;
-    b->K.gm1f = (float)(gamma - 1.0);
+    b->K = make_scheme_const(prm, gamma);
     b->sqrt_eps_f = (float)sqrt(prm->eps);
     b->cap_slots = max_instances;
     // each instance's block is rounded up to 64 elements

@@ -41,10 +41,16 @@ constexpr double MD_A3 = 3.0 / 640.0;
 static __constant__ double c_table1_f64[8][5] = WCNS_TABLE1_ROWS;
 static __constant__ float c_table1_f32[8][5] = WCNS_TABLE1_ROWS;
 
+// Weight functions of the node-to-midpoint interpolation (values of the
+// C ABI's WCNS_W_*).
+enum { W_TENO = 0, W_JS = 1, W_LINEAR = 2, W_Z = 3 };
+
 struct SchemeConst {
     double gamma, gm1;
     double C, eps, CT;
     int q;
+    int weights;         // W_TENO | W_JS | W_LINEAR | W_Z
+    double eps_js;       // epsilon of Eq. 14
     double keep_all_K;   // tau < K * (min beta + eps) guarantees no cut (exact test)
     float Cf, CTf, Kf;
     float gammaf, gm1f;  // gamma, gamma - 1 in float

@@ -107,10 +107,9 @@ __device__ __forceinline__ void project_fp64(const ProjFP64<ND>& P, const double
 // Eq. 10, 11, 15 and 16-18 on one stencil s[0..4] = u_{i-2} .. u_{i+2},
 // in one fixed order; chi_k is evaluated as s_k / sum s with
 // s_k = (g_k / max g)^q, which equals Eq. 17 and cannot overflow.
-__device__ __forceinline__ int select_fp64(const double s[5], const SchemeConst& K, double D1[3],
-                                           double D2[3])
+__device__ __forceinline__ void derivs_fp64(const double s[5], double D1[3], double D2[3],
+                                            double beta[3])
 {
-    double beta[3];
     D1[0] = mul_(0.5, add_(sub_(s[0], mul_(4.0, s[1])), mul_(3.0, s[2])));
     D1[1] = mul_(0.5, sub_(s[3], s[1]));
     D1[2] = mul_(0.5, sub_(add_(mul_(-3.0, s[2]), mul_(4.0, s[3])), s[4]));
@@ -119,6 +118,13 @@ __device__ __forceinline__ int select_fp64(const double s[5], const SchemeConst&
     D2[2] = add_(sub_(s[2], mul_(2.0, s[3])), s[4]);
 #pragma unroll
     for (int k = 0; k < 3; ++k) beta[k] = add_(mul_(D1[k], D1[k]), mul_(D2[k], D2[k]));
+}
+
+__device__ __forceinline__ int select_fp64(const double s[5], const SchemeConst& K, double D1[3],
+                                           double D2[3])
+{
+    double beta[3];
+    derivs_fp64(s, D1, D2, beta);
     const double tau = fabs(sub_(beta[0], beta[2]));
     // No stencil can be cut unless the largest gamma exceeds the smallest by
     // the factor (3 C_T)^(-1/q); this bound (with a 2% margin) lets smooth
@@ -176,6 +182,47 @@ __device__ __forceinline__ double interp_fp64(int flags, const double s[5], cons
         const double uk = add_(add_(s[2], mul_(D1[k], 0.5)), mul_(D2[k], 0.125));
         const double w = flags == 7 ? (k == 0 ? 1.0 / 16.0 : (k == 1 ? 10.0 / 16.0 : 5.0 / 16.0))
                                     : c_omega[flags][k];
+        u = k == 0 ? mul_(w, uk) : add_(u, mul_(w, uk));
+    }
+    return u;
+}
+
+// u_L of one stencil s[0..4] = u_{i-2} .. u_{i+2} with the weights K.weights
+// selects: TENO (flags of Eq. 18, weights of Eq. 19), WCNS-JS (Eq. 14),
+// WCNS-Z (alpha_k = d_k (1 + tau_5 / (beta_k + eps)), Borges et al.) or the
+// linear weights d_k of Eq. 13.  Eq. 12 with omega_k = alpha_k / sum alpha,
+// alpha summed in k order.  flags = 7 for every choice but TENO.
+__device__ __forceinline__ double interp_weights_fp64(const double s[5], const SchemeConst& K,
+                                                      int& flags)
+{
+    double D1[3], D2[3];
+    if (K.weights == W_TENO) {
+        flags = select_fp64(s, K, D1, D2);
+        return interp_fp64(flags, s, D1, D2);
+    }
+    double beta[3];
+    derivs_fp64(s, D1, D2, beta);
+    flags = 7;
+    if (K.weights == W_LINEAR) return interp_fp64(7, s, D1, D2);
+    const double d[3] = {1.0 / 16.0, 10.0 / 16.0, 5.0 / 16.0};
+    double a[3];
+    if (K.weights == W_Z) {
+        const double tau = fabs(sub_(beta[0], beta[2]));
+#pragma unroll
+        for (int k = 0; k < 3; ++k) a[k] = mul_(d[k], add_(1.0, div_(tau, add_(beta[k], K.eps))));
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const double b = add_(beta[k], K.eps_js);
+            a[k] = div_(d[k], mul_(b, b));
+        }
+    }
+    const double asum = add_(add_(a[0], a[1]), a[2]);
+    double u = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double uk = add_(add_(s[2], mul_(D1[k], 0.5)), mul_(D2[k], 0.125));
+        const double w = div_(a[k], asum);
         u = k == 0 ? mul_(w, uk) : add_(u, mul_(w, uk));
     }
     return u;
@@ -308,13 +355,12 @@ __device__ __forceinline__ void face_fp64(double (&u)[6][ND + 2], const SchemeCo
     double wL[NV], wR[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-        double sl[5], sr[5], D1[3], D2[3];
+        double sl[5], sr[5];
 #pragma unroll
         for (int m = 0; m < 5; ++m) { sl[m] = u[m][k]; sr[m] = u[5 - m][k]; }
-        const int fL = select_fp64(sl, K, D1, D2);
-        wL[k] = interp_fp64(fL, sl, D1, D2);
-        const int fR = select_fp64(sr, K, D1, D2);
-        wR[k] = interp_fp64(fR, sr, D1, D2);
+        int fL, fR;
+        wL[k] = interp_weights_fp64(sl, K, fL);
+        wR[k] = interp_weights_fp64(sr, K, fR);
         fl[k] = (uint8_t)(fL | (fR << 3));
     }
     double UL[NV], UR[NV];

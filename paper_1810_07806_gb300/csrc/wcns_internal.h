@@ -1,9 +1,60 @@
 // wcns_internal.h -- launch interface between the C ABI and the kernels.
 #pragma once
 #include <cuda_runtime.h>
+#include <math.h>
+#include "../../include/wcns.h"
 #include "wcns_sweep.cuh"
 
 namespace wcns {
+
+static_assert((int)W_TENO == (int)WCNS_W_TENO && (int)W_JS == (int)WCNS_W_JS &&
+                  (int)W_LINEAR == (int)WCNS_W_LINEAR && (int)W_Z == (int)WCNS_W_Z,
+              "weight codes");
+
+// Checks the scheme options every entry point shares: nullptr when valid,
+// otherwise the reason.
+inline const char* scheme_params_error(const wcns_scheme_params* p)
+{
+    if (p->flux != WCNS_FLUX_ROE && p->flux != WCNS_FLUX_VANLEER) return "unsupported flux";
+    if (p->diff != WCNS_DIFF_MD6) return "unsupported difference scheme";
+    if (p->weights < WCNS_W_TENO || p->weights > WCNS_W_Z) return "unknown weights";
+    if (p->precision != WCNS_FP64 && p->precision != WCNS_FP32)
+        return "precision must be WCNS_FP64 or WCNS_FP32";
+    if (p->weights != WCNS_W_TENO && p->precision != WCNS_FP64)
+        return "JS, linear and Z weights need precision WCNS_FP64";
+    if (p->characteristic != 1) return "characteristic must be 1";
+    if (p->entropy_fix != 0) return "entropy_fix must be 0";
+    if (!(p->C > 0.0) || !(p->eps > 0.0) || !(p->CT > 0.0) || !(p->CT < 1.0 / 3.0))
+        return "need C > 0, eps > 0, 0 < C_T < 1/3";
+    if (p->q < 1 || p->q > 16) return "q must be in 1..16";
+    if (p->weights == WCNS_W_JS && !(p->eps_js > 0.0)) return "eps_js must be positive";
+    if (!(p->cfl > 0.0)) return "cfl must be positive";
+    return nullptr;
+}
+
+// Device constants of a valid parameter set.
+inline SchemeConst make_scheme_const(const wcns_scheme_params* p, double gamma)
+{
+    SchemeConst K{};
+    K.gamma = gamma;
+    K.gm1 = gamma - 1.0;
+    K.C = p->C;
+    K.eps = p->eps;
+    K.CT = p->CT;
+    K.q = p->q;
+    K.weights = p->weights;
+    K.eps_js = p->eps_js;
+    // A stencil can only be cut if max g / min g exceeds (3 C_T)^(-1/q); since
+    // max g / min g <= 1 + tau / (C (min beta + eps)), tau below
+    // 0.98 (ratio - 1) C (min beta + eps) keeps all three.
+    K.keep_all_K = 0.98 * (pow(3.0 * p->CT, -1.0 / p->q) - 1.0) * p->C;
+    K.Cf = (float)p->C;
+    K.CTf = (float)p->CT;
+    K.Kf = (float)K.keep_all_K;
+    K.gammaf = (float)gamma;
+    K.gm1f = (float)(gamma - 1.0);
+    return K;
+}
 
 // Launch one sweep of direction dir, FP64 or FP32 (input and output in the
 // sweep's precision).

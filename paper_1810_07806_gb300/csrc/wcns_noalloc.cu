@@ -67,14 +67,7 @@ extern "C" wcns_status wcns_step_rk3_noalloc(const wcns_grid* g, double gamma,
     if (!(gamma > 1.0)) return fail(WCNS_ERR_INVALID, "gamma must exceed 1");
     if (prm->precision != WCNS_FP64)
         return fail(WCNS_ERR_INVALID, "wcns_step_rk3_noalloc: precision must be WCNS_FP64");
-    if (prm->flux != WCNS_FLUX_ROE && prm->flux != WCNS_FLUX_VANLEER)
-        return fail(WCNS_ERR_INVALID, "unsupported flux");
-    if (prm->diff != WCNS_DIFF_MD6 || prm->weights != WCNS_W_TENO || prm->characteristic != 1 ||
-        prm->entropy_fix != 0)
-        return fail(WCNS_ERR_INVALID, "unsupported scheme option");
-    if (!(prm->C > 0.0) || !(prm->eps > 0.0) || !(prm->CT > 0.0) || !(prm->CT < 1.0 / 3.0) ||
-        prm->q < 1 || prm->q > 16 || !(prm->cfl > 0.0))
-        return fail(WCNS_ERR_INVALID, "need C > 0, eps > 0, 0 < C_T < 1/3, 1 <= q <= 16, cfl > 0");
+    if (const char* why = scheme_params_error(prm)) return fail(WCNS_ERR_INVALID, why);
 
     const int nd = g->ndim, nv = nd + 2;
     int n[3] = {1, 1, 1}, periodic[3] = {0, 0, 0};
@@ -125,17 +118,7 @@ extern "C" wcns_status wcns_step_rk3_noalloc(const wcns_grid* g, double gamma,
     double* U0 = static_cast<double*>(U);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
 
-    SchemeConst K{};
-    K.gamma = gamma;
-    K.gm1 = gamma - 1.0;
-    K.C = prm->C;
-    K.eps = prm->eps;
-    K.CT = prm->CT;
-    K.q = prm->q;
-    K.keep_all_K = 0.98 * (pow(3.0 * prm->CT, -1.0 / prm->q) - 1.0) * prm->C;
-    K.Cf = (float)prm->C;
-    K.CTf = (float)prm->CT;
-    K.Kf = (float)K.keep_all_K;
+    const SchemeConst K = make_scheme_const(prm, gamma);
 
     // the buffer keeps the previous call's contents: clear what must start at zero
     if ((e = launch_reset_clock(INFINITY, sc, s)) != cudaSuccess) return cuda_fail(e, "clock reset");

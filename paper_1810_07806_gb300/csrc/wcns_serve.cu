@@ -48,7 +48,8 @@ struct Running {
     long long nodes;
 };
 
-using ClassKey = std::tuple<int, int, int, double, double, double, double, int, double>;
+// Requests share a batch when every scheme constant and gamma agree.
+using ClassKey = std::tuple<int, int, int, double, double, double, double, int, double, int, double>;
 
 struct ClassBatch {
     wcns_batch* b = nullptr;
@@ -59,7 +60,8 @@ struct ClassBatch {
 ClassKey key_of(const wcns_request& r)
 {
     const wcns_scheme_params& p = r.params;
-    return ClassKey(r.grid.ndim, p.precision, p.flux, p.C, p.eps, p.CT, p.cfl, p.q, r.gamma);
+    return ClassKey(r.grid.ndim, p.precision, p.flux, p.C, p.eps, p.CT, p.cfl, p.q, r.gamma, p.weights,
+                    p.weights == WCNS_W_JS ? p.eps_js : 0.0);
 }
 
 size_t bytes_per_node(int ndim, int precision)

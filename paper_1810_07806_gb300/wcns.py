@@ -15,6 +15,8 @@ OK, ERR_INVALID, ERR_NOMEM, ERR_NONPHYSICAL, ERR_TIMEOUT, ERR_BUSY, ERR_CUDA = r
 BC_TRANSMISSIVE, BC_PERIODIC = 0, 1
 FLUX_ROE, FLUX_VANLEER = 0, 1
 FP64, FP32 = 0, 1
+W_TENO, W_JS, W_LINEAR, W_Z = 0, 1, 2, 3
+SCALAR_ADVECTION, SCALAR_BURGERS = 0, 1
 
 
 class WcnsError(RuntimeError):
@@ -31,7 +33,8 @@ class Grid(C.Structure):
 class SchemeParams(C.Structure):
     _fields_ = [("flux", C.c_int), ("diff", C.c_int), ("weights", C.c_int), ("C", C.c_double),
                 ("eps", C.c_double), ("CT", C.c_double), ("q", C.c_int), ("characteristic", C.c_int),
-                ("precision", C.c_int), ("cfl", C.c_double), ("entropy_fix", C.c_int)]
+                ("precision", C.c_int), ("cfl", C.c_double), ("entropy_fix", C.c_int),
+                ("eps_js", C.c_double)]
 
 
 _lib = None
@@ -223,6 +226,56 @@ def step_rk3_noalloc(grid, gamma, params, U, dt=0.0, want_dt=False, stream=None)
     check(fn(C.byref(grid), float(gamma), C.byref(params), _ptr(U), float(dt),
              C.byref(d) if want_dt else None, _stream(stream)))
     return d.value if want_dt else None
+
+
+def _scalar_lines(u):
+    if u.dim() == 1:
+        return 1, u.shape[0], u.shape[0]
+    if u.dim() != 2 or u.stride(1) != 1:
+        raise ValueError("u must be (n,) or (count, n) with unit stride along n")
+    return u.shape[0], u.shape[1], u.stride(0)
+
+
+def _scalar_fns():
+    L = lib()
+    vp = C.c_void_p
+    L.wcns_scalar_max_nodes.restype = C.c_int
+    L.wcns_scalar_rhs.argtypes = [C.c_int, C.POINTER(SchemeParams), C.c_int, C.c_double, C.c_int, vp,
+                                  C.c_longlong, vp, vp]
+    L.wcns_scalar_run.argtypes = [C.c_int, C.POINTER(SchemeParams), C.c_int, C.c_double, C.c_double,
+                                  C.c_int, C.c_int, vp, C.c_longlong, vp]
+    L.wcns_scalar_rhs.restype = C.c_int
+    L.wcns_scalar_run.restype = C.c_int
+    return L
+
+
+def scalar_max_nodes():
+    """Largest line the scalar solver accepts on the current device."""
+    return _scalar_fns().wcns_scalar_max_nodes()
+
+
+def scalar_rhs(kind, u, h, L=None, stream=None, **params):
+    """wcns_scalar_rhs: L = -f'(u) (Eq. 6 flux, Eq. 3 derivative) for each
+    periodic line of u, a float64 CUDA tensor of shape (n,) or (count, n)."""
+    count, n, ld = _scalar_lines(u)
+    if L is None:
+        L = u.new_empty(u.shape)
+    if L.shape != u.shape or L.stride() != u.stride():
+        raise ValueError("L must have the layout of u")
+    p = default_params(**params)
+    check(_scalar_fns().wcns_scalar_rhs(int(kind), C.byref(p), n, float(h), count, _ptr(u), ld, _ptr(L),
+                                        _stream(stream)))
+    return L
+
+
+def scalar_run(kind, u, h, t_end, nsteps, stream=None, **params):
+    """wcns_scalar_run: nsteps SSP-RK3 steps of size t_end / nsteps on each
+    periodic line of u (float64 CUDA tensor (n,) or (count, n)), in place."""
+    count, n, ld = _scalar_lines(u)
+    p = default_params(**params)
+    check(_scalar_fns().wcns_scalar_run(int(kind), C.byref(p), n, float(h), float(t_end), int(nsteps), count,
+                                        _ptr(u), ld, _stream(stream)))
+    return u
 
 
 class Batch:

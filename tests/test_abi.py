@@ -34,6 +34,7 @@ def test_default_params_are_the_papers():
     assert (p.C, p.eps, p.CT, p.q) == (1.0, 1e-40, 1e-5, 6)   # Eq. 16, Sec. 2.3
     assert p.characteristic == 1 and p.weights == 0 and p.diff == 0
     assert p.precision == wcns.FP64
+    assert p.eps_js == 1e-6                                    # Eq. 14
 
 
 def _create(grid, gamma=1.4, **kw):
@@ -46,7 +47,9 @@ def _create(grid, gamma=1.4, **kw):
 @pytest.mark.parametrize("bad", [
     dict(ndim=0), dict(ndim=4), dict(gamma=1.0), dict(q=0), dict(CT=0.5), dict(C=0.0),
     dict(flux=7), dict(characteristic=0), dict(entropy_fix=1), dict(precision=3), dict(cfl=0.0),
-    dict(n=(1,)), dict(half_periodic=True)])
+    dict(n=(1,)), dict(half_periodic=True), dict(weights=4), dict(weights=-1),
+    dict(weights=wcns.W_JS, precision=wcns.FP32), dict(weights=wcns.W_Z, precision=wcns.FP32),
+    dict(weights=wcns.W_JS, eps_js=0.0)])
 def test_create_rejects_bad_arguments_without_a_gpu(bad):
     ndim = bad.get("ndim", 1)
     n = bad.get("n", (16,))
@@ -67,3 +70,27 @@ def test_null_arguments_are_rejected():
     assert L.wcns_rhs(None, None, None, None, None) == wcns.ERR_INVALID
     assert L.wcns_step_rk3(None, None, 0.0, None, None) == wcns.ERR_INVALID
     assert L.wcns_destroy(None) == wcns.OK
+
+
+@pytest.mark.parametrize("bad", [
+    dict(kind=2), dict(kind=-1), dict(n=0), dict(count=0), dict(ld=15), dict(h=0.0),
+    dict(h=float("nan")), dict(precision=wcns.FP32), dict(weights=9), dict(q=0), dict(null=True)])
+def test_scalar_entry_points_validate_before_touching_a_gpu(bad):
+    L = wcns._scalar_fns()
+    p = wcns.default_params(**{k: v for k, v in bad.items() if k in ("precision", "weights", "q")})
+    kind, n, count = bad.get("kind", 0), bad.get("n", 16), bad.get("count", 1)
+    ld, h = bad.get("ld", 16), bad.get("h", 1.0 / 16)
+    ptr = None if bad.get("null") else C.c_void_p(16)   # never dereferenced: rejected first
+    assert L.wcns_scalar_rhs(kind, C.byref(p), n, h, count, ptr, ld, ptr, None) == wcns.ERR_INVALID
+    assert L.wcns_scalar_run(kind, C.byref(p), n, h, 1.0, 4, count, ptr, ld, None) == wcns.ERR_INVALID
+    assert len(wcns.lib().wcns_last_error()) > 0
+
+
+def test_scalar_run_rejects_bad_time_arguments():
+    L = wcns._scalar_fns()
+    p = wcns.default_params()
+    ptr = C.c_void_p(16)
+    assert L.wcns_scalar_run(0, C.byref(p), 16, 0.1, 1.0, -1, 1, ptr, 16, None) == wcns.ERR_INVALID
+    assert L.wcns_scalar_run(0, C.byref(p), 16, 0.1, float("inf"), 4, 1, ptr, 16, None) == wcns.ERR_INVALID
+    # zero steps is a no-op that touches nothing
+    assert L.wcns_scalar_run(0, C.byref(p), 16, 0.1, 1.0, 0, 1, ptr, 16, None) == wcns.OK

@@ -249,10 +249,13 @@ def test_table2_gaussian_advection(N):
         assert got["tcns"] == pytest.approx(got["linear"], rel=1e-6)
 
 
-@pytest.mark.parametrize("N", [41, 81, 161])
+@pytest.mark.parametrize("N", [41, 81, 161, 321, 641])
 def test_table3_burgers(N):
     """L_inf errors of Table 3 (Sec. 3.3) at t = 0.2 against the exact
-    characteristic solution."""
+    characteristic solution, all four columns, every printed N.  The step is
+    dt = 0.1 h / max|u0| (max|u0| = 1.5): the paper's finest-grid entries
+    carry its own time error, which this step reproduces to 0.5%, while a
+    refined step moves the N = 641 entries by 16%."""
     tab = _table("table3_burgers_linf.txt")[N]
     n = N - 1
     h = 2.0 / n
@@ -260,11 +263,11 @@ def test_table3_burgers(N):
     u0f = lambda z: 0.5 + np.sin(np.pi * z)
     du0 = lambda z: np.pi * np.cos(np.pi * z)
     ue = burgers_exact(x, 0.2, u0f, du0)
-    steps = int(math.ceil(0.2 / (0.05 * h / 1.5)))
-    for key, w in (("tcns", O.W_TENO), ("js", O.W_JS), ("z", O.W_Z)):
+    steps = int(math.ceil(0.2 / (0.1 * h / 1.5)))
+    for key, w in (("tcns", O.W_TENO), ("linear", O.W_LINEAR), ("js", O.W_JS), ("z", O.W_Z)):
         u = O.scalar_run(O.make_cfg(weights=w), 1, u0f(x), h, 0.2, steps)
         err = np.max(np.abs(u - ue))
-        assert abs(err / tab[key] - 1) < 0.015, (key, err, tab[key])
+        assert abs(err / tab[key] - 1) < 0.006, (key, err, tab[key])
 
 
 def test_rk3_step_is_third_order_taylor_polynomial():
