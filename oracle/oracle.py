@@ -9,7 +9,8 @@ import numpy as np
 
 from . import build as _build
 
-FLUX_ROE, FLUX_VANLEER = 0, 1
+FLUX_ROE, FLUX_VANLEER, FLUX_AUSM = 0, 1, 2
+DIFF_MD, DIFF_HWCNS, DIFF_MND = 0, 1, 2
 W_TENO, W_JS, W_LINEAR, W_Z = 0, 1, 2, 3
 
 _dp = C.POINTER(C.c_double)
@@ -21,7 +22,7 @@ class OraCfg(C.Structure):
         ("ndim", C.c_int), ("n", C.c_int * 3), ("h", C.c_double * 3), ("periodic", C.c_int * 3),
         ("gamma", C.c_double), ("flux", C.c_int), ("weights", C.c_int),
         ("C", C.c_double), ("eps", C.c_double), ("CT", C.c_double), ("q", C.c_int),
-        ("eps_js", C.c_double), ("characteristic", C.c_int),
+        ("eps_js", C.c_double), ("characteristic", C.c_int), ("diff", C.c_int),
     ]
 
 
@@ -42,6 +43,9 @@ def lib():
         L.ora_roe_eigen.argtypes = [C.c_int, C.c_int, C.c_double, _dp, _dp, _dp, _dp, _dp]
         L.ora_roe_flux.argtypes = [C.c_int, C.c_int, C.c_double, _dp, _dp, _dp]
         L.ora_vanleer_half.argtypes = [C.c_int, C.c_int, C.c_double, _dp, C.c_int, _dp]
+        L.ora_ausm_flux.argtypes = [C.c_int, C.c_int, C.c_double, _dp, _dp, _dp]
+        L.ora_ausm_split.argtypes = [C.c_double, C.c_double, C.c_int, _dp, _dp]
+        L.ora_diff_coeffs.argtypes = [C.c_int, _dp]
         L.ora_flags_offset.restype = C.c_long
         L.ora_flags_offset.argtypes = [C.POINTER(OraCfg), C.c_int]
         L.ora_flags_size.restype = C.c_long
@@ -73,9 +77,9 @@ def _p(a):
 
 def make_cfg(ndim=1, n=(1, 1, 1), h=(1.0, 1.0, 1.0), periodic=(0, 0, 0), gamma=1.4,
              flux=FLUX_ROE, weights=W_TENO, C_=1.0, eps=1e-40, CT=1e-5, q=6, eps_js=1e-6,
-             characteristic=1):
+             characteristic=1, diff=DIFF_MD):
     """Scheme constants default to the paper's: C = 1, eps = 1e-40, q = 6 (Eq. 16),
-    C_T = 1e-5 (Sec. 2.3), JS eps = 1e-6 (Eq. 14)."""
+    C_T = 1e-5 (Sec. 2.3), JS eps = 1e-6 (Eq. 14), MD differencing (Eq. 3)."""
     c = OraCfg()
     c.ndim = ndim
     for a in range(3):
@@ -84,6 +88,7 @@ def make_cfg(ndim=1, n=(1, 1, 1), h=(1.0, 1.0, 1.0), periodic=(0, 0, 0), gamma=1
         c.periodic[a] = int(periodic[a]) if a < len(periodic) else 0
     c.gamma, c.flux, c.weights = gamma, flux, weights
     c.C, c.eps, c.CT, c.q, c.eps_js, c.characteristic = C_, eps, CT, q, eps_js, characteristic
+    c.diff = diff
     return c
 
 
@@ -109,6 +114,27 @@ def md_coeffs():
     a = np.zeros(3)
     lib().ora_md_coeffs(_p(a))
     return a
+
+
+def diff_coeffs(diff):
+    """Coefficients of Eq. 3, 4 or 5 as the oracle uses them."""
+    a = np.zeros(3)
+    lib().ora_diff_coeffs(int(diff), _p(a))
+    return a
+
+
+def ausm_flux(nd, d, gamma, UL, UR):
+    F = np.zeros(nd + 2)
+    lib().ora_ausm_flux(nd, d, gamma, _p(np.ascontiguousarray(UL, dtype=np.float64)),
+                        _p(np.ascontiguousarray(UR, dtype=np.float64)), _p(F))
+    return F
+
+
+def ausm_split(M, p, sign):
+    """(M^+-, p^+-) of one side (sign = +1 or -1)."""
+    Ms, ps = C.c_double(), C.c_double()
+    lib().ora_ausm_split(float(M), float(p), int(sign), C.byref(Ms), C.byref(ps))
+    return Ms.value, ps.value
 
 
 def phys_flux(nd, d, gamma, U):

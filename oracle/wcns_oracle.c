@@ -15,6 +15,7 @@
  * What it computes, step by step, in the paper's order:
  *   Eq. 2    du_i/dt = -f'_i, summed over directions (dimension by dimension)
  *   Eq. 3    sixth-order explicit midpoint-to-node difference (MD)
+ *   Eq. 4-5  the HWCNS and MND alternatives (midpoint and node fluxes)
  *   Eq. 6    scalar upwind midpoint flux (scalar problems)
  *   Eq. 8-11 three 3-point sub-stencils and their Taylor interpolants
  *   Eq. 12-13 convex combination, optimal weights d = (1, 10, 5)/16
@@ -23,13 +24,22 @@
  *            (cited, not printed): alpha_k = d_k (1 + tau_5 / (beta_k + eps))
  *   Eq. 16-19 TENO scale separation gamma_k, normalisation chi_k, sharp
  *            cutoff delta_k, and the final weights omega_k^(T)
- *   Sec. 3   characteristic-variable interpolation, ideal gas, van Leer or
- *            Roe midpoint flux, third-order SSP Runge-Kutta under a CFL rule.
+ *   Sec. 3   characteristic-variable interpolation, ideal gas, van Leer,
+ *            Roe or AUSM midpoint flux (Sec. 1 names all three), third-order
+ *            SSP Runge-Kutta under a CFL rule.
  *
  * Readings of points the paper leaves open (each one is listed in the
  * design notes with its reason):
  *   - MD coefficients a = (75/64, -25/384, 3/640): sixth-order Taylor
- *     matching of Eq. 3 (the paper defers them to its references).
+ *     matching of Eq. 3 (the paper defers them to its references); by the
+ *     same matching b = (64/45, -2/9, 1/180) for Eq. 4 and
+ *     c = (3/2, -3/10, 1/30) for Eq. 5.  The node fluxes of Eq. 4-5 are the
+ *     physical fluxes of the node states.
+ *   - AUSM is the original advection upstream splitting of Liou and
+ *     Steffen (1993): interface Mach number M_L^+ + M_R^- and pressure
+ *     p_L^+ + p_R^- from the second- and third-degree Mach polynomials,
+ *     each side with its own speed of sound, the convected vector upwinded
+ *     by the sign of the interface Mach number.
  *   - The characteristic projection uses the eigenvectors of the flux
  *     Jacobian at the Roe average of the two nodes that bound the face; the
  *     same projection serves the left- and right-biased interpolations.
@@ -54,7 +64,8 @@
 #define ORA_GHOST 5
 
 /* Scheme switches (the oracle's own numbering). */
-enum { ORA_FLUX_ROE = 0, ORA_FLUX_VANLEER = 1 };
+enum { ORA_FLUX_ROE = 0, ORA_FLUX_VANLEER = 1, ORA_FLUX_AUSM = 2 };
+enum { ORA_DIFF_MD = 0, ORA_DIFF_HWCNS = 1, ORA_DIFF_MND = 2 };
 enum { ORA_W_TENO = 0, ORA_W_JS = 1, ORA_W_LINEAR = 2, ORA_W_Z = 3 };
 
 typedef struct {
@@ -69,6 +80,7 @@ typedef struct {
     int q;                /* Eq. 16: 6                                   */
     double eps_js;        /* Eq. 14: 1e-6                                */
     int characteristic;   /* 1 = interpolate characteristic variables    */
+    int diff;             /* ORA_DIFF_*: Eq. 3, 4 or 5                   */
 } ora_cfg;
 
 /* ------------------------------------------------------------------ */
@@ -80,6 +92,35 @@ static const double MD_A2 = -25.0 / 384.0;
 static const double MD_A3 = 3.0 / 640.0;
 
 void ora_md_coeffs(double a[3]) { a[0] = MD_A1; a[1] = MD_A2; a[2] = MD_A3; }
+
+/* Eq. 4 (HWCNS): f'_i h = b1 (f_{i+1/2} - f_{i-1/2}) + b2 (f_{i+1} - f_{i-1})
+ * + b3 (f_{i+2} - f_{i-2}); half-widths 1/2, 1, 2.  Eq. 5 (MND): c1 (...)
+ * + c2 (f_{i+1} - f_{i-1}) + c3 (f_{i+3/2} - f_{i-3/2}); half-widths 1/2, 1,
+ * 3/2.  Both from sum coef_m (2 w_m) w_m^(p-1) = [p = 1], p = 1, 3, 5. */
+static const double HW_B1 = 64.0 / 45.0;
+static const double HW_B2 = -2.0 / 9.0;
+static const double HW_B3 = 1.0 / 180.0;
+static const double MND_C1 = 3.0 / 2.0;
+static const double MND_C2 = -3.0 / 10.0;
+static const double MND_C3 = 1.0 / 30.0;
+
+void ora_diff_coeffs(int diff, double c[3])
+{
+    if (diff == ORA_DIFF_HWCNS) { c[0] = HW_B1; c[1] = HW_B2; c[2] = HW_B3; }
+    else if (diff == ORA_DIFF_MND) { c[0] = MND_C1; c[1] = MND_C2; c[2] = MND_C3; }
+    else { c[0] = MD_A1; c[1] = MD_A2; c[2] = MD_A3; }
+}
+
+/* f'_i h from the six midpoint fluxes fm[0..5] = f_{i-5/2} .. f_{i+5/2} and
+ * the five node fluxes fn[0..4] = f_{i-2} .. f_{i+2} by Eq. 3, 4 or 5. */
+static double diff_node(int diff, const double fm[6], const double fn[5])
+{
+    if (diff == ORA_DIFF_HWCNS)
+        return HW_B1 * (fm[3] - fm[2]) + HW_B2 * (fn[3] - fn[1]) + HW_B3 * (fn[4] - fn[0]);
+    if (diff == ORA_DIFF_MND)
+        return MND_C1 * (fm[3] - fm[2]) + MND_C2 * (fn[3] - fn[1]) + MND_C3 * (fm[4] - fm[1]);
+    return MD_A1 * (fm[3] - fm[2]) + MD_A2 * (fm[4] - fm[1]) + MD_A3 * (fm[5] - fm[0]);
+}
 
 /* ------------------------------------------------------------------ */
 /* Eq. 10-11 times h and h^2 (the h-free forms), Eq. 9, Eq. 15.        */
@@ -357,6 +398,59 @@ void ora_vanleer_half(int nd, int d, double gamma, const double* U, int sign, do
     vanleer_half(nd, d, gamma, U, sign, F);
 }
 
+/* AUSM (Liou and Steffen 1993).  Split Mach numbers and pressures of one
+ * side: M+- = +-(M +- 1)^2 / 4 and p+- = p (M +- 1)^2 (2 -+ M) / 4 when
+ * |M| <= 1, otherwise the upwind values (M +- |M|) / 2 and p (M +- |M|) / (2 M).
+ * F = m (Phi_L + Phi_R) / 2 - |m| (Phi_R - Phi_L) / 2 + (0, p_n, 0) with
+ * m = M_L^+ + M_R^-, p_n = p_L^+ + p_R^- on the normal momentum, and
+ * Phi = rho c (1, u_1 .. u_nd, H). */
+static void ausm_split(double M, double p, int sign, double* Ms, double* ps)
+{
+    const double s = (double)sign;
+    if (fabs(M) <= 1.0) {
+        *Ms = s * 0.25 * (M + s) * (M + s);
+        *ps = 0.25 * p * (M + s) * (M + s) * (2.0 - s * M);
+    } else {
+        *Ms = 0.5 * (M + s * fabs(M));
+        *ps = 0.5 * p * (M + s * fabs(M)) / M;
+    }
+}
+
+static void ausm_flux(int nd, int d, double gamma, const double* UL, const double* UR, double* F)
+{
+    const int nv = nd + 2;
+    const double* U[2] = {UL, UR};
+    double Phi[2][ORA_MAXV], M[2], p[2];
+    for (int side = 0; side < 2; ++side) {
+        const double* W = U[side];
+        const double rho = W[0];
+        p[side] = pressure(nd, gamma, W);
+        const double c = sqrt(gamma * p[side] / rho);
+        M[side] = (W[1 + d] / rho) / c;
+        const double rc = rho * c;
+        Phi[side][0] = rc;
+        for (int a = 0; a < nd; ++a) Phi[side][1 + a] = rc * (W[1 + a] / rho);
+        Phi[side][nv - 1] = rc * ((W[nv - 1] + p[side]) / rho);
+    }
+    double Mp, pp, Mm, pm;
+    ausm_split(M[0], p[0], +1, &Mp, &pp);
+    ausm_split(M[1], p[1], -1, &Mm, &pm);
+    const double m = Mp + Mm;
+    for (int v = 0; v < nv; ++v)
+        F[v] = 0.5 * m * (Phi[0][v] + Phi[1][v]) - 0.5 * fabs(m) * (Phi[1][v] - Phi[0][v]);
+    F[1 + d] += pp + pm;
+}
+
+void ora_ausm_flux(int nd, int d, double gamma, const double* UL, const double* UR, double* F)
+{
+    ausm_flux(nd, d, gamma, UL, UR, F);
+}
+
+void ora_ausm_split(double M, double p, int sign, double* Ms, double* ps)
+{
+    ausm_split(M, p, sign, Ms, ps);
+}
+
 void ora_roe_flux(int nd, int d, double gamma, const double* UL, const double* UR, double* F)
 {
     roe_flux(nd, d, gamma, UL, UR, F);
@@ -424,6 +518,8 @@ static void face_flux(const ora_cfg* cfg, int d, const double* P, int j, double*
     }
     if (cfg->flux == ORA_FLUX_ROE) {                            /* A6 */
         roe_flux(nd, d, cfg->gamma, UL, UR, F);
+    } else if (cfg->flux == ORA_FLUX_AUSM) {
+        ausm_flux(nd, d, cfg->gamma, UL, UR, F);
     } else {
         double Fp[ORA_MAXV], Fm[ORA_MAXV];
         vanleer_half(nd, d, cfg->gamma, UL, +1, Fp);
@@ -469,17 +565,24 @@ static void euler_line(const ora_cfg* cfg, int d, const double* line, long node_
             if (margin) margin[k * fl_field_stride + f] = mg[k];
         }
     }
-    /* A7: Eq. 3.  Node i: faces i+1/2 -> f = i+3, i-1/2 -> i+2, i+3/2 -> i+4,
-     * i-3/2 -> i+1, i+5/2 -> i+5, i-5/2 -> i. */
+    /* A7: Eq. 3 (or 4, 5).  Node i: faces i-5/2 .. i+5/2 are f = i .. i+5;
+     * the node fluxes of Eq. 4-5 are the physical fluxes of nodes i-2..i+2. */
+    double* Fn = NULL;
+    if (cfg->diff != ORA_DIFF_MD) {
+        Fn = (double*)malloc(sizeof(double) * (n + 4) * nv);   /* nodes -2 .. n+1 */
+        for (int m = -2; m < n + 2; ++m)
+            phys_flux(nd, d, cfg->gamma, &P[(m + ORA_GHOST) * nv], &Fn[(m + 2) * nv]);
+    }
     const double ih = 1.0 / cfg->h[d];
     for (int i = 0; i < n; ++i) {
         for (int v = 0; v < nv; ++v) {
-            double fp = MD_A1 * (Fc[(i + 3) * nv + v] - Fc[(i + 2) * nv + v])
-                      + MD_A2 * (Fc[(i + 4) * nv + v] - Fc[(i + 1) * nv + v])
-                      + MD_A3 * (Fc[(i + 5) * nv + v] - Fc[(i + 0) * nv + v]);
-            Lout[i * node_stride + v * var_stride] -= fp * ih;  /* Eq. 2 */
+            double fm[6], fn[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+            for (int k = 0; k < 6; ++k) fm[k] = Fc[(i + k) * nv + v];
+            if (Fn) for (int k = 0; k < 5; ++k) fn[k] = Fn[(i + k) * nv + v];
+            Lout[i * node_stride + v * var_stride] -= diff_node(cfg->diff, fm, fn) * ih;  /* Eq. 2 */
         }
     }
+    free(Fn);
     free(P);
     free(Fc);
 }
@@ -713,9 +816,9 @@ void ora_scalar_rhs(const ora_cfg* cfg, int kind, int n, double h, const double*
         F[f] = 0.5 * ((scalar_f(kind, uR) + scalar_f(kind, uL)) - fabs(a) * (uR - uL)); /* Eq. 6 */
     }
     for (int i = 0; i < n; ++i) {
-        double fp = MD_A1 * (F[i + 3] - F[i + 2]) + MD_A2 * (F[i + 4] - F[i + 1])
-                  + MD_A3 * (F[i + 5] - F[i + 0]);
-        L[i] = -fp / h;
+        double fn[5];
+        for (int k = 0; k < 5; ++k) fn[k] = scalar_f(kind, u[((i - 2 + k) % n + n) % n]);
+        L[i] = -diff_node(cfg->diff, &F[i], fn) / h;
     }
     free(F);
 }
