@@ -9,7 +9,7 @@ RHS evaluations; value = nodes x 3 x steps x ranks / max-over-ranks time.
 The FP64 plain path is timed on the same workload and reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload tgv256|quad1024|sod400]
+                  [--workload tgv256|quad1024|sod400|batch1d|serve|scalar]
 
 With N > 1 (torchrun) every rank advances its own replica (weak scaling,
 no data-path collective: the instances are independent).
@@ -39,6 +39,13 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12     # SMs x FP64 FMA/clk x FMA x
 # op = 1) with every stencil taking the no-cut branch (smooth flow).
 FACE_FLOPS = {1: 520, 2: 770, 3: 1040}
 NODE_FLOPS = {1: 30, 2: 40, 3: 50}
+# FP64 operations per node per RHS of the scalar path (linear advection,
+# TCNS weights, every stencil on the no-cut branch), one flop per add, mul,
+# abs, min or divide (the fixed-order FP64 path contracts nothing into FMA):
+# two interpolations of 54 (sub-stencil derivatives 30, smoothness test 7,
+# Eq. 12 17), the Eq. 6 flux 6, the Eq. 3 difference and 1/h 10, and the
+# SSP-RK3 stage combination 4 on average.
+SCALAR_NODE_FLOPS = 2 * 54 + 6 + 10 + 4
 
 
 def parse():
@@ -48,7 +55,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tgv256",
-                    choices=["tgv256", "quad1024", "sod400", "batch1d", "serve"])
+                    choices=["tgv256", "quad1024", "sod400", "batch1d", "serve", "scalar"])
     ap.add_argument("--requests", type=int, default=32, help="serve: requests replayed from the trace")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrival rate (1/s)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain-path line")
@@ -472,8 +479,160 @@ def serve_arm(args):
         "all_ok": all(got[i]["status"] == 0 for i in range(len(trace)))}))
 
 
+SCALAR_N, SCALAR_LINES, SCALAR_STEPS_PER_CALL = 1600, 152 * 8, 100
+
+
+def scalar_lines():
+    """Gaussian pulses exp(-300 (x - c)^2) of Table 2's finest grid (N = 1601,
+    1600 unique periodic nodes on [0, 1)), centres c ~ U[0.3, 0.7] (seed 1810)."""
+    import numpy as np
+    h = 1.0 / SCALAR_N
+    x = h * np.arange(SCALAR_N)
+    c = np.random.default_rng(1810).uniform(0.3, 0.7, (SCALAR_LINES, 1))
+    return np.exp(-300.0 * (x[None, :] - c) ** 2), h
+
+
+def scalar_oracle_rate(h, u, budget_s):
+    """The FP64 oracle's scalar solver on one line, steps doubled until about
+    budget_s of CPU work; returns node-RHS evaluations per second."""
+    from oracle import oracle as O
+    cfg = O.make_cfg()
+    steps, total_t, total = 8, 0.0, 0.0
+    while total_t < budget_s:
+        t0 = time.perf_counter()
+        O.scalar_run(cfg, 0, u, h, steps * 0.01 * h, steps)
+        dt = time.perf_counter() - t0
+        total_t += dt
+        total += u.size * 3 * steps
+        steps *= 2
+    return total / total_t, total_t, total
+
+
+def scalar_arm(args):
+    """Scalar path (linear advection, TCNS, FP64): 1216 independent lines of
+    Table 2's finest grid; one bench step = 100 SSP-RK3 steps of every line
+    in one launch (dt = 0.01 h).  Also the time to reproduce Table 2's
+    N = 1601 TCNS entry (t = 1, 160000 steps) on one line."""
+    import numpy as np
+    import torch
+    from paper_1810_07806_gb300 import wcns
+    U0, h = scalar_lines()
+    nodes = U0.size
+    k = SCALAR_STEPS_PER_CALL
+    t_call = k * 0.01 * h
+    dev = torch.device("cuda", 0)
+    U = torch.from_numpy(U0).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(max(3, args.warmup)):
+        wcns.scalar_run(wcns.SCALAR_ADVECTION, U, h, t_call, k)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0])
+    clocks.start()
+    total_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        wcns.scalar_run(wcns.SCALAR_ADVECTION, U, h, t_call, k)
+        e1.record()
+        torch.cuda.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    clk = clocks.stop()
+    ms = total_ms / args.steps
+    value = nodes * 3 * k / ms * 1e3
+    # end to end: host state in, k steps, host state out, every bench step
+    host = torch.from_numpy(U0.copy()).pin_memory()
+    out = torch.empty_like(host).pin_memory()
+    Ud = torch.empty_like(U)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        Ud.copy_(host, non_blocking=True)
+        wcns.scalar_run(wcns.SCALAR_ADVECTION, Ud, h, t_call, k)
+        out.copy_(Ud, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e = nodes * 3 * k * args.steps / (time.perf_counter() - t0)
+    nbytes = U0.size * 8
+    # Table 2, N = 1601, TCNS, t = 1 on one line
+    x = h * np.arange(SCALAR_N)
+    u0 = np.exp(-300.0 * (x - 0.5) ** 2)
+    one = torch.from_numpy(u0.copy()).to(dev)
+    nsteps = int(math.ceil(1.0 / (0.01 * h)))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    wcns.scalar_run(wcns.SCALAR_ADVECTION, one, h, 1.0, nsteps)
+    e1.record()
+    torch.cuda.synchronize()
+    t2_ms = e0.elapsed_time(e1)
+    t2_err = float(np.max(np.abs(one.cpu().numpy() - u0)))
+    achieved = value * SCALAR_NODE_FLOPS / 1e12
+    cpu = None
+    if not args.no_cpu:
+        rate, secs, work = scalar_oracle_rate(h, u0, 10.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "one 1600-node line, %.3g node-RHS evaluations in %.1f s (the scalar oracle "
+                         "is single-threaded)" % (work, secs)}
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "gaussian_advection_1d_periodic_%dx%d_lines" % (SCALAR_LINES, SCALAR_N),
+                   "weights": "tcns", "rk3_steps_per_bench_step": k, "dt": "0.01 h",
+                   "l2": "flushed (256 MiB write) between timed steps",
+                   "launch": "one cluster launch per bench step (16-CTA clusters, line resident in DSMEM)"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "scalar_kernel (whole run on chip)",
+                     "flops_per_node_rhs": SCALAR_NODE_FLOPS,
+                     "peak_note": "FP64 FMA peak derived from 152 SMs x 2 FP64 FMA/clk x 2070 MHz; "
+                                  "the fixed-order path issues no FMA, so 0.5 is its ceiling"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "gpu_launches": args.steps, "clocks": clk,
+        "table2_n1601_tcns": {"ms": t2_ms, "rk3_steps": nsteps, "linf_error": t2_err,
+                              "printed": 3.64e-9},
+    }))
+
+
+def scalar_reference_arm(args):
+    """The oracle's scalar solver on this host, each bench step a bounded
+    sample (one line, a few RK3 steps) of the same workload."""
+    U0, h = scalar_lines()
+    from oracle import oracle as O
+    cfg = O.make_cfg()
+    budget = max(0.2, 150.0 / max(1, args.steps + args.warmup))
+    steps = 4
+    t0 = time.perf_counter()
+    O.scalar_run(cfg, 0, U0[0], h, steps * 0.01 * h, steps)
+    steps = max(1, int(steps * budget / max(time.perf_counter() - t0, 1e-4)))
+    for _ in range(args.warmup):
+        O.scalar_run(cfg, 0, U0[0], h, steps * 0.01 * h, steps)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.scalar_run(cfg, 0, U0[0], h, steps * 0.01 * h, steps)
+    el = time.perf_counter() - t0
+    value = SCALAR_N * 3 * steps * args.steps / el
+    sample = "one %d-node line, %d RK3 steps per bench step, FP64 oracle (single thread)" % (SCALAR_N, steps)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "gaussian_advection_1d_periodic_%dx%d_lines" % (SCALAR_LINES, SCALAR_N),
+                   "weights": "tcns", "precision": "fp64 (CPU oracle)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
 def main():
     args = parse()
+    if args.workload == "scalar":
+        if int(os.environ.get("RANK", "0")) == 0:
+            (scalar_arm if args.impl == "ours" else scalar_reference_arm)(args)
+        return
     if args.workload == "batch1d" and args.impl == "ours":
         return batch_arm(args)
     if args.workload == "serve" and args.impl == "ours":

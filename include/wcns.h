@@ -40,8 +40,14 @@ typedef enum {
 } wcns_status;
 
 enum { WCNS_BC_TRANSMISSIVE = 0, WCNS_BC_PERIODIC = 1 };
-enum { WCNS_FLUX_ROE = 0, WCNS_FLUX_VANLEER = 1 };
-enum { WCNS_DIFF_MD6 = 0 };
+/* Midpoint flux (Sec. 1 names all three): Roe flux-difference splitting,
+ * van Leer flux-vector splitting, Liou-Steffen AUSM. */
+enum { WCNS_FLUX_ROE = 0, WCNS_FLUX_VANLEER = 1, WCNS_FLUX_AUSM = 2 };
+/* Midpoint-to-node difference: Eq. 3 (MD, a = 75/64, -25/384, 3/640), Eq. 4
+ * (HWCNS, b = 64/45, -2/9, 1/180 on midpoints i+-1/2 and the physical fluxes
+ * of nodes i+-1, i+-2) or Eq. 5 (MND, c = 3/2, -3/10, 1/30 on midpoints
+ * i+-1/2, i+-3/2 and nodes i+-1); all sixth order. */
+enum { WCNS_DIFF_MD6 = 0, WCNS_DIFF_HWCNS = 1, WCNS_DIFF_MND = 2 };
 /* Interpolation weights: TENO selection (Eq. 16-19, the paper's scheme),
  * WCNS-JS (Eq. 14), linear (the optimal weights d_k of Eq. 13, i.e. Eq. 7)
  * and WCNS-Z (the weights of Borges et al. that the paper compares with,
@@ -67,8 +73,8 @@ typedef struct {
  * C_T = 1e-5 (Sec. 2.3), characteristic interpolation (Sec. 3), sixth-order
  * MD differencing (Eq. 3), Roe flux, FP64, CFL 0.5. */
 typedef struct {
-    int flux;            /* WCNS_FLUX_ROE | WCNS_FLUX_VANLEER                 */
-    int diff;            /* WCNS_DIFF_MD6                                     */
+    int flux;            /* WCNS_FLUX_ROE | WCNS_FLUX_VANLEER | WCNS_FLUX_AUSM */
+    int diff;            /* WCNS_DIFF_MD6 | WCNS_DIFF_HWCNS | WCNS_DIFF_MND    */
     int weights;         /* WCNS_W_TENO | _JS | _LINEAR | _Z                  */
     double C, eps, CT;   /* Eq. 16 and Eq. 18 constants (eps also serves Z)   */
     int q;               /* Eq. 16 power, 1..16                               */
@@ -302,7 +308,9 @@ wcns_status wcns_server_stats(wcns_server* sv, wcns_server_stats_t* stats);
  * approximate eigenvalue a = 1 (advection) or a = (u_L + u_R) / 2
  * (Burgers); u_L and u_R come from the node-to-midpoint interpolation of
  * Sec. 2.2 with the weights params->weights selects (no characteristic
- * projection: there is one field); the derivative is Eq. 3.  FP64 only.
+ * projection: there is one field); the derivative is Eq. 3, 4 or 5 as
+ * params->diff selects (node fluxes f(u_i)).  params->flux is not used.
+ * FP64 only.
  *
  * `count` independent lines of n unique nodes each (periodic: node n is
  * node 0; h is the node spacing) sit in device memory at u + i * ld,

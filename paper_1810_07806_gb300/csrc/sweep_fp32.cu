@@ -48,6 +48,7 @@ cudaError_t WCNS_CAT(launch_sweep_fp32_cfg, SWEEP_CFG)(int nd, int dir, int flux
                                                         cudaStream_t s)
 {
     return flux == FLUX_ROE ? dispatch<FLUX_ROE>(nd, dir, a, s, false)
+                            : flux == FLUX_AUSM ? dispatch<FLUX_AUSM>(nd, dir, a, s, false)
                             : dispatch<FLUX_VANLEER>(nd, dir, a, s, false);
 }
 
@@ -56,9 +57,10 @@ cudaError_t WCNS_CAT(prepare_sweeps_fp32_cfg, SWEEP_CFG)()
     SweepArgs a{};
     for (int nd = SWEEP_CFG == 0 ? 1 : 2; nd <= 3; ++nd)
         for (int d = 0; d < nd; ++d)
-            for (int f = 0; f < 2; ++f) {
+            for (int f = 0; f < 3; ++f) {
                 cudaError_t e = f == 0 ? dispatch<FLUX_ROE>(nd, d, a, 0, true)
-                                       : dispatch<FLUX_VANLEER>(nd, d, a, 0, true);
+                                       : f == 1 ? dispatch<FLUX_VANLEER>(nd, d, a, 0, true)
+                                       : dispatch<FLUX_AUSM>(nd, d, a, 0, true);
                 if (e != cudaSuccess) return e;
             }
     return cudaSuccess;

@@ -37,6 +37,7 @@ static cudaError_t dispatch(int nd, int dir, const SweepArgs& a, cudaStream_t s,
 cudaError_t launch_sweep_fp64(int nd, int dir, int flux, const SweepArgs& a, cudaStream_t s)
 {
     return flux == FLUX_ROE ? dispatch<FLUX_ROE>(nd, dir, a, s, false)
+                            : flux == FLUX_AUSM ? dispatch<FLUX_AUSM>(nd, dir, a, s, false)
                             : dispatch<FLUX_VANLEER>(nd, dir, a, s, false);
 }
 
@@ -48,9 +49,10 @@ cudaError_t prepare_sweeps_fp64()
     SweepArgs a{};
     for (int nd = 1; nd <= 3; ++nd)
         for (int d = 0; d < nd; ++d)
-            for (int f = 0; f < 2; ++f) {
+            for (int f = 0; f < 3; ++f) {
                 cudaError_t e = f == 0 ? dispatch<FLUX_ROE>(nd, d, a, 0, true)
-                                       : dispatch<FLUX_VANLEER>(nd, d, a, 0, true);
+                                       : f == 1 ? dispatch<FLUX_VANLEER>(nd, d, a, 0, true)
+                                       : dispatch<FLUX_AUSM>(nd, d, a, 0, true);
                 if (e != cudaSuccess) return e;
             }
     return cudaSuccess;

@@ -24,6 +24,16 @@ constexpr int GHOST = 5;   // node i reads nodes i-5 .. i+5
 constexpr double MD_A1 = 75.0 / 64.0;
 constexpr double MD_A2 = -25.0 / 384.0;
 constexpr double MD_A3 = 3.0 / 640.0;
+// Eq. 4 (HWCNS: midpoints i+-1/2, nodes i+-1, i+-2) and Eq. 5 (MND: midpoints
+// i+-1/2, nodes i+-1, midpoints i+-3/2), by the same sixth-order matching.
+constexpr double HW_B1 = 64.0 / 45.0;
+constexpr double HW_B2 = -2.0 / 9.0;
+constexpr double HW_B3 = 1.0 / 180.0;
+constexpr double MND_C1 = 3.0 / 2.0;
+constexpr double MND_C2 = -3.0 / 10.0;
+constexpr double MND_C3 = 1.0 / 30.0;
+// Midpoint-to-node formulas (values of the C ABI's WCNS_DIFF_*).
+enum { DIFF_MD = 0, DIFF_HWCNS = 1, DIFF_MND = 2 };
 
 // Table 1: coefficients (a_{i-2} .. a_{i+2}) of the single five-point
 // stencil equivalent to each retained set, indexed by the flag word
@@ -51,6 +61,7 @@ struct SchemeConst {
     int q;
     int weights;         // W_TENO | W_JS | W_LINEAR | W_Z
     double eps_js;       // epsilon of Eq. 14
+    int diff;            // DIFF_MD | DIFF_HWCNS | DIFF_MND
     double keep_all_K;   // tau < K * (min beta + eps) guarantees no cut (exact test)
     float Cf, CTf, Kf;
     float gammaf, gm1f;  // gamma, gamma - 1 in float
@@ -221,6 +232,45 @@ __device__ __forceinline__ void roe_flux(const T* UL, const T* UR, T pL, T pR, T
     Dm[ND + 1] = e;
 #pragma unroll
     for (int v = 0; v < NV; ++v) F[v] = T(0.5) * (FL[v] + FR[v] - Dm[v]);
+}
+
+// AUSM (Liou and Steffen 1993): interface Mach number M_L^+ + M_R^- and
+// pressure p_L^+ + p_R^- (second- and third-degree Mach polynomials for
+// |M| <= 1, upwind values outside), each side with its own speed of sound;
+// F = m (Phi_L + Phi_R)/2 - |m| (Phi_R - Phi_L)/2 + p_n e_D with
+// Phi = rho c (1, u, H).
+template <typename T>
+__device__ __forceinline__ void ausm_split(T M, T p, T s, T& Ms, T& ps)
+{
+    if (fabs(M) <= T(1)) {
+        const T a = (M + s) * (M + s);
+        Ms = s * T(0.25) * a;
+        ps = T(0.25) * p * a * (T(2) - s * M);
+    } else {
+        const T a = T(0.5) * (M + s * fabs(M));
+        Ms = a;
+        ps = p * a / M;
+    }
+}
+
+template <int ND, int D, typename T>
+__device__ __forceinline__ void ausm_flux(const T* UL, const T* UR, T pL, T pR, T gamma, T* F)
+{
+    constexpr int NV = ND + 2;
+    const T iL = T(1) / UL[0], iR = T(1) / UR[0];
+    const T cL = sqrt(gamma * pL * iL), cR = sqrt(gamma * pR * iR);
+    const T ML = UL[1 + D] * iL / cL, MR = UR[1 + D] * iR / cR;
+    T Mp, pp, Mm, pm;
+    ausm_split(ML, pL, T(1), Mp, pp);
+    ausm_split(MR, pR, T(-1), Mm, pm);
+    const T m = Mp + Mm;
+    // per-side weights of rho c: (m + |m|)/2 on the left, (m - |m|)/2 on the right
+    const T wl = T(0.5) * (m + fabs(m)) * cL, wr = T(0.5) * (m - fabs(m)) * cR;
+    F[0] = wl * UL[0] + wr * UR[0];
+#pragma unroll
+    for (int a = 0; a < ND; ++a) F[1 + a] = wl * UL[1 + a] + wr * UR[1 + a];
+    F[1 + D] += pp + pm;
+    F[NV - 1] = wl * (UL[NV - 1] + pL) + wr * (UR[NV - 1] + pR);
 }
 
 // van Leer (1982) flux vector splitting: F = F+(U_L) + F-(U_R).

@@ -333,6 +333,54 @@ __device__ __forceinline__ void vanleer_half_fp64(const double* U, double gamma,
     F[NV - 1] = mul_(fm, add_(div_(mul_(wn, wn), den), mul_(0.5, t2)));
 }
 
+// AUSM (Liou and Steffen 1993), one side's split Mach number and pressure
+// (s = +1: M+, p+ of the left state; s = -1: M-, p- of the right state).
+__device__ __forceinline__ void ausm_split_fp64(double M, double p, double s, double& Ms, double& ps)
+{
+    if (fabs(M) <= 1.0) {
+        const double a = add_(M, s);
+        Ms = mul_(mul_(mul_(s, 0.25), a), a);
+        ps = mul_(mul_(mul_(mul_(0.25, p), a), a), sub_(2.0, mul_(s, M)));
+    } else {
+        const double t = add_(M, mul_(s, fabs(M)));
+        Ms = mul_(0.5, t);
+        ps = div_(mul_(mul_(0.5, p), t), M);
+    }
+}
+
+// AUSM flux: F = m (Phi_L + Phi_R)/2 - |m| (Phi_R - Phi_L)/2 + (p_L^+ + p_R^-) e_D,
+// m = M_L^+ + M_R^-, Phi = rho c (1, u, H), each side with its own c.
+template <int ND, int D>
+__device__ __forceinline__ void ausm_flux_fp64(const double* UL, const double* UR, double gamma,
+                                               double gm1, double* F)
+{
+    constexpr int NV = ND + 2;
+    const double* W[2] = {UL, UR};
+    double Phi[2][NV], M[2], p[2];
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const double* X = W[side];
+        const double rho = X[0];
+        p[side] = pressure_exact<ND>(X, gm1);
+        const double c = __dsqrt_rn(div_(mul_(gamma, p[side]), rho));
+        M[side] = div_(div_(X[1 + D], rho), c);
+        const double rc = mul_(rho, c);
+        Phi[side][0] = rc;
+#pragma unroll
+        for (int a = 0; a < ND; ++a) Phi[side][1 + a] = mul_(rc, div_(X[1 + a], rho));
+        Phi[side][NV - 1] = mul_(rc, div_(add_(X[NV - 1], p[side]), rho));
+    }
+    double Mp, pp, Mm, pm;
+    ausm_split_fp64(M[0], p[0], 1.0, Mp, pp);
+    ausm_split_fp64(M[1], p[1], -1.0, Mm, pm);
+    const double m = add_(Mp, Mm);
+    const double hm = mul_(0.5, m), ham = mul_(0.5, fabs(m));
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+        F[v] = sub_(mul_(hm, add_(Phi[0][v], Phi[1][v])), mul_(ham, sub_(Phi[1][v], Phi[0][v])));
+    F[1 + D] = add_(F[1 + D], add_(pp, pm));
+}
+
 // The whole face j+1/2 from the six nodes u[0..5] = U_{j-2} .. U_{j+3}.
 template <int ND, int DIR, int FLUX>
 __device__ __forceinline__ void face_fp64(double (&u)[6][ND + 2], const SchemeConst& K, double* F,
@@ -374,6 +422,8 @@ __device__ __forceinline__ void face_fp64(double (&u)[6][ND + 2], const SchemeCo
     }
     if (FLUX == 0) {
         roe_flux_fp64<ND, DIR>(UL, UR, gm1, F);
+    } else if (FLUX == 2) {
+        ausm_flux_fp64<ND, DIR>(UL, UR, K.gamma, gm1, F);
     } else {
         double Fp[NV], Fm[NV];
         vanleer_half_fp64<ND, DIR>(UL, K.gamma, gm1, 1.0, Fp);
@@ -381,6 +431,18 @@ __device__ __forceinline__ void face_fp64(double (&u)[6][ND + 2], const SchemeCo
 #pragma unroll
         for (int v = 0; v < NV; ++v) F[v] = add_(Fp[v], Fm[v]);
     }
+}
+
+// Eq. 4 or 5 for one node and variable from the midpoint fluxes
+// f0..f5 = f_{i-5/2} .. f_{i+5/2} and the node-flux differences
+// d1 = f_{i+1} - f_{i-1}, d2 = f_{i+2} - f_{i-2} (sums left to right);
+// returns the derivative times h.
+__device__ __forceinline__ double diff_alt_fp64(int diff, double f1, double f2, double f3, double f4,
+                                                double d1, double d2)
+{
+    if (diff == DIFF_HWCNS)
+        return add_(add_(mul_(HW_B1, sub_(f3, f2)), mul_(HW_B2, d1)), mul_(HW_B3, d2));
+    return add_(add_(mul_(MND_C1, sub_(f3, f2)), mul_(MND_C2, d1)), mul_(MND_C3, sub_(f4, f1)));
 }
 
 // Eq. 3 for one node and variable: fp = (a1 d1 + a2 d2) + a3 d3; returns fp / h

@@ -7,6 +7,10 @@
 
 namespace wcns {
 
+static_assert((int)DIFF_MD == (int)WCNS_DIFF_MD6 && (int)DIFF_HWCNS == (int)WCNS_DIFF_HWCNS &&
+                  (int)DIFF_MND == (int)WCNS_DIFF_MND && (int)FLUX_AUSM == (int)WCNS_FLUX_AUSM &&
+                  (int)FLUX_ROE == (int)WCNS_FLUX_ROE && (int)FLUX_VANLEER == (int)WCNS_FLUX_VANLEER,
+              "scheme codes");
 static_assert((int)W_TENO == (int)WCNS_W_TENO && (int)W_JS == (int)WCNS_W_JS &&
                   (int)W_LINEAR == (int)WCNS_W_LINEAR && (int)W_Z == (int)WCNS_W_Z,
               "weight codes");
@@ -15,8 +19,10 @@ static_assert((int)W_TENO == (int)WCNS_W_TENO && (int)W_JS == (int)WCNS_W_JS &&
 // otherwise the reason.
 inline const char* scheme_params_error(const wcns_scheme_params* p)
 {
-    if (p->flux != WCNS_FLUX_ROE && p->flux != WCNS_FLUX_VANLEER) return "unsupported flux";
-    if (p->diff != WCNS_DIFF_MD6) return "unsupported difference scheme";
+    if (p->flux != WCNS_FLUX_ROE && p->flux != WCNS_FLUX_VANLEER && p->flux != WCNS_FLUX_AUSM)
+        return "unsupported flux";
+    if (p->diff != WCNS_DIFF_MD6 && p->diff != WCNS_DIFF_HWCNS && p->diff != WCNS_DIFF_MND)
+        return "unsupported difference scheme";
     if (p->weights < WCNS_W_TENO || p->weights > WCNS_W_Z) return "unknown weights";
     if (p->precision != WCNS_FP64 && p->precision != WCNS_FP32)
         return "precision must be WCNS_FP64 or WCNS_FP32";
@@ -44,6 +50,7 @@ inline SchemeConst make_scheme_const(const wcns_scheme_params* p, double gamma)
     K.q = p->q;
     K.weights = p->weights;
     K.eps_js = p->eps_js;
+    K.diff = p->diff;
     // A stencil can only be cut if max g / min g exceeds (3 C_T)^(-1/q); since
     // max g / min g <= 1 + tau / (C (min beta + eps)), tau below
     // 0.98 (ratio - 1) C (min beta + eps) keeps all three.

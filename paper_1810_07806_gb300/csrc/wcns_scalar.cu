@@ -28,7 +28,7 @@ namespace wcns {
 namespace {
 
 constexpr int SC_THREADS = 128;
-constexpr int SC_MAX_SEG = 8192;   // nodes per CTA: (3 seg + 10) doubles of shared memory
+constexpr int SC_MAX_SEG = 6144;   // nodes per CTA: (4 seg + 14) doubles of shared memory
 
 struct ScalarArgs {
     const double* uin;    // input lines (RHS mode)
@@ -87,6 +87,8 @@ __global__ void __launch_bounds__(SC_THREADS) scalar_kernel(const ScalarArgs a)
     double* ue = sm;                    // [seg + 5]: 2 ghost nodes, owned nodes, 3 ghost nodes
     double* Fe = sm + (seg + 5);        // [seg + 5]: 3 ghost faces, owned faces, 2 ghost faces
     double* u0 = sm + 2 * (seg + 5);    // [seg]: state at the start of the RK3 step
+    double* Fn = u0 + seg;              // [seg + 4]: node fluxes f(u), nodes lo-2 .. lo+cnt+1 (Eq. 4-5)
+    const int diff = a.K.diff;
     const int lo = rank * seg;
     const int cnt = max(0, min(seg, n - lo));
     const double* gin = RUN ? a.u + line * a.ld : a.uin + line * a.ld;
@@ -109,6 +111,8 @@ __global__ void __launch_bounds__(SC_THREADS) scalar_kernel(const ScalarArgs a)
         __syncthreads();
         // face lo+l+1/2 reads nodes lo+l-2 .. lo+l+3 = ue[l .. l+5]
         for (int l = tid; l < cnt; l += SC_THREADS) Fe[3 + l] = scalar_face<KIND>(ue + l, a.K);
+        if (diff != DIFF_MD)
+            for (int m = tid; m < cnt + 4; m += SC_THREADS) Fn[m] = flux_of<KIND>(ue[m]);
         cl.sync();   // every CTA's faces are in place
         if (tid < 5 && cnt > 0) {
             const long long g = tid < 3 ? (long long)lo - 3 + tid : (long long)lo + cnt + (tid - 3);
@@ -122,8 +126,12 @@ __global__ void __launch_bounds__(SC_THREADS) scalar_kernel(const ScalarArgs a)
         for (int l = tid; l < cnt; l += SC_THREADS) {
             // node i = lo+l: f[0..5] = faces i-5/2 .. i+5/2 = Fe[l .. l+5]
             const double* f = Fe + l;
-            const double fp = add_(add_(mul_(MD_A1, sub_(f[3], f[2])), mul_(MD_A2, sub_(f[4], f[1]))),
-                                   mul_(MD_A3, sub_(f[5], f[0])));
+            const double* fn = Fn + l;   // f(u) at nodes i-2 .. i+2
+            const double fp =
+                diff == DIFF_MD
+                    ? add_(add_(mul_(MD_A1, sub_(f[3], f[2])), mul_(MD_A2, sub_(f[4], f[1]))),
+                           mul_(MD_A3, sub_(f[5], f[0])))
+                    : diff_alt_fp64(diff, f[1], f[2], f[3], f[4], sub_(fn[3], fn[1]), sub_(fn[4], fn[0]));
             const double Li = div_(-fp, a.h);
             if (!RUN) {
                 a.L[line * a.ld + lo + l] = Li;
@@ -149,7 +157,7 @@ __global__ void __launch_bounds__(SC_THREADS) scalar_kernel(const ScalarArgs a)
 template <int KIND, bool RUN>
 cudaError_t launch_one(const ScalarArgs& a, int count, int csize, cudaStream_t s)
 {
-    const size_t smem = (size_t)(3 * a.seg + 10) * sizeof(double);
+    const size_t smem = (size_t)(4 * a.seg + 14) * sizeof(double);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)((long long)count * csize));
     cfg.blockDim = dim3(SC_THREADS);
@@ -169,7 +177,7 @@ template <int KIND, bool RUN>
 cudaError_t prepare_one(int want_cluster, int* ok_cluster)
 {
     auto k = scalar_kernel<KIND, RUN>;
-    const int smem = (3 * SC_MAX_SEG + 10) * (int)sizeof(double);
+    const int smem = (4 * SC_MAX_SEG + 14) * (int)sizeof(double);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     if (want_cluster > 8) {

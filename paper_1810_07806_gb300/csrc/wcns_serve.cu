@@ -49,7 +49,7 @@ struct Running {
 };
 
 // Requests share a batch when every scheme constant and gamma agree.
-using ClassKey = std::tuple<int, int, int, double, double, double, double, int, double, int, double>;
+using ClassKey = std::tuple<int, int, int, double, double, double, double, int, double, int, double, int>;
 
 struct ClassBatch {
     wcns_batch* b = nullptr;
@@ -61,7 +61,7 @@ ClassKey key_of(const wcns_request& r)
 {
     const wcns_scheme_params& p = r.params;
     return ClassKey(r.grid.ndim, p.precision, p.flux, p.C, p.eps, p.CT, p.cfl, p.q, r.gamma, p.weights,
-                    p.weights == WCNS_W_JS ? p.eps_js : 0.0);
+                    p.weights == WCNS_W_JS ? p.eps_js : 0.0, p.diff);
 }
 
 size_t bytes_per_node(int ndim, int precision)

@@ -7,16 +7,20 @@
 //      boundary rule (transmissive = copy the boundary node, periodic = wrap);
 //  (2) computes the TS + 5 midpoint fluxes of each line, one face per
 //      thread: characteristic projection, TENO selection and Table-1
-//      interpolation of both biased values, back-projection, Roe or van
-//      Leer flux (Sec. 2-3 of arXiv 1810.07806), into shared memory;
-//  (3) forms -f'_i by the sixth-order MD difference (Eq. 3) and writes or
-//      accumulates it into L (Eq. 2: the directions are summed).
+//      interpolation of both biased values (or the JS, Z or linear
+//      weights), back-projection, Roe, van Leer or AUSM flux (Sec. 1-3 of
+//      arXiv 1810.07806), into shared memory;
+//  (3) forms -f'_i by the sixth-order MD difference (Eq. 3), or the HWCNS or
+//      MND difference (Eq. 4, 5) with the physical fluxes of the staged
+//      nodes, and writes or accumulates it into L (Eq. 2: the directions
+//      are summed).
 #pragma once
+#include <type_traits>
 #include "wcns_fp64.cuh"
 
 namespace wcns {
 
-enum { FLUX_ROE = 0, FLUX_VANLEER = 1 };
+enum { FLUX_ROE = 0, FLUX_VANLEER = 1, FLUX_AUSM = 2 };
 
 // Batched sweeps run over many independent grids ("instances") of one
 // dimension at once: each CTA takes one tile from a table and reads its
@@ -238,12 +242,40 @@ __device__ __forceinline__ void face_flux(float (&u)[6][ND + 2], const SweepArgs
     }
     if (FLUX == FLUX_ROE) {
         roe_flux<ND, DIR>(UL, UR, pL, pR, gm1, F);
+    } else if (FLUX == FLUX_AUSM) {
+        ausm_flux<ND, DIR>(UL, UR, pL, pR, a.K.gammaf, F);
     } else {
         float Fp[NV], Fm[NV];
         vanleer_half<ND, DIR>(UL, pL, a.K.gammaf, gm1, 1.f, Fp);
         vanleer_half<ND, DIR>(UR, pR, a.K.gammaf, gm1, -1.f, Fm);
 #pragma unroll
         for (int v = 0; v < NV; ++v) F[v] = Fp[v] + Fm[v];
+    }
+}
+
+// f(U_{s+k}) - f(U_{s-k}) in direction DIR for the staged nodes of line l
+// (physical fluxes; FP64 in the oracle's order).
+template <int ND, int DIR, int TL, int P, typename T>
+__device__ __forceinline__ void node_flux_diff(const T* sS, int l, int s, int k, const SchemeConst& K,
+                                               T* d)
+{
+    constexpr int NV = ND + 2;
+    T Up[NV], Um[NV], Fp[NV], Fm[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        Up[v] = sS[sidx<DIR, TL, P>(v, l, s + k)];
+        Um[v] = sS[sidx<DIR, TL, P>(v, l, s - k)];
+    }
+    if constexpr (sizeof(T) == 8) {
+        phys_flux_fp64<ND, DIR>(Up, K.gm1, Fp);
+        phys_flux_fp64<ND, DIR>(Um, K.gm1, Fm);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) d[v] = sub_(Fp[v], Fm[v]);
+    } else {
+        phys_flux<ND, DIR>(Up, pressure_of<ND>(Up, K.gm1f), Fp);
+        phys_flux<ND, DIR>(Um, pressure_of<ND>(Um, K.gm1f), Fm);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) d[v] = Fp[v] - Fm[v];
     }
 }
 
@@ -435,57 +467,83 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) swee
     if constexpr (kPre) cp_async_wait<0>();    // prefetched L has landed
     __syncthreads();
 
-    // (3) Eq. 3 at nodes pos0 .. pos0 + tcount - 1
+    // (3) Eq. 3 (or Eq. 4, 5) at nodes pos0 .. pos0 + tcount - 1.  The node
+    // loop is instantiated twice so that the Eq. 3 loop carries no trace of
+    // the node fluxes Eq. 4-5 need.
     T* L = Lb;
-    for (int e = threadIdx.x; e < TL * TS; e += blockDim.x) {
-        int l, t;
-        if (DIR == 0) { t = e % TS; l = e / TS; } else { l = e % TL; t = e / TL; }
-        if (l >= lcount || t >= tcount) continue;
-        const long long g = base0 + l * lstride + (long long)(pos0 + t) * sd;
+    const int diff = a.K.diff;
+    auto node_phase = [&](auto alt_tag) {
+        constexpr bool ALT = decltype(alt_tag)::value;
+        for (int e = threadIdx.x; e < TL * TS; e += blockDim.x) {
+            int l, t;
+            if (DIR == 0) { t = e % TS; l = e / TS; } else { l = e % TL; t = e / TL; }
+            if (l >= lcount || t >= tcount) continue;
+            const long long g = base0 + l * lstride + (long long)(pos0 + t) * sd;
+            // Eq. 4-5 also difference the physical fluxes of the nodes i+-1
+            // (and i+-2): d1 = f_{i+1} - f_{i-1}, d2 = f_{i+2} - f_{i-2}
+            T d1[NV], d2[NV];
+            if constexpr (ALT) {
+                node_flux_diff<ND, DIR, TL, P>(sS, l, t + GHOST, 1, a.K, d1);
+                if (diff == DIFF_HWCNS) node_flux_diff<ND, DIR, TL, P>(sS, l, t + GHOST, 2, a.K, d2);
+                else
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            const T f0 = sF[sidx<DIR, TL, NF>(v, l, t + 0)], f1 = sF[sidx<DIR, TL, NF>(v, l, t + 1)];
-            const T f2 = sF[sidx<DIR, TL, NF>(v, l, t + 2)], f3 = sF[sidx<DIR, TL, NF>(v, l, t + 3)];
-            const T f4 = sF[sidx<DIR, TL, NF>(v, l, t + 4)], f5 = sF[sidx<DIR, TL, NF>(v, l, t + 5)];
-            if constexpr (sizeof(T) == 8) {
-                const double q = md_fp64(f0, f1, f2, f3, f4, f5, ih);   // L -= f'
-                L[v * N + g] = a.accumulate ? sub_(L[v * N + g], q) : -q;
-            } else {
-                const T fp = fma(T(MD_A1), f3 - f2, fma(T(MD_A2), f4 - f1, T(MD_A3) * (f5 - f0)));
-                const T val = -fp * ih;
-                T lv = val;
-                if (a.accumulate) {
-                    if constexpr (kPre) lv = sL[sidx<DIR, TL, TS>(v, l, t)] + val;
-                    else lv = L[v * N + g] + val;
-                }
-                if constexpr (G::FUSE) {
-                    if (a.fuse_stage) {
-                        // SSP-RK3 stage on U = U0 + D (FP64 base, FP32 increment):
-                        //   D1 = dt L;  D2 = (D1 + dt L)/4;  U0 += 2/3 (D2 + dt L)
-                        const float dt = (float)*dtp;
-                        const double u0 = sU0[sidx<DIR, TL, TS>(v, l, t)];
-                        const long long gi = v * N + g;
-                        if (a.fuse_stage == 1) {
-                            const float dd = dt * lv;
-                            Db[gi] = dd;
-                            Sob[gi] = __double2float_rn(u0) + dd;
-                        } else if (a.fuse_stage == 2) {
-                            const float dd = 0.25f * fmaf(dt, lv, sD[sidx<DIR, TL, TS>(v, l, t)]);
-                            Db[gi] = dd;
-                            Sob[gi] = __double2float_rn(u0) + dd;
-                        } else {
-                            const float dd = (2.0f / 3.0f) * fmaf(dt, lv, sD[sidx<DIR, TL, TS>(v, l, t)]);
-                            const double un = u0 + (double)dd;
-                            U0b[gi] = un;
-                            Sob[gi] = __double2float_rn(un);
-                        }
-                        continue;
+                    for (int v = 0; v < NV; ++v) d2[v] = T(0);
+            }
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const T f0 = sF[sidx<DIR, TL, NF>(v, l, t + 0)], f1 = sF[sidx<DIR, TL, NF>(v, l, t + 1)];
+                const T f2 = sF[sidx<DIR, TL, NF>(v, l, t + 2)], f3 = sF[sidx<DIR, TL, NF>(v, l, t + 3)];
+                const T f4 = sF[sidx<DIR, TL, NF>(v, l, t + 4)], f5 = sF[sidx<DIR, TL, NF>(v, l, t + 5)];
+                if constexpr (sizeof(T) == 8) {
+                    double q;                                      // L -= f'
+                    if constexpr (ALT) q = mul_(diff_alt_fp64(diff, f1, f2, f3, f4, d1[v], d2[v]), ih);
+                    else q = md_fp64(f0, f1, f2, f3, f4, f5, ih);
+                    L[v * N + g] = a.accumulate ? sub_(L[v * N + g], q) : -q;
+                } else {
+                    T fp;
+                    if constexpr (!ALT)
+                        fp = fma(T(MD_A1), f3 - f2, fma(T(MD_A2), f4 - f1, T(MD_A3) * (f5 - f0)));
+                    else if (diff == DIFF_HWCNS)
+                        fp = fma(T(HW_B1), f3 - f2, fma(T(HW_B2), d1[v], T(HW_B3) * d2[v]));
+                    else
+                        fp = fma(T(MND_C1), f3 - f2, fma(T(MND_C2), d1[v], T(MND_C3) * (f4 - f1)));
+                    const T val = -fp * ih;
+                    T lv = val;
+                    if (a.accumulate) {
+                        if constexpr (kPre) lv = sL[sidx<DIR, TL, TS>(v, l, t)] + val;
+                        else lv = L[v * N + g] + val;
                     }
+                    if constexpr (G::FUSE) {
+                        if (a.fuse_stage) {
+                            // SSP-RK3 stage on U = U0 + D (FP64 base, FP32 increment):
+                            //   D1 = dt L;  D2 = (D1 + dt L)/4;  U0 += 2/3 (D2 + dt L)
+                            const float dt = (float)*dtp;
+                            const double u0 = sU0[sidx<DIR, TL, TS>(v, l, t)];
+                            const long long gi = v * N + g;
+                            if (a.fuse_stage == 1) {
+                                const float dd = dt * lv;
+                                Db[gi] = dd;
+                                Sob[gi] = __double2float_rn(u0) + dd;
+                            } else if (a.fuse_stage == 2) {
+                                const float dd = 0.25f * fmaf(dt, lv, sD[sidx<DIR, TL, TS>(v, l, t)]);
+                                Db[gi] = dd;
+                                Sob[gi] = __double2float_rn(u0) + dd;
+                            } else {
+                                const float dd = (2.0f / 3.0f) * fmaf(dt, lv, sD[sidx<DIR, TL, TS>(v, l, t)]);
+                                const double un = u0 + (double)dd;
+                                U0b[gi] = un;
+                                Sob[gi] = __double2float_rn(un);
+                            }
+                            continue;
+                        }
+                    }
+                    L[v * N + g] = lv;
                 }
-                L[v * N + g] = lv;
             }
         }
-    }
+    };
+    if (diff == DIFF_MD) node_phase(std::false_type{});
+    else node_phase(std::true_type{});
 }
 
 }  // namespace wcns

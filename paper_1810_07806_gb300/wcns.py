@@ -13,7 +13,8 @@ LIB_PATH = os.path.join(HERE, "libwcns.so")
 
 OK, ERR_INVALID, ERR_NOMEM, ERR_NONPHYSICAL, ERR_TIMEOUT, ERR_BUSY, ERR_CUDA = range(7)
 BC_TRANSMISSIVE, BC_PERIODIC = 0, 1
-FLUX_ROE, FLUX_VANLEER = 0, 1
+FLUX_ROE, FLUX_VANLEER, FLUX_AUSM = 0, 1, 2
+DIFF_MD6, DIFF_HWCNS, DIFF_MND = 0, 1, 2
 FP64, FP32 = 0, 1
 W_TENO, W_JS, W_LINEAR, W_Z = 0, 1, 2, 3
 SCALAR_ADVECTION, SCALAR_BURGERS = 0, 1

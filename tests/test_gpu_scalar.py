@@ -129,7 +129,7 @@ def test_scalar_run_of_zero_steps_is_a_no_op():
 
 def test_scalar_max_nodes_is_accepted():
     nmax = wcns.scalar_max_nodes()
-    assert nmax >= 8 * 8192
+    assert nmax >= 8 * 6144
     x = torch.linspace(0, 1, nmax, dtype=torch.float64, device=DEV)
     u = torch.sin(2 * math.pi * x)
     L = wcns.scalar_rhs(wcns.SCALAR_ADVECTION, u, 1.0 / nmax)
