@@ -52,7 +52,8 @@ enum { WCNS_DIFF_MD6 = 0, WCNS_DIFF_HWCNS = 1, WCNS_DIFF_MND = 2 };
  * WCNS-JS (Eq. 14), linear (the optimal weights d_k of Eq. 13, i.e. Eq. 7)
  * and WCNS-Z (the weights of Borges et al. that the paper compares with,
  * alpha_k = d_k (1 + tau_5 / (beta_k + eps)) with the tau_5 of Eq. 16).
- * JS, linear and Z are available in FP64 only. */
+ * All four run in FP64 everywhere and in FP32 single grids (rescaled like
+ * the TENO indicators, tile configuration 0); FP32 batches take TENO only. */
 enum { WCNS_W_TENO = 0, WCNS_W_JS = 1, WCNS_W_LINEAR = 2, WCNS_W_Z = 3 };
 enum { WCNS_FP64 = 0, WCNS_FP32 = 1 };
 
@@ -156,8 +157,9 @@ wcns_status wcns_fallback_count(wcns_handle* h, long long* count, int reset, voi
  * direction's sweep (lines per tile x nodes per line; the halo depth is fixed
  * at 5 by the stencil) on the FP64 device state U, and keeps the fastest for
  * this handle.  chosen (nullable) receives the configuration per direction
- * (0 = default).  FP64 and 1D handles keep configuration 0.  Results do not
- * depend on the configuration.  Synchronises the stream. */
+ * (0 = default).  FP64 and 1D handles, and FP32 handles with the JS, linear
+ * or Z weights (one compiled configuration), keep configuration 0.  Results
+ * do not depend on the configuration.  Synchronises the stream. */
 wcns_status wcns_autotune(wcns_handle* h, const void* U, int* chosen, void* stream);
 
 /* Set (set non-NULL: one configuration 0..2 per direction; ignored by FP64

@@ -20,11 +20,12 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
 # FP64 units keep IEEE division and square root (always the case for double).
 FP32_FLAGS = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
 EXTRA = {"sweep_fp32.cu": FP32_FLAGS, "sweep_fp32_cfg1.cu": FP32_FLAGS, "sweep_fp32_cfg2.cu": FP32_FLAGS,
-         "sweep_batch_fp32.cu": FP32_FLAGS}
+         "sweep_batch_fp32.cu": FP32_FLAGS, "sweep_fp32_weights.cu": FP32_FLAGS,
+         "sweep_fp32_weights_lin.cu": FP32_FLAGS, "sweep_fp32_weights_z.cu": FP32_FLAGS}
 SOURCES = ["wcns_api.cu", "wcns_rk.cu", "sweep_fp64.cu", "sweep_fp32.cu", "sweep_fp32_cfg1.cu",
            "sweep_fp32_cfg2.cu", "wcns_noalloc.cu",
            "wcns_batch.cu", "sweep_batch_fp64.cu", "sweep_batch_fp32.cu", "wcns_serve.cu",
-           "wcns_scalar.cu"]
+           "wcns_scalar.cu", "sweep_fp32_weights.cu", "sweep_fp32_weights_lin.cu", "sweep_fp32_weights_z.cu"]
 
 
 def nvcc():
@@ -45,6 +46,7 @@ def build(force=False, verbose=False, ptxas_info=False):
     os.makedirs(BUILD, exist_ok=True)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     deps.append(os.path.join(CSRC, "sweep_fp32.cu"))   # included by the other configurations
+    deps.append(os.path.join(CSRC, "sweep_fp32_weights.cu"))   # included by the other weights
     deps.append(os.path.join(HERE, "..", "include", "wcns.h"))
     jobs = []
     for s in SOURCES:

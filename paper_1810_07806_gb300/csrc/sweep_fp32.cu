@@ -69,6 +69,7 @@ cudaError_t WCNS_CAT(prepare_sweeps_fp32_cfg, SWEEP_CFG)()
 #if SWEEP_CFG == 0
 cudaError_t launch_sweep_fp32(int nd, int dir, int flux, int cfg, const SweepArgs& a, cudaStream_t s)
 {
+    if (a.K.weights != W_TENO) return launch_sweep_fp32_weights(a.K.weights, nd, dir, flux, a, s);
     if (nd == 1 || cfg == 0) return launch_sweep_fp32_cfg0(nd, dir, flux, a, s);
     if (cfg == 1) return launch_sweep_fp32_cfg1(nd, dir, flux, a, s);
     return launch_sweep_fp32_cfg2(nd, dir, flux, a, s);
@@ -79,6 +80,7 @@ cudaError_t prepare_sweeps_fp32()
     cudaError_t e = prepare_sweeps_fp32_cfg0();
     if (e == cudaSuccess) e = prepare_sweeps_fp32_cfg1();
     if (e == cudaSuccess) e = prepare_sweeps_fp32_cfg2();
+    if (e == cudaSuccess) e = prepare_sweeps_fp32_weights();
     return e;
 }
 #endif

@@ -447,7 +447,8 @@ extern "C" wcns_status wcns_autotune(wcns_handle* h, const void* U, int* chosen,
     set_last_error(nullptr);
     if (!h || !U) return fail(WCNS_ERR_INVALID, "wcns_autotune: null argument");
     cudaStream_t s = (cudaStream_t)stream;
-    if (h->p.precision == WCNS_FP32 && h->ndim >= 2) {
+    // the comparison weights have one tile configuration; TENO has three
+    if (h->p.precision == WCNS_FP32 && h->ndim >= 2 && h->p.weights == WCNS_W_TENO) {
         const long long M = (long long)h->nv * h->N;
         float* A = (float*)h->U1;
         CK(launch_to_fp32((const double*)U, A, M, nullptr, s), "autotune state");

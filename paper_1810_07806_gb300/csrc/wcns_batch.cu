@@ -429,6 +429,8 @@ wcns_status wcns_batch_create(int ndim, double gamma, const wcns_scheme_params* 
     if (ndim < 1 || ndim > 3) return bfail(WCNS_ERR_INVALID, "ndim must be 1, 2 or 3");
     if (!(gamma > 1.0)) return bfail(WCNS_ERR_INVALID, "gamma must exceed 1");
     if (const char* why = scheme_params_error(prm)) return bfail(WCNS_ERR_INVALID, "%s", why);
+    if (prm->precision == WCNS_FP32 && prm->weights != WCNS_W_TENO)
+        return bfail(WCNS_ERR_INVALID, "FP32 batches take TENO weights only (JS, linear, Z: use WCNS_FP64)");
     if (max_nodes < 1 || max_instances < 1) return bfail(WCNS_ERR_INVALID, "capacities must be positive");
 
     wcns_batch* b = new wcns_batch();

@@ -62,6 +62,7 @@ struct SchemeConst {
     int weights;         // W_TENO | W_JS | W_LINEAR | W_Z
     double eps_js;       // epsilon of Eq. 14
     int diff;            // DIFF_MD | DIFF_HWCNS | DIFF_MND
+    float sqrt_eps_jsf;  // sqrt(eps of Eq. 14) in float, for the FP32 rescaled JS eps
     double keep_all_K;   // tau < K * (min beta + eps) guarantees no cut (exact test)
     float Cf, CTf, Kf;
     float gammaf, gm1f;  // gamma, gamma - 1 in float
@@ -141,6 +142,82 @@ __device__ __forceinline__ void select_pair_fp32(const float s[6], float sqrt_ep
     const float r2 = 0.5f * (-3.0f * t[3] + 4.0f * t[2] - t[1]);
     fL = cut_fp32(l0 * l0 + a2 * a2, l1 * l1 + b2 * b2, l2 * l2 + c2 * c2, eps_s, K);
     fR = cut_fp32(r0 * r0 + d2 * d2, r1 * r1 + c2 * c2, r2 * r2 + b2 * b2, eps_s, K);
+}
+
+// Eq. 12 with the comparison weights (FP32), both biased values of one
+// characteristic field from its six values s[0..5] = w_{j-2} .. w_{j+3}.
+// The values are rescaled by sc = max |s| (floored at FLT_MIN) as for the
+// TENO cut, so beta_k and tau are O(1) and eps becomes eps / sc^2.  With
+// b_k = beta_k + eps and b_m = min b:
+//   WCNS-Z  (alpha_k = d_k (1 + tau_5 / b_k)):  omega_k ~ d_k (b_m/b_k)(b_k + tau)/(b_m + tau)
+//   WCNS-JS (Eq. 14, alpha_k = d_k / b_k^2):    omega_k ~ d_k (b_m / b_k)^2
+// (alpha_k divided by its value at b_m: every factor is bounded, nothing
+// overflows); the JS eps is clamped to [FLT_MIN, 1e30], where the weights
+// are already the linear ones.  Linear: omega_k = d_k, i.e. Eq. 7.
+template <int WT>
+__device__ __forceinline__ void weights_pair_fp32(const float s[6], float sqrt_eps, const SchemeConst& K,
+                                                  float& uL, float& uR)
+{
+    float sc = 0.f;
+#pragma unroll
+    for (int m = 0; m < 6; ++m) sc = fmaxf(sc, fabsf(s[m]));
+    sc = fmaxf(sc, 1.17549435e-38f);
+    const float inv = __frcp_rn(sc);
+    float t[6];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) t[m] = s[m] * inv;
+    const float a2 = t[0] - 2.0f * t[1] + t[2];
+    const float b2 = t[1] - 2.0f * t[2] + t[3];
+    const float c2 = t[2] - 2.0f * t[3] + t[4];
+    const float d2 = t[3] - 2.0f * t[4] + t[5];
+    const float D1L[3] = {0.5f * (t[0] - 4.0f * t[1] + 3.0f * t[2]), 0.5f * (t[3] - t[1]),
+                          0.5f * (-3.0f * t[2] + 4.0f * t[3] - t[4])};
+    const float D2L[3] = {a2, b2, c2};
+    const float D1R[3] = {0.5f * (t[5] - 4.0f * t[4] + 3.0f * t[3]), 0.5f * (t[2] - t[4]),
+                          0.5f * (-3.0f * t[3] + 4.0f * t[2] - t[1])};
+    const float D2R[3] = {d2, c2, b2};
+    const float d[3] = {1.0f / 16.0f, 10.0f / 16.0f, 5.0f / 16.0f};
+    float eps_s;
+    if constexpr (WT == W_JS) {
+        const float e = K.sqrt_eps_jsf * inv;
+        eps_s = fminf(fmaxf(e * e, 1.17549435e-38f), 1e30f);
+    } else {
+        const float e = sqrt_eps * inv;
+        eps_s = fmaxf(e * e, 1.17549435e-38f);
+    }
+    auto side = [&](const float* D1, const float* D2, float centre) {
+        float w[3];
+        if constexpr (WT == W_LINEAR) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) w[k] = d[k];
+        } else {
+            float b[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) b[k] = fmaf(D1[k], D1[k], D2[k] * D2[k]) + eps_s;
+            const float bm = fminf(fminf(b[0], b[1]), b[2]);
+            if constexpr (WT == W_Z) {
+                const float tau = fabsf(b[0] - b[2]);
+                const float den = __frcp_rn(bm + tau);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) w[k] = d[k] * (bm * __frcp_rn(b[k])) * ((b[k] + tau) * den);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float r = bm * __frcp_rn(b[k]);
+                    w[k] = d[k] * r * r;
+                }
+            }
+            const float iw = __frcp_rn(w[0] + w[1] + w[2]);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) w[k] *= iw;
+        }
+        float u = 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) u = fmaf(w[k], fmaf(0.125f, D2[k], fmaf(0.5f, D1[k], centre)), u);
+        return u * sc;
+    };
+    uL = side(D1L, D2L, t[2]);
+    uR = side(D1R, D2R, t[3]);
 }
 
 // Eq. 12 with the weights of Eq. 19, as the equivalent Table-1 stencil.

@@ -26,8 +26,6 @@ inline const char* scheme_params_error(const wcns_scheme_params* p)
     if (p->weights < WCNS_W_TENO || p->weights > WCNS_W_Z) return "unknown weights";
     if (p->precision != WCNS_FP64 && p->precision != WCNS_FP32)
         return "precision must be WCNS_FP64 or WCNS_FP32";
-    if (p->weights != WCNS_W_TENO && p->precision != WCNS_FP64)
-        return "JS, linear and Z weights need precision WCNS_FP64";
     if (p->characteristic != 1) return "characteristic must be 1";
     if (p->entropy_fix != 0) return "entropy_fix must be 0";
     if (!(p->C > 0.0) || !(p->eps > 0.0) || !(p->CT > 0.0) || !(p->CT < 1.0 / 3.0))
@@ -51,6 +49,7 @@ inline SchemeConst make_scheme_const(const wcns_scheme_params* p, double gamma)
     K.weights = p->weights;
     K.eps_js = p->eps_js;
     K.diff = p->diff;
+    K.sqrt_eps_jsf = (float)sqrt(p->eps_js > 0.0 ? p->eps_js : 0.0);
     // A stencil can only be cut if max g / min g exceeds (3 C_T)^(-1/q); since
     // max g / min g <= 1 + tau / (C (min beta + eps)), tau below
     // 0.98 (ratio - 1) C (min beta + eps) keeps all three.
@@ -73,6 +72,15 @@ cudaError_t launch_sweep_fp32_cfg2(int nd, int dir, int flux, const SweepArgs& a
 cudaError_t prepare_sweeps_fp32_cfg0();
 cudaError_t prepare_sweeps_fp32_cfg1();
 cudaError_t prepare_sweeps_fp32_cfg2();
+// FP32 sweeps with the comparison weights (tile configuration 0).
+cudaError_t launch_sweep_fp32_weights(int wt, int nd, int dir, int flux, const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_sweep_fp32_w1(int nd, int dir, int flux, const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_sweep_fp32_w2(int nd, int dir, int flux, const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_sweep_fp32_w3(int nd, int dir, int flux, const SweepArgs& a, cudaStream_t s);
+cudaError_t prepare_sweeps_fp32_weights();
+cudaError_t prepare_sweeps_fp32_w1();
+cudaError_t prepare_sweeps_fp32_w2();
+cudaError_t prepare_sweeps_fp32_w3();
 // Batched sweeps over a tile table (wcns_batch.cu); ntiles CTAs.
 cudaError_t launch_sweep_batch_fp64(int nd, int dir, int flux, const SweepArgs& a, long long ntiles,
                                     cudaStream_t s);

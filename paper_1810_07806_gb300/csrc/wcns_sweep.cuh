@@ -134,7 +134,8 @@ __device__ __forceinline__ int sidx(int v, int l, int s)
 }
 
 // ---------------------------------------------------------------- FP64 face
-template <int ND, int DIR, int FLUX>
+// (the FP64 face selects the weights at run time: WT is not used)
+template <int ND, int DIR, int FLUX, int WT>
 __device__ __forceinline__ void face_flux(double (&u)[6][ND + 2], const SweepArgs& a, double* F,
                                           uint8_t* fl, bool& fell_back)
 {
@@ -142,7 +143,9 @@ __device__ __forceinline__ void face_flux(double (&u)[6][ND + 2], const SweepArg
 }
 
 // ---------------------------------------------------------------- FP32 face
-template <int ND, int DIR, int FLUX>
+// WT: the weights, fixed at compile time (W_TENO, or the comparison weights
+// W_JS, W_LINEAR, W_Z in their own instances).
+template <int ND, int DIR, int FLUX, int WT>
 __device__ __forceinline__ void face_flux(float (&u)[6][ND + 2], const SweepArgs& a, float* F,
                                           uint8_t* fl, bool& fell_back)
 {
@@ -201,11 +204,16 @@ __device__ __forceinline__ void face_flux(float (&u)[6][ND + 2], const SweepArgs
         for (int m = 0; m < 6; ++m) s6[m] = u[m][k];
 #pragma unroll
         for (int m = 0; m < 5; ++m) { sl[m] = u[m][k]; sr[m] = u[5 - m][k]; }
-        int fL, fR;
-        select_pair_fp32(s6, a.sqrt_eps_f, a.K, fL, fR);
-        wL[k] = interp_row<float>(fL, sl);
-        wR[k] = interp_row<float>(fR, sr);
-        fl[k] = (uint8_t)(fL | (fR << 3));
+        if constexpr (WT == W_TENO) {
+            int fL, fR;
+            select_pair_fp32(s6, a.sqrt_eps_f, a.K, fL, fR);
+            wL[k] = interp_row<float>(fL, sl);
+            wR[k] = interp_row<float>(fR, sr);
+            fl[k] = (uint8_t)(fL | (fR << 3));
+        } else {
+            weights_pair_fp32<WT>(s6, a.sqrt_eps_f, a.K, wL[k], wR[k]);
+            fl[k] = 0x3F;
+        }
     }
     float UL[NV], UR[NV];
     {
@@ -280,7 +288,7 @@ __device__ __forceinline__ void node_flux_diff(const T* sS, int l, int s, int k,
 }
 
 // ---------------------------------------------------------------- kernel
-template <typename T, typename LT, int ND, int DIR, int FLUX, bool BATCH = false, int CFG = 0>
+template <typename T, typename LT, int ND, int DIR, int FLUX, bool BATCH = false, int CFG = 0, int WT = 0>
 __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) sweep_kernel(const SweepArgs a)
 {
     constexpr int NV = ND + 2;
@@ -449,7 +457,7 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) swee
         T F[NV];
         uint8_t fl[NV];
         bool fell = false;
-        face_flux<ND, DIR, FLUX>(u, a, F, fl, fell);
+        face_flux<ND, DIR, FLUX, WT>(u, a, F, fl, fell);
         // faces shared with the next tile are owned (counted, flagged) by it
         const bool owned = f < TS || pos0 + TS >= nd;
         fb += (fell && owned) ? 1 : 0;

@@ -48,8 +48,7 @@ def _create(grid, gamma=1.4, **kw):
     dict(ndim=0), dict(ndim=4), dict(gamma=1.0), dict(q=0), dict(CT=0.5), dict(C=0.0),
     dict(flux=7), dict(characteristic=0), dict(entropy_fix=1), dict(precision=3), dict(cfl=0.0),
     dict(n=(1,)), dict(half_periodic=True), dict(weights=4), dict(weights=-1),
-    dict(weights=wcns.W_JS, precision=wcns.FP32), dict(weights=wcns.W_Z, precision=wcns.FP32),
-    dict(weights=wcns.W_JS, eps_js=0.0)])
+    dict(weights=wcns.W_JS, eps_js=0.0), dict(flux=3), dict(diff=3), dict(diff=-1)])
 def test_create_rejects_bad_arguments_without_a_gpu(bad):
     ndim = bad.get("ndim", 1)
     n = bad.get("n", (16,))
@@ -94,3 +93,14 @@ def test_scalar_run_rejects_bad_time_arguments():
     assert L.wcns_scalar_run(0, C.byref(p), 16, 0.1, float("inf"), 4, 1, ptr, 16, None) == wcns.ERR_INVALID
     # zero steps is a no-op that touches nothing
     assert L.wcns_scalar_run(0, C.byref(p), 16, 0.1, 1.0, 0, 1, ptr, 16, None) == wcns.OK
+
+
+def test_fp32_batch_rejects_comparison_weights_without_a_gpu():
+    L = wcns.lib()
+    L.wcns_batch_create.argtypes = [C.c_int, C.c_double, C.POINTER(wcns.SchemeParams), C.c_longlong, C.c_int,
+                                    C.POINTER(C.c_void_p)]
+    for w in (wcns.W_JS, wcns.W_LINEAR, wcns.W_Z):
+        p = wcns.default_params(weights=w, precision=wcns.FP32)
+        h = C.c_void_p()
+        assert L.wcns_batch_create(1, 1.4, C.byref(p), 1000, 4, C.byref(h)) == wcns.ERR_INVALID
+        assert h.value is None

@@ -171,3 +171,47 @@ def test_scalar_path_with_eq4_eq5_bit_identical(kind, diff):
         t_end = steps * 0.2 * h / np.max(np.abs(u))
         wcns.scalar_run(kind, Ud, h, t_end, steps, diff=DIFF[diff][0])
         assert np.array_equal(Ud.cpu().numpy(), O.scalar_run(cfg, kind, u, h, t_end, steps))
+
+
+@pytest.mark.parametrize("weights", ["js", "linear", "z"])
+def test_fp32_comparison_weights_close_to_fp64(weights):
+    """FP32 single grids with the comparison weights (rescaled indicators):
+    smooth flow within the same flux-scale bound as TENO; flags report
+    all stencils kept."""
+    wg = {"z": wcns.W_Z, "js": wcns.W_JS, "linear": wcns.W_LINEAR}[weights]
+    for pb in (inputs.taylor_green(24), inputs.density_wave_1d(64), inputs.four_quadrant(40, ny=33)):
+        for flux in ("roe", "ausm"):
+            L64 = _gpu_rhs(pb, pb.U0, flux, "md", weights=wg)[0]
+            L32, fl32, _ = _gpu_rhs(pb, pb.U0, flux, "md", precision=wcns.FP32, weights=wg)
+            assert np.all(fl32 == 0x3F)
+            S = _flux_scale(pb.U0, pb).reshape((-1,) + (1,) * pb.ndim)
+            rel = np.max(np.abs(L32 - L64) / (np.abs(L64) + S))
+            bound = 2e-6 if pb.name != "four_quadrant" else 2e-5
+            assert rel < bound, (pb.name, flux, rel)
+
+
+@pytest.mark.parametrize("weights", ["js", "z"])
+def test_fp32_comparison_weights_sod_end_state(weights):
+    wg = {"z": wcns.W_Z, "js": wcns.W_JS}[weights]
+    pb = inputs.shock_tube(400)
+    out = {}
+    for prec in (wcns.FP64, wcns.FP32):
+        s = wcns.Solver.for_problem(pb, weights=wg, precision=prec, cfl=0.5)
+        Ud = torch.from_numpy(pb.U0.copy()).to(DEV)
+        s.advance(Ud, 0.2, check_every=16)
+        out[prec] = Ud.cpu().numpy()
+        s.close()
+    rel = np.sum(np.abs(out[wcns.FP32] - out[wcns.FP64]), axis=1) / np.sum(np.abs(out[wcns.FP64]), axis=1)
+    assert np.all(rel <= 1e-4), rel
+
+
+def test_fp32_weights_of_an_all_zero_or_tiny_field_are_finite():
+    """A field that is zero (or at the eps floor) everywhere keeps finite
+    weights: the rescaled JS eps is clamped and the Z ratios are bounded."""
+    pb = inputs.taylor_green(16)
+    U = pb.U0.copy()
+    U[3] = 0.0          # w-momentum exactly zero
+    U[1] *= 1e-30       # u-momentum tiny
+    for wg in (wcns.W_JS, wcns.W_Z, wcns.W_LINEAR):
+        L32 = _gpu_rhs(pb, U, "roe", "md", precision=wcns.FP32, weights=wg)[0]
+        assert np.all(np.isfinite(L32))
