@@ -11,6 +11,7 @@ from . import build as _build
 
 FLUX_ROE, FLUX_VANLEER, FLUX_AUSM = 0, 1, 2
 DIFF_MD, DIFF_HWCNS, DIFF_MND = 0, 1, 2
+BC_AUTO, BC_REFLECT, BC_FIXED = 0, 2, 3
 W_TENO, W_JS, W_LINEAR, W_Z = 0, 1, 2, 3
 
 _dp = C.POINTER(C.c_double)
@@ -23,6 +24,8 @@ class OraCfg(C.Structure):
         ("gamma", C.c_double), ("flux", C.c_int), ("weights", C.c_int),
         ("C", C.c_double), ("eps", C.c_double), ("CT", C.c_double), ("q", C.c_int),
         ("eps_js", C.c_double), ("characteristic", C.c_int), ("diff", C.c_int),
+        ("bc_lo", C.c_int * 3), ("bc_hi", C.c_int * 3), ("bc_state", ((C.c_double * 5) * 2) * 3),
+        ("gravity", C.c_double * 3),
     ]
 
 
@@ -77,9 +80,13 @@ def _p(a):
 
 def make_cfg(ndim=1, n=(1, 1, 1), h=(1.0, 1.0, 1.0), periodic=(0, 0, 0), gamma=1.4,
              flux=FLUX_ROE, weights=W_TENO, C_=1.0, eps=1e-40, CT=1e-5, q=6, eps_js=1e-6,
-             characteristic=1, diff=DIFF_MD):
+             characteristic=1, diff=DIFF_MD, bc_lo=(0, 0, 0), bc_hi=(0, 0, 0), bc_state=None,
+             gravity=(0.0, 0.0, 0.0)):
     """Scheme constants default to the paper's: C = 1, eps = 1e-40, q = 6 (Eq. 16),
-    C_T = 1e-5 (Sec. 2.3), JS eps = 1e-6 (Eq. 14), MD differencing (Eq. 3)."""
+    C_T = 1e-5 (Sec. 2.3), JS eps = 1e-6 (Eq. 14), MD differencing (Eq. 3).
+    bc_lo / bc_hi: BC_AUTO (periodic flag), BC_REFLECT or BC_FIXED per axis;
+    bc_state[axis][side] = conserved state of a FIXED side; gravity = body
+    force per unit mass."""
     c = OraCfg()
     c.ndim = ndim
     for a in range(3):
@@ -89,6 +96,16 @@ def make_cfg(ndim=1, n=(1, 1, 1), h=(1.0, 1.0, 1.0), periodic=(0, 0, 0), gamma=1
     c.gamma, c.flux, c.weights = gamma, flux, weights
     c.C, c.eps, c.CT, c.q, c.eps_js, c.characteristic = C_, eps, CT, q, eps_js, characteristic
     c.diff = diff
+    for a in range(3):
+        c.bc_lo[a] = int(bc_lo[a]) if a < len(bc_lo) else 0
+        c.bc_hi[a] = int(bc_hi[a]) if a < len(bc_hi) else 0
+        c.gravity[a] = float(gravity[a]) if a < len(gravity) else 0.0
+        if bc_state is not None and a < len(bc_state):
+            for side in range(2):
+                st = bc_state[a][side]
+                if st is not None:
+                    for v in range(len(st)):
+                        c.bc_state[a][side][v] = float(st[v])
     return c
 
 

@@ -51,7 +51,12 @@
  *     where the literal form is finite.  delta_k = 0 iff chi_k < C_T.
  *   - SSP-RK3 in Shu-Osher form; dt = CFL / max_i sum_d (|u_d| + c)/h_d.
  *   - Transmissive boundaries copy the boundary node into 5 ghost nodes;
- *     periodic boundaries wrap.
+ *     periodic boundaries wrap.  Reflecting walls (Sec. 3.9, Rayleigh-Taylor)
+ *     sit on the face outside the boundary node: ghost -1-k mirrors node k
+ *     with the normal momentum negated.  Fixed-state boundaries fill every
+ *     ghost node with the given state.
+ *   - A body force g per unit mass adds (0, rho g, rho u.g) to the RHS
+ *     (Sec. 3.9: g = (0, 1)), after the directions are summed.
  *   - If an interpolated midpoint state has rho <= 0 or p <= 0 the face
  *     falls back to first order (U_L = U_j, U_R = U_{j+1}) and is counted.
  */
@@ -66,6 +71,8 @@
 /* Scheme switches (the oracle's own numbering). */
 enum { ORA_FLUX_ROE = 0, ORA_FLUX_VANLEER = 1, ORA_FLUX_AUSM = 2 };
 enum { ORA_DIFF_MD = 0, ORA_DIFF_HWCNS = 1, ORA_DIFF_MND = 2 };
+/* Boundary kinds per side; AUTO follows periodic[] (periodic or transmissive). */
+enum { ORA_BC_AUTO = 0, ORA_BC_REFLECT = 2, ORA_BC_FIXED = 3 };
 enum { ORA_W_TENO = 0, ORA_W_JS = 1, ORA_W_LINEAR = 2, ORA_W_Z = 3 };
 
 typedef struct {
@@ -81,6 +88,9 @@ typedef struct {
     double eps_js;        /* Eq. 14: 1e-6                                */
     int characteristic;   /* 1 = interpolate characteristic variables    */
     int diff;             /* ORA_DIFF_*: Eq. 3, 4 or 5                   */
+    int bc_lo[3], bc_hi[3];               /* ORA_BC_* per axis side      */
+    double bc_state[3][2][ORA_MAXV];      /* conserved state, FIXED sides */
+    double gravity[3];                    /* body force per unit mass    */
 } ora_cfg;
 
 /* ------------------------------------------------------------------ */
@@ -528,14 +538,52 @@ static void face_flux(const ora_cfg* cfg, int d, const double* P, int j, double*
     }
 }
 
-/* A1: node m of a line (any integer m) under the boundary rule of d. */
-static int ghost_source(const ora_cfg* cfg, int d, int m)
+/* A1: node m of a line (any integer m) under the boundary rule of d: writes
+ * the node's conserved variables into out[] from the line accessor
+ * (line[node * node_stride + v * var_stride]). */
+static void ghost_node(const ora_cfg* cfg, int d, const double* line, long node_stride,
+                       long var_stride, int m, double* out)
 {
-    const int n = cfg->n[d];
-    if (cfg->periodic[d]) return ((m % n) + n) % n;
-    if (m < 0) return 0;
-    if (m >= n) return n - 1;
-    return m;
+    const int n = cfg->n[d], nv = cfg->ndim + 2;
+    int src = m, sign = 1;
+    if (cfg->periodic[d]) {
+        src = ((m % n) + n) % n;
+    } else if (m < 0 || m >= n) {
+        const int kind = m < 0 ? cfg->bc_lo[d] : cfg->bc_hi[d];
+        if (kind == ORA_BC_FIXED) {
+            for (int v = 0; v < nv; ++v) out[v] = cfg->bc_state[d][m < 0 ? 0 : 1][v];
+            return;
+        }
+        if (kind == ORA_BC_REFLECT) {
+            while (src < 0 || src >= n) {       /* mirror about the wall faces */
+                src = src < 0 ? -1 - src : 2 * n - 1 - src;
+                sign = -sign;
+            }
+        } else {
+            src = m < 0 ? 0 : n - 1;            /* transmissive: zero gradient */
+        }
+    }
+    for (int v = 0; v < nv; ++v) out[v] = line[src * node_stride + v * var_stride];
+    if (sign < 0) out[1 + d] = -out[1 + d];
+}
+
+/* Body force: L += (0, rho g, rho u.g) at every node, sums in axis order. */
+static int has_gravity(const ora_cfg* cfg)
+{
+    return cfg->gravity[0] != 0.0 || cfg->gravity[1] != 0.0 || cfg->gravity[2] != 0.0;
+}
+
+static void add_source(const ora_cfg* cfg, const double* U, double* L, long N)
+{
+    const int nd = cfg->ndim, nv = nd + 2;
+    for (long i = 0; i < N; ++i) {
+        double se = 0.0;
+        for (int a = 0; a < nd; ++a) {
+            L[(1 + a) * N + i] += cfg->gravity[a] * U[i];
+            se += cfg->gravity[a] * U[(1 + a) * N + i];
+        }
+        L[(nv - 1) * N + i] += se;
+    }
 }
 
 /* One direction of the semi-discrete operator on one grid line.
@@ -551,11 +599,8 @@ static void euler_line(const ora_cfg* cfg, int d, const double* line, long node_
     const int np = n + 2 * ORA_GHOST, nf = n + 5;
     double* P = (double*)malloc(sizeof(double) * np * nv);   /* padded nodes */
     double* Fc = (double*)malloc(sizeof(double) * nf * nv);  /* face fluxes  */
-    for (int m = -ORA_GHOST; m < n + ORA_GHOST; ++m) {       /* A1 */
-        int src = ghost_source(cfg, d, m);
-        for (int v = 0; v < nv; ++v)
-            P[(m + ORA_GHOST) * nv + v] = line[src * node_stride + v * var_stride];
-    }
+    for (int m = -ORA_GHOST; m < n + ORA_GHOST; ++m)         /* A1 */
+        ghost_node(cfg, d, line, node_stride, var_stride, m, &P[(m + ORA_GHOST) * nv]);
     for (int f = 0; f < nf; ++f) {
         uint8_t fl[ORA_MAXV];
         double mg[ORA_MAXV];
@@ -657,6 +702,7 @@ long ora_euler_rhs(const ora_cfg* cfg, const double* U, double* L, uint8_t* flag
             if (st.litdev > ld) ld = st.litdev;
         }
     }
+    if (has_gravity(cfg)) add_source(cfg, U, L, N);
     if (litdev) *litdev = ld;
     return nonphys;
 }
@@ -697,23 +743,33 @@ long ora_euler_rhs_at(const ora_cfg* cfg, const double* U, long npts, const long
         for (int v = 0; v < nv; ++v) acc[v] = 0.0;
         for (int d = 0; d < nd; ++d) {
             double P[(2 * ORA_GHOST + 1) * ORA_MAXV];   /* nodes i-5 .. i+5 */
-            for (int m = -ORA_GHOST; m <= ORA_GHOST; ++m) {
-                long c[3] = {coord[0], coord[1], coord[2]};
-                c[d] = ghost_source(cfg, d, (int)coord[d] + m);
-                long off = 0;
-                for (int a = nd - 1; a >= 0; --a) off = off * cfg->n[a] + c[a];
-                for (int v = 0; v < nv; ++v) P[(m + ORA_GHOST) * nv + v] = U[v * N + off];
-            }
+            long c0[3] = {coord[0], coord[1], coord[2]};
+            c0[d] = 0;
+            long base = 0;
+            for (int a = nd - 1; a >= 0; --a) base = base * cfg->n[a] + c0[a];
+            for (int m = -ORA_GHOST; m <= ORA_GHOST; ++m)
+                ghost_node(cfg, d, U + base, axis_stride(cfg, d), N, (int)coord[d] + m,
+                           &P[(m + ORA_GHOST) * nv]);
             /* faces i-5/2 .. i+5/2 are j = i-3 .. i+2; with the padded origin at
              * node i, j runs -3 .. 2 and the face array index is j + 3 */
-            double Fc[6][ORA_MAXV];
+            double Fc[6][ORA_MAXV], Fn[5][ORA_MAXV];
             for (int f = 0; f < 6; ++f) face_flux(cfg, d, P, f - 3, Fc[f], NULL, NULL, &st);
+            for (int k = 0; k < 5; ++k) phys_flux(nd, d, cfg->gamma, &P[(k - 2 + ORA_GHOST) * nv], Fn[k]);
             const double ih = 1.0 / cfg->h[d];
             for (int v = 0; v < nv; ++v) {
-                double fp = MD_A1 * (Fc[3][v] - Fc[2][v]) + MD_A2 * (Fc[4][v] - Fc[1][v])
-                          + MD_A3 * (Fc[5][v] - Fc[0][v]);
-                acc[v] -= fp * ih;
+                double fm[6], fn[5];
+                for (int k = 0; k < 6; ++k) fm[k] = Fc[k][v];
+                for (int k = 0; k < 5; ++k) fn[k] = Fn[k][v];
+                acc[v] -= diff_node(cfg->diff, fm, fn) * ih;
             }
+        }
+        if (has_gravity(cfg)) {
+            double se = 0.0;
+            for (int a = 0; a < nd; ++a) {
+                acc[1 + a] += cfg->gravity[a] * U[idx[p]];
+                se += cfg->gravity[a] * U[(1 + a) * N + idx[p]];
+            }
+            acc[nv - 1] += se;
         }
         for (int v = 0; v < nv; ++v) Lout[v * npts + p] = acc[v];
         nonphys += st.nonphys;

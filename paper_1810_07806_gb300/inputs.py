@@ -8,9 +8,14 @@ All states are returned as float64 numpy arrays in SoA layout
 U[var][z][y][x] (x fastest) with conserved variables
 (rho, rho*u_1, ..., rho*u_nd, E), E = p/(gamma-1) + rho |u|^2 / 2.
 
-Grid convention: non-periodic axes place node i at lo + i*h with
+Grid convention: transmissive axes place node i at lo + i*h with
 h = (hi - lo)/(n - 1) (both end points are nodes); periodic axes place node i
-at lo + i*h with h = (hi - lo)/n (the end point is the image of node 0).
+at lo + i*h with h = (hi - lo)/n (the end point is the image of node 0); axes
+with a reflecting wall or a fixed-state side place node i at the cell centre
+lo + (i + 1/2) h with h = (hi - lo)/n (walls sit on the outer faces).
+
+Boundary kinds (the library's codes): 0 transmissive, 1 periodic,
+2 reflecting wall, 3 fixed state.
 """
 import math
 from dataclasses import dataclass, field
@@ -58,6 +63,10 @@ class Problem:
     U0: np.ndarray
     t_end: float = 0.0
     h: tuple = field(default=())
+    bc_lo: tuple = (0, 0, 0)          # boundary kind of the low side of each axis
+    bc_hi: tuple = (0, 0, 0)
+    bc_state: tuple = None            # [axis][side] conserved state of fixed sides
+    gravity: tuple = (0.0, 0.0, 0.0)  # body force per unit mass
 
     @property
     def nv(self):
@@ -245,3 +254,35 @@ def random_rough_state(ndim, n, seed, gamma=1.4):
     vel = [field_(-1.0, 1.0) for _ in range(ndim)]
     p = field_(0.1, 2.0)
     return prim_to_cons(rho, vel, p, gamma)
+
+
+# ---------------------------------------------------------------- Rayleigh-Taylor
+BC_TRANSMISSIVE, BC_PERIODIC, BC_REFLECTING, BC_FIXED = 0, 1, 2, 3
+
+
+def rayleigh_taylor(nx=128, ny=None, amp=0.025, gamma=5.0 / 3.0, t_end=1.95):
+    """Sec. 3.9: [0, 0.25] x [0, 1], heavy fluid (rho = 2, p = 1 + 2y) below
+    y = 1/2, light fluid (rho = 1, p = y + 3/2, the reading of the garbled
+    upper pressure that keeps p continuous and hydrostatic) above, v =
+    -amp a cos(8 pi x) with a the local sound speed, u = 0, gamma = 5/3.
+    Reflecting walls at x = 0, 0.25; fixed states (2, 0, 0, 1) below y = 0 and
+    (1, 0, 0, 2.5) above y = 1; body force g = (0, 1), i.e. the source
+    (0, 0, rho, rho v).  Cell-centred nodes, ny = 4 nx (square cells)."""
+    ny = 4 * nx if ny is None else ny
+    hx, hy = 0.25 / nx, 1.0 / ny
+    x = (np.arange(nx) + 0.5) * hx
+    y = (np.arange(ny) + 0.5) * hy
+    Y, X = np.meshgrid(y, x, indexing="ij")
+    lower = Y < 0.5
+    rho = np.where(lower, 2.0, 1.0)
+    p = np.where(lower, 1.0 + 2.0 * Y, Y + 1.5)
+    a = np.sqrt(gamma * p / rho)
+    v = -amp * a * np.cos(8.0 * np.pi * X)
+    U = prim_to_cons(rho, [np.zeros_like(rho), v], p, gamma)
+    bottom = prim_to_cons(np.array(2.0), [np.array(0.0), np.array(0.0)], np.array(1.0), gamma)
+    top = prim_to_cons(np.array(1.0), [np.array(0.0), np.array(0.0)], np.array(2.5), gamma)
+    return Problem("rayleigh_taylor", 2, (nx, ny), (0.0, 0.0), (0.25, 1.0), (0, 0), gamma,
+                   np.ascontiguousarray(U), t_end, (hx, hy),
+                   bc_lo=(BC_REFLECTING, BC_FIXED, 0), bc_hi=(BC_REFLECTING, BC_FIXED, 0),
+                   bc_state=((None, None), (tuple(bottom), tuple(top)), (None, None)),
+                   gravity=(0.0, 1.0, 0.0))
