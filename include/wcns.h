@@ -39,7 +39,10 @@ typedef enum {
     WCNS_ERR_CUDA = 6         /* a CUDA runtime call failed                      */
 } wcns_status;
 
-enum { WCNS_BC_TRANSMISSIVE = 0, WCNS_BC_PERIODIC = 1 };
+/* Boundary kinds: zero-gradient copy of the boundary node (Sec. 3.4),
+ * periodic wrap, reflecting wall, fixed (Dirichlet) state; the last two are
+ * the Rayleigh-Taylor boundaries of Sec. 3.9. */
+enum { WCNS_BC_TRANSMISSIVE = 0, WCNS_BC_PERIODIC = 1, WCNS_BC_REFLECTING = 2, WCNS_BC_FIXED = 3 };
 /* Midpoint flux (Sec. 1 names all three): Roe flux-difference splitting,
  * van Leer flux-vector splitting, Liou-Steffen AUSM. */
 enum { WCNS_FLUX_ROE = 0, WCNS_FLUX_VANLEER = 1, WCNS_FLUX_AUSM = 2 };
@@ -57,16 +60,27 @@ enum { WCNS_DIFF_MD6 = 0, WCNS_DIFF_HWCNS = 1, WCNS_DIFF_MND = 2 };
 enum { WCNS_W_TENO = 0, WCNS_W_JS = 1, WCNS_W_LINEAR = 2, WCNS_W_Z = 3 };
 enum { WCNS_FP64 = 0, WCNS_FP32 = 1 };
 
-/* Uniform grid.  Axis a has n[a] nodes on [lo[a], hi[a]].  A transmissive
- * axis places nodes on both end points, h = (hi - lo)/(n - 1); a periodic
- * axis has n unique nodes, h = (hi - lo)/n.  bc[a][0] / bc[a][1] are the
- * low / high side; periodic must be set on both sides.  Axes >= ndim are
- * ignored.  n[a] >= 2 (transmissive) or >= 1 (periodic). */
+/* Uniform grid.  Axis a has n[a] nodes on [lo[a], hi[a]].  An axis whose
+ * two sides are transmissive places nodes on both end points,
+ * h = (hi - lo)/(n - 1); any other axis has h = (hi - lo)/n: a periodic axis
+ * has n unique nodes, and an axis with a reflecting wall or a fixed state
+ * places its nodes at cell centres lo + (i + 1/2) h, the walls on the outer
+ * faces.  bc[a][0] / bc[a][1] are the low / high side; periodic must be set
+ * on both sides.  A reflecting side mirrors the nodes about the wall face
+ * with the normal momentum negated (needs n[a] >= 5); a fixed side fills
+ * its 5 ghost nodes with bc_state[a][side] (conserved variables rho,
+ * rho u_1 .. rho u_ndim, E; rho > 0, p > 0).  gravity is a body force per
+ * unit mass: the RHS gains (0, rho g, rho u.g) (Sec. 3.9: g = (0, 1)).
+ * Axes >= ndim are ignored.  n[a] >= 2 (transmissive) or >= 1 (periodic).
+ * Reflecting and fixed sides and gravity are single-grid features (batches
+ * and the server reject them). */
 typedef struct {
     int ndim;
     int n[3];
     double lo[3], hi[3];
     int bc[3][2];
+    double bc_state[3][2][5];
+    double gravity[3];
 } wcns_grid;
 
 /* Scheme parameters (Sec. 2 of the paper).  wcns_default_params() fills the

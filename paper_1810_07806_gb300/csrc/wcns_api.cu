@@ -18,6 +18,7 @@ struct wcns_handle {
     long long N = 0;
     double h[3] = {1, 1, 1}, inv_h[3] = {0, 0, 0};
     int periodic[3] = {0, 0, 0};
+    GridInfo G;                 // boundary kinds, fixed states, gravity
     double gamma = 1.4;
     wcns_scheme_params p{};
     SchemeConst K{};
@@ -100,31 +101,20 @@ wcns_status wcns_create(const wcns_grid* g, double gamma, const wcns_scheme_para
     if (!(gamma > 1.0)) return fail(WCNS_ERR_INVALID, "gamma must exceed 1");
     if (const char* why = scheme_params_error(prm)) return fail(WCNS_ERR_INVALID, "%s", why);
 
+    GridInfo G;
+    char why[256];
+    if (const char* msg = grid_error(g, gamma, G, why, sizeof why)) return fail(WCNS_ERR_INVALID, "%s", msg);
     wcns_handle* h = new wcns_handle();
-    h->ndim = g->ndim;
-    h->nv = g->ndim + 2;
-    h->N = 1;
-    for (int a = 0; a < g->ndim; ++a) {
-        const int per = g->bc[a][0] == WCNS_BC_PERIODIC;
-        if ((g->bc[a][1] == WCNS_BC_PERIODIC) != per) {
-            delete h;
-            return fail(WCNS_ERR_INVALID, "axis %d: periodic must be set on both sides", a);
-        }
-        for (int sd = 0; sd < 2; ++sd)
-            if (g->bc[a][sd] != WCNS_BC_PERIODIC && g->bc[a][sd] != WCNS_BC_TRANSMISSIVE) {
-                delete h;
-                return fail(WCNS_ERR_INVALID, "axis %d: unknown boundary kind", a);
-            }
-        if (g->n[a] < (per ? 1 : 2) || !(g->hi[a] > g->lo[a])) {
-            delete h;
-            return fail(WCNS_ERR_INVALID, "axis %d: bad node count or extent", a);
-        }
-        h->n[a] = g->n[a];
-        h->periodic[a] = per;
-        h->h[a] = (g->hi[a] - g->lo[a]) / (per ? g->n[a] : g->n[a] - 1);
-        h->inv_h[a] = 1.0 / h->h[a];
-        h->N *= g->n[a];
+    h->ndim = G.ndim;
+    h->nv = G.nv;
+    h->N = G.N;
+    for (int a = 0; a < 3; ++a) {
+        h->n[a] = G.n[a];
+        h->periodic[a] = G.periodic[a];
+        h->h[a] = G.h[a];
+        h->inv_h[a] = G.inv_h[a];
     }
+    h->G = G;
     // launch limits: the outer axis of the y and z sweeps is a grid z-dimension
     if ((h->ndim == 3 && (h->n[1] > 65535 || h->n[2] > 65535)) || h->N > (1LL << 40)) {
         delete h;
@@ -243,6 +233,14 @@ static cudaError_t run_rhs(wcns_handle* h, const void* U, void* L, uint8_t* flag
         a.dt = dtp;
         a.K = h->K;
         a.sqrt_eps_f = h->sqrt_eps_f;
+        a.bc_lo = h->G.bc[d][0];
+        a.bc_hi = h->G.bc[d][1];
+        for (int sd = 0; sd < 2; ++sd)
+            for (int v = 0; v < 5; ++v) a.bcs[sd][v] = h->G.bc_state[d][sd][v];
+        if (h->G.has_gravity && k == h->ndim - 1) {   // the last sweep adds the source
+            a.source = 1;
+            for (int b = 0; b < 3; ++b) a.grav[b] = h->G.gravity[b];
+        }
         if (fuse_stage && d == 0) {
             a.fuse_stage = fuse_stage;
             a.U0 = U0;
@@ -471,6 +469,10 @@ extern "C" wcns_status wcns_autotune(wcns_handle* h, const void* U, int* chosen,
                 a.fallback = h->fallback;
                 a.K = h->K;
                 a.sqrt_eps_f = h->sqrt_eps_f;
+                a.bc_lo = h->G.bc[d][0];
+                a.bc_hi = h->G.bc[d][1];
+                for (int sd = 0; sd < 2; ++sd)
+                    for (int v = 0; v < 5; ++v) a.bcs[sd][v] = h->G.bc_state[d][sd][v];
                 CK(launch_sweep_fp32(h->ndim, d, h->p.flux, cfg, a, s), "autotune warm-up");
                 CK(cudaEventRecord(e0, s), "event");
                 for (int r = 0; r < 3; ++r) CK(launch_sweep_fp32(h->ndim, d, h->p.flux, cfg, a, s), "autotune");

@@ -516,6 +516,12 @@ wcns_status wcns_batch_add(wcns_batch* b, const wcns_grid* g, const double* U0, 
     if (!b || !g || !U0 || !slot_out) return bfail(WCNS_ERR_INVALID, "wcns_batch_add: null argument");
     if (g->ndim != b->ndim) return bfail(WCNS_ERR_INVALID, "grid dimension differs from the batch's");
     if (!(t_end >= 0.0)) return bfail(WCNS_ERR_INVALID, "t_end must be >= 0");
+    if (grid_has_single_grid_features(g))
+        return bfail(WCNS_ERR_INVALID, "batches take periodic and transmissive boundaries without a body force");
+    for (int a = 0; a < b->ndim; ++a)
+        for (int sd = 0; sd < 2; ++sd)
+            if (g->bc[a][sd] != WCNS_BC_PERIODIC && g->bc[a][sd] != WCNS_BC_TRANSMISSIVE)
+                return bfail(WCNS_ERR_INVALID, "unknown boundary kind");
     BatchSlot s;
     s.N = 1;
     for (int a = 0; a < b->ndim; ++a) {

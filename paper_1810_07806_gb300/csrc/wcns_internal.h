@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdio.h>
 #include "../../include/wcns.h"
 #include "wcns_sweep.cuh"
 
@@ -11,6 +12,9 @@ static_assert((int)DIFF_MD == (int)WCNS_DIFF_MD6 && (int)DIFF_HWCNS == (int)WCNS
                   (int)DIFF_MND == (int)WCNS_DIFF_MND && (int)FLUX_AUSM == (int)WCNS_FLUX_AUSM &&
                   (int)FLUX_ROE == (int)WCNS_FLUX_ROE && (int)FLUX_VANLEER == (int)WCNS_FLUX_VANLEER,
               "scheme codes");
+static_assert((int)BC_TRANSMISSIVE == (int)WCNS_BC_TRANSMISSIVE && (int)BC_PERIODIC == (int)WCNS_BC_PERIODIC &&
+                  (int)BC_REFLECTING == (int)WCNS_BC_REFLECTING && (int)BC_FIXED == (int)WCNS_BC_FIXED,
+              "boundary codes");
 static_assert((int)W_TENO == (int)WCNS_W_TENO && (int)W_JS == (int)WCNS_W_JS &&
                   (int)W_LINEAR == (int)WCNS_W_LINEAR && (int)W_Z == (int)WCNS_W_Z,
               "weight codes");
@@ -34,6 +38,83 @@ inline const char* scheme_params_error(const wcns_scheme_params* p)
     if (p->weights == WCNS_W_JS && !(p->eps_js > 0.0)) return "eps_js must be positive";
     if (!(p->cfl > 0.0)) return "cfl must be positive";
     return nullptr;
+}
+
+// A checked grid: node counts, spacings and the boundary rule of each axis.
+struct GridInfo {
+    int ndim = 0, nv = 0;
+    int n[3] = {1, 1, 1};
+    long long N = 1;
+    double h[3] = {1, 1, 1}, inv_h[3] = {0, 0, 0};
+    int periodic[3] = {0, 0, 0};
+    int bc[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    double bc_state[3][2][5] = {};
+    double gravity[3] = {0, 0, 0};
+    bool special_bc = false;   // some side reflects or holds a fixed state
+    bool has_gravity = false;
+};
+
+// Checks a grid and fills G; nullptr when valid, otherwise the reason (in
+// buf).  Spacing: (hi - lo)/(n - 1) when both sides of the axis are
+// transmissive, (hi - lo)/n otherwise.
+inline const char* grid_error(const wcns_grid* g, double gamma, GridInfo& G, char* buf, size_t bufsz)
+{
+    if (g->ndim < 1 || g->ndim > 3) return "ndim must be 1, 2 or 3";
+    G.ndim = g->ndim;
+    G.nv = g->ndim + 2;
+    for (int a = 0; a < g->ndim; ++a) {
+        const int lo = g->bc[a][0], hi = g->bc[a][1];
+        for (int k : {lo, hi})
+            if (k < WCNS_BC_TRANSMISSIVE || k > WCNS_BC_FIXED) {
+                snprintf(buf, bufsz, "axis %d: unknown boundary kind", a);
+                return buf;
+            }
+        const int per = lo == WCNS_BC_PERIODIC;
+        if ((hi == WCNS_BC_PERIODIC) != per) {
+            snprintf(buf, bufsz, "axis %d: periodic must be set on both sides", a);
+            return buf;
+        }
+        const bool both_trans = lo == WCNS_BC_TRANSMISSIVE && hi == WCNS_BC_TRANSMISSIVE;
+        const bool reflect = lo == WCNS_BC_REFLECTING || hi == WCNS_BC_REFLECTING;
+        if (g->n[a] < (both_trans ? 2 : (reflect ? 5 : 1)) || !(g->hi[a] > g->lo[a])) {
+            snprintf(buf, bufsz, "axis %d: bad node count or extent (a reflecting axis needs 5 nodes)", a);
+            return buf;
+        }
+        for (int sd = 0; sd < 2; ++sd) {
+            G.bc[a][sd] = g->bc[a][sd];
+            if (g->bc[a][sd] == WCNS_BC_REFLECTING) G.special_bc = true;
+            if (g->bc[a][sd] != WCNS_BC_FIXED) continue;
+            G.special_bc = true;
+            const double* st = g->bc_state[a][sd];
+            double ke = 0.0;
+            for (int b = 0; b < g->ndim; ++b) ke += st[1 + b] * st[1 + b];
+            const double p = (gamma - 1.0) * (st[g->ndim + 1] - 0.5 * ke / st[0]);
+            if (!(st[0] > 0.0) || !(p > 0.0) || !isfinite(p)) {
+                snprintf(buf, bufsz, "axis %d side %d: the fixed state needs rho > 0 and p > 0", a, sd);
+                return buf;
+            }
+            for (int v = 0; v < G.nv; ++v) G.bc_state[a][sd][v] = st[v];
+        }
+        G.n[a] = g->n[a];
+        G.periodic[a] = per;
+        G.h[a] = (g->hi[a] - g->lo[a]) / (both_trans ? g->n[a] - 1 : g->n[a]);
+        G.inv_h[a] = 1.0 / G.h[a];
+        G.N *= g->n[a];
+        if (!isfinite(g->gravity[a])) return "gravity must be finite";
+        G.gravity[a] = g->gravity[a];
+        if (g->gravity[a] != 0.0) G.has_gravity = true;
+    }
+    return nullptr;
+}
+
+// Reflecting or fixed sides, or a body force: single-grid features.
+inline bool grid_has_single_grid_features(const wcns_grid* g)
+{
+    for (int a = 0; a < g->ndim && a < 3; ++a) {
+        if (g->bc[a][0] >= WCNS_BC_REFLECTING || g->bc[a][1] >= WCNS_BC_REFLECTING) return true;
+        if (g->gravity[a] != 0.0) return true;
+    }
+    return false;
 }
 
 // Device constants of a valid parameter set.

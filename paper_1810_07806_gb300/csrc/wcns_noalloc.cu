@@ -68,6 +68,8 @@ extern "C" wcns_status wcns_step_rk3_noalloc(const wcns_grid* g, double gamma,
     if (prm->precision != WCNS_FP64)
         return fail(WCNS_ERR_INVALID, "wcns_step_rk3_noalloc: precision must be WCNS_FP64");
     if (const char* why = scheme_params_error(prm)) return fail(WCNS_ERR_INVALID, why);
+    if (grid_has_single_grid_features(g))
+        return fail(WCNS_ERR_INVALID, "wcns_step_rk3_noalloc: periodic and transmissive boundaries only, no body force");
 
     const int nd = g->ndim, nv = nd + 2;
     int n[3] = {1, 1, 1}, periodic[3] = {0, 0, 0};

@@ -21,6 +21,7 @@
 namespace wcns {
 
 enum { FLUX_ROE = 0, FLUX_VANLEER = 1, FLUX_AUSM = 2 };
+enum { BC_TRANSMISSIVE = 0, BC_PERIODIC = 1, BC_REFLECTING = 2, BC_FIXED = 3 };
 
 // Batched sweeps run over many independent grids ("instances") of one
 // dimension at once: each CTA takes one tile from a table and reads its
@@ -67,6 +68,14 @@ struct SweepArgs {
     double* U0;
     float* D;
     float* S_out;
+    // boundary rule of a non-periodic direction (single grids; batches leave
+    // both sides transmissive): WCNS_BC_* kinds of the low and high side and
+    // the fixed states; the last sweep of an RHS adds the body-force source
+    // (0, rho g, rho u.g) when source is set
+    int bc_lo, bc_hi;
+    double bcs[2][5];
+    int source;
+    double grav[3];
     // batched mode only
     const BatchInst* insts;
     const BatchTile* tiles;
@@ -385,6 +394,9 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) swee
     // periodic axis is shorter than the staged window.
     const LT* U = Ub;
     const bool wrap_mod = periodic && nd < P;
+    // reflecting walls (ghost -1-k mirrors node k, normal momentum negated;
+    // the axis has at least 5 nodes) and fixed states: synchronous copies
+    const bool bc_special = !BATCH && (a.bc_lo >= BC_REFLECTING || a.bc_hi >= BC_REFLECTING);
     for (int e = threadIdx.x; e < TL * P; e += blockDim.x) {
         int l, s;
         if (DIR == 0) { s = e % P; l = e / P; } else { l = e % TL; s = e / TL; }
@@ -393,6 +405,25 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) swee
         if (periodic) {
             if (wrap_mod) { p %= nd; if (p < 0) p += nd; }
             else p = p < 0 ? p + nd : (p >= nd ? p - nd : p);
+        } else if (bc_special && (p < 0 || p >= nd)) {
+            const int kind = p < 0 ? a.bc_lo : a.bc_hi;
+            if (kind == BC_FIXED) {
+                const double* st = a.bcs[p < 0 ? 0 : 1];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) sS[sidx<DIR, TL, P>(v, l, s)] = (T)st[v];
+                continue;
+            }
+            if (kind == BC_REFLECTING) {
+                const int q = p < 0 ? -1 - p : 2 * nd - 1 - p;
+                const LT* src = U + base0 + l * lstride + (long long)q * sd;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    const T val = (T)src[v * N];
+                    sS[sidx<DIR, TL, P>(v, l, s)] = v == 1 + DIR ? -val : val;
+                }
+                continue;
+            }
+            p = p < 0 ? 0 : nd - 1;   // the other side is transmissive
         } else {
             p = min(max(p, 0), nd - 1);
         }
@@ -480,6 +511,8 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) swee
     // the node fluxes Eq. 4-5 need.
     T* L = Lb;
     const int diff = a.K.diff;
+    // ALT: Eq. 4-5 and / or the body-force source; the plain Eq. 3 instance
+    // carries neither
     auto node_phase = [&](auto alt_tag) {
         constexpr bool ALT = decltype(alt_tag)::value;
         for (int e = threadIdx.x; e < TL * TS; e += blockDim.x) {
@@ -489,13 +522,29 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) swee
             const long long g = base0 + l * lstride + (long long)(pos0 + t) * sd;
             // Eq. 4-5 also difference the physical fluxes of the nodes i+-1
             // (and i+-2): d1 = f_{i+1} - f_{i-1}, d2 = f_{i+2} - f_{i-2}
-            T d1[NV], d2[NV];
+            T d1[NV], d2[NV], S[NV];
             if constexpr (ALT) {
-                node_flux_diff<ND, DIR, TL, P>(sS, l, t + GHOST, 1, a.K, d1);
-                if (diff == DIFF_HWCNS) node_flux_diff<ND, DIR, TL, P>(sS, l, t + GHOST, 2, a.K, d2);
-                else
 #pragma unroll
-                    for (int v = 0; v < NV; ++v) d2[v] = T(0);
+                for (int v = 0; v < NV; ++v) d1[v] = d2[v] = S[v] = T(0);
+                if (diff != DIFF_MD) node_flux_diff<ND, DIR, TL, P>(sS, l, t + GHOST, 1, a.K, d1);
+                if (diff == DIFF_HWCNS) node_flux_diff<ND, DIR, TL, P>(sS, l, t + GHOST, 2, a.K, d2);
+                if (a.source) {
+                    // (0, rho g_a, sum_a g_a m_a), the sum from 0 in axis order
+                    const T rho = sS[sidx<DIR, TL, P>(0, l, t + GHOST)];
+                    T se = T(0);
+#pragma unroll
+                    for (int b = 0; b < ND; ++b) {
+                        const T gb = T(a.grav[b]), mb = sS[sidx<DIR, TL, P>(1 + b, l, t + GHOST)];
+                        if constexpr (sizeof(T) == 8) {
+                            S[1 + b] = mul_(gb, rho);
+                            se = add_(se, mul_(gb, mb));
+                        } else {
+                            S[1 + b] = gb * rho;
+                            se = fma(gb, mb, se);
+                        }
+                    }
+                    S[NV - 1] = se;
+                }
             }
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
@@ -504,12 +553,20 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) swee
                 const T f4 = sF[sidx<DIR, TL, NF>(v, l, t + 4)], f5 = sF[sidx<DIR, TL, NF>(v, l, t + 5)];
                 if constexpr (sizeof(T) == 8) {
                     double q;                                      // L -= f'
-                    if constexpr (ALT) q = mul_(diff_alt_fp64(diff, f1, f2, f3, f4, d1[v], d2[v]), ih);
+                    if constexpr (ALT)
+                        q = diff == DIFF_MD ? md_fp64(f0, f1, f2, f3, f4, f5, ih)
+                                            : mul_(diff_alt_fp64(diff, f1, f2, f3, f4, d1[v], d2[v]), ih);
                     else q = md_fp64(f0, f1, f2, f3, f4, f5, ih);
-                    L[v * N + g] = a.accumulate ? sub_(L[v * N + g], q) : -q;
+                    double lval = a.accumulate ? sub_(L[v * N + g], q) : -q;
+                    if constexpr (ALT) {
+                        if (a.source && v > 0) lval = add_(lval, S[v]);   // after every direction
+                    }
+                    L[v * N + g] = lval;
                 } else {
                     T fp;
                     if constexpr (!ALT)
+                        fp = fma(T(MD_A1), f3 - f2, fma(T(MD_A2), f4 - f1, T(MD_A3) * (f5 - f0)));
+                    else if (diff == DIFF_MD)
                         fp = fma(T(MD_A1), f3 - f2, fma(T(MD_A2), f4 - f1, T(MD_A3) * (f5 - f0)));
                     else if (diff == DIFF_HWCNS)
                         fp = fma(T(HW_B1), f3 - f2, fma(T(HW_B2), d1[v], T(HW_B3) * d2[v]));
@@ -520,6 +577,9 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) swee
                     if (a.accumulate) {
                         if constexpr (kPre) lv = sL[sidx<DIR, TL, TS>(v, l, t)] + val;
                         else lv = L[v * N + g] + val;
+                    }
+                    if constexpr (ALT) {
+                        if (a.source) lv += S[v];
                     }
                     if constexpr (G::FUSE) {
                         if (a.fuse_stage) {
@@ -550,7 +610,7 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) swee
             }
         }
     };
-    if (diff == DIFF_MD) node_phase(std::false_type{});
+    if (diff == DIFF_MD && !a.source) node_phase(std::false_type{});
     else node_phase(std::true_type{});
 }
 

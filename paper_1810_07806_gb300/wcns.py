@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libwcns.so")
 
 OK, ERR_INVALID, ERR_NOMEM, ERR_NONPHYSICAL, ERR_TIMEOUT, ERR_BUSY, ERR_CUDA = range(7)
-BC_TRANSMISSIVE, BC_PERIODIC = 0, 1
+BC_TRANSMISSIVE, BC_PERIODIC, BC_REFLECTING, BC_FIXED = 0, 1, 2, 3
 FLUX_ROE, FLUX_VANLEER, FLUX_AUSM = 0, 1, 2
 DIFF_MD6, DIFF_HWCNS, DIFF_MND = 0, 1, 2
 FP64, FP32 = 0, 1
@@ -28,7 +28,7 @@ class WcnsError(RuntimeError):
 
 class Grid(C.Structure):
     _fields_ = [("ndim", C.c_int), ("n", C.c_int * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
-                ("bc", (C.c_int * 2) * 3)]
+                ("bc", (C.c_int * 2) * 3), ("bc_state", ((C.c_double * 5) * 2) * 3), ("gravity", C.c_double * 3)]
 
 
 class SchemeParams(C.Structure):
@@ -91,7 +91,10 @@ def default_params(**kw):
     return p
 
 
-def make_grid(ndim, n, lo, hi, periodic):
+def make_grid(ndim, n, lo, hi, periodic, bc_lo=None, bc_hi=None, bc_state=None, gravity=None):
+    """periodic axes wrap; other axes are transmissive unless bc_lo / bc_hi
+    give a kind per axis (BC_REFLECTING, BC_FIXED with bc_state[axis][side]
+    the conserved state).  gravity: body force per unit mass."""
     g = Grid()
     g.ndim = ndim
     for a in range(3):
@@ -101,7 +104,25 @@ def make_grid(ndim, n, lo, hi, periodic):
         kind = BC_PERIODIC if (a < ndim and periodic[a]) else BC_TRANSMISSIVE
         g.bc[a][0] = kind
         g.bc[a][1] = kind
+        if a < ndim and not periodic[a]:
+            if bc_lo is not None and bc_lo[a] in (BC_REFLECTING, BC_FIXED):
+                g.bc[a][0] = bc_lo[a]
+            if bc_hi is not None and bc_hi[a] in (BC_REFLECTING, BC_FIXED):
+                g.bc[a][1] = bc_hi[a]
+        if bc_state is not None and a < len(bc_state) and bc_state[a] is not None:
+            for sd in range(2):
+                st = bc_state[a][sd]
+                if st is not None:
+                    for v in range(len(st)):
+                        g.bc_state[a][sd][v] = float(st[v])
+        g.gravity[a] = float(gravity[a]) if (gravity is not None and a < len(gravity)) else 0.0
     return g
+
+
+def grid_of(pb):
+    """The wcns_grid of an inputs.Problem (boundary kinds, fixed states, gravity)."""
+    return make_grid(pb.ndim, pb.n, pb.lo, pb.hi, pb.periodic, getattr(pb, "bc_lo", None),
+                     getattr(pb, "bc_hi", None), getattr(pb, "bc_state", None), getattr(pb, "gravity", None))
 
 
 def _stream(stream):
@@ -118,19 +139,19 @@ def _ptr(t):
 class Solver:
     """One grid + scheme on the current CUDA device (a wcns_handle)."""
 
-    def __init__(self, ndim, n, lo, hi, periodic, gamma=1.4, **params):
+    def __init__(self, ndim, n, lo, hi, periodic, gamma=1.4, grid=None, **params):
         self.ndim = ndim
         self.n = tuple(int(v) for v in n[:ndim])
         self.nv = ndim + 2
         self.params = default_params(**params)
-        self.grid = make_grid(ndim, n, lo, hi, periodic)
+        self.grid = grid if grid is not None else make_grid(ndim, n, lo, hi, periodic)
         h = C.c_void_p()
         check(lib().wcns_create(C.byref(self.grid), gamma, C.byref(self.params), C.byref(h)))
         self.h = h
 
     @classmethod
     def for_problem(cls, pb, **params):
-        return cls(pb.ndim, pb.n, pb.lo, pb.hi, pb.periodic, pb.gamma, **params)
+        return cls(pb.ndim, pb.n, pb.lo, pb.hi, pb.periodic, pb.gamma, grid=grid_of(pb), **params)
 
     def close(self):
         if getattr(self, "h", None):
@@ -328,7 +349,7 @@ class Batch:
         """Add a Problem (inputs.Problem); U0: a CUDA tensor or a numpy array
         (defaults to pb.U0).  Returns the slot."""
         import numpy as np
-        g = make_grid(pb.ndim, pb.n, pb.lo, pb.hi, pb.periodic)
+        g = grid_of(pb)
         U0 = pb.U0 if U0 is None else U0
         slot = C.c_int()
         if isinstance(U0, np.ndarray):
@@ -435,7 +456,7 @@ class Server:
         import numpy as np
         U0 = np.ascontiguousarray(pb.U0, dtype=np.float64)
         req = Request()
-        req.grid = make_grid(pb.ndim, pb.n, pb.lo, pb.hi, pb.periodic)
+        req.grid = grid_of(pb)
         req.gamma = pb.gamma
         req.params = default_params(**params)
         req.U0 = U0.ctypes.data_as(C.POINTER(C.c_double))

@@ -104,3 +104,38 @@ def test_fp32_batch_rejects_comparison_weights_without_a_gpu():
         h = C.c_void_p()
         assert L.wcns_batch_create(1, 1.4, C.byref(p), 1000, 4, C.byref(h)) == wcns.ERR_INVALID
         assert h.value is None
+
+
+@pytest.mark.parametrize("case", ["reflect_short", "kind4", "fixed_bad_rho", "fixed_bad_p", "gravity_nan"])
+def test_create_rejects_bad_boundaries_without_a_gpu(case):
+    g = wcns.make_grid(2, (16, 16), (0, 0), (1, 1), (0, 0))
+    if case == "reflect_short":
+        g.n[0] = 4
+        g.bc[0][0] = wcns.BC_REFLECTING
+    elif case == "kind4":
+        g.bc[1][1] = 4
+    elif case in ("fixed_bad_rho", "fixed_bad_p"):
+        g.bc[1][0] = wcns.BC_FIXED
+        state = (0.0, 0.0, 0.0, 1.0) if case == "fixed_bad_rho" else (1.0, 0.0, 0.0, -1.0)
+        for v in range(4):
+            g.bc_state[1][0][v] = state[v]
+    else:
+        g.gravity[1] = float("nan")
+    st, h = _create(g)
+    assert st == wcns.ERR_INVALID and h.value is None
+    assert len(wcns.lib().wcns_last_error()) > 0
+
+
+def test_noalloc_step_rejects_single_grid_features_without_a_gpu():
+    L = wcns.lib()
+    fn = L.wcns_step_rk3_noalloc
+    fn.argtypes = [C.POINTER(wcns.Grid), C.c_double, C.POINTER(wcns.SchemeParams), C.c_void_p, C.c_double,
+                   C.POINTER(C.c_double), C.c_void_p]
+    p = wcns.default_params()
+    for kind in ("gravity", "reflect"):
+        g = wcns.make_grid(2, (16, 16), (0, 0), (1, 1), (0, 0))
+        if kind == "gravity":
+            g.gravity[1] = 1.0
+        else:
+            g.bc[0][0] = g.bc[0][1] = wcns.BC_REFLECTING
+        assert fn(C.byref(g), 1.4, C.byref(p), C.c_void_p(16), 0.0, None, None) == wcns.ERR_INVALID

@@ -1,0 +1,138 @@
+"""GPU parity of the Rayleigh-Taylor ingredients (Sec. 3.9) through the C ABI:
+reflecting walls, fixed-state sides and the body-force source, against the
+FP64 oracle (bit for bit) and the FP64 path (FP32, bounded)."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1810_07806_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1810_07806_gb300 import wcns  # noqa: E402
+
+DEV = "cuda:0"
+FLUX = {"roe": (wcns.FLUX_ROE, O.FLUX_ROE), "vanleer": (wcns.FLUX_VANLEER, O.FLUX_VANLEER),
+        "ausm": (wcns.FLUX_AUSM, O.FLUX_AUSM)}
+
+
+def ora_cfg(pb, flux="roe", diff=O.DIFF_MD):
+    oc = lambda k: k if k in (O.BC_REFLECT, O.BC_FIXED) else O.BC_AUTO
+    return O.make_cfg(ndim=pb.ndim, n=pb.n, h=pb.h, periodic=pb.periodic, gamma=pb.gamma, flux=FLUX[flux][1],
+                      diff=diff, bc_lo=tuple(oc(k) for k in pb.bc_lo), bc_hi=tuple(oc(k) for k in pb.bc_hi),
+                      bc_state=pb.bc_state, gravity=pb.gravity)
+
+
+def gpu_rhs(pb, U, flux="roe", precision=wcns.FP64, diff=wcns.DIFF_MD6):
+    s = wcns.Solver.for_problem(pb, flux=FLUX[flux][0], precision=precision, diff=diff)
+    dt = torch.float32 if precision == wcns.FP32 else torch.float64
+    Ud = torch.from_numpy(np.ascontiguousarray(U)).to(DEV, dt)
+    Ld = torch.empty_like(Ud)
+    fl = torch.zeros(s.flags_bytes, dtype=torch.uint8, device=DEV)
+    s.rhs(Ud, Ld, fl)
+    torch.cuda.synchronize()
+    out = Ld.double().cpu().numpy(), fl.cpu().numpy(), s.fallback_count()
+    s.close()
+    return out
+
+
+def _mixed(nd, n, seed, lo, hi, gravity=(0.0, 0.0, 0.0)):
+    """Rough state with the given boundary kinds per axis side; fixed sides
+    hold random physical states."""
+    rng = np.random.default_rng(seed)
+    U = inputs.random_rough_state(nd, n, seed)
+    states = []
+    for a in range(3):
+        pair = []
+        for sd in range(2):
+            rho, p = rng.uniform(0.5, 2.0), rng.uniform(0.5, 2.0)
+            vel = [np.array(rng.uniform(-0.5, 0.5)) for _ in range(nd)]
+            pair.append(tuple(inputs.prim_to_cons(np.array(rho), vel, np.array(p), 1.4)))
+        states.append(tuple(pair))
+    periodic = tuple(1 if lo[a] == wcns.BC_PERIODIC else 0 for a in range(nd))
+    h = tuple((1.0 + 0.3 * a) / (n[a] - 1 if (lo[a], hi[a]) == (0, 0) else n[a]) for a in range(nd))
+    return inputs.Problem("mixed", nd, tuple(n), (0.0,) * nd, tuple(1.0 + 0.3 * a for a in range(nd)), periodic,
+                          1.4, np.ascontiguousarray(U), 0.0, h, bc_lo=tuple(lo) + (0,) * (3 - nd),
+                          bc_hi=tuple(hi) + (0,) * (3 - nd), bc_state=tuple(states), gravity=gravity)
+
+
+R, F, T, P = wcns.BC_REFLECTING, wcns.BC_FIXED, wcns.BC_TRANSMISSIVE, wcns.BC_PERIODIC
+
+
+@pytest.mark.parametrize("flux", sorted(FLUX))
+def test_rayleigh_taylor_rhs_bit_identical(flux):
+    pb = inputs.rayleigh_taylor(16)
+    cfg = ora_cfg(pb, flux)
+    states = [pb.U0]
+    U = pb.U0.copy()
+    for _ in range(4):
+        O.rk3_step(cfg, U, 2e-3)
+    states.append(U)
+    for Us in states:
+        Lo, flo, _, np_o, _ = O.euler_rhs(cfg, Us, want_flags=True)
+        Lg, flg, np_g = gpu_rhs(pb, Us, flux)
+        assert np.array_equal(Lg, Lo), np.max(np.abs(Lg - Lo))
+        assert np.array_equal(flg, flo) and np_g == np_o
+
+
+@pytest.mark.parametrize("nd,n,lo,hi", [
+    (1, (37,), (R,), (F,)), (1, (9,), (F,), (T,)), (1, (5,), (R,), (R,)),
+    (2, (23, 17), (R, F), (T, R)), (2, (16, 30), (P, F), (P, F)), (2, (70, 7), (F, R), (R, T)),
+    (3, (11, 9, 13), (R, P, F), (R, P, T)), (3, (7, 12, 6), (F, R, R), (T, F, R))])
+@pytest.mark.parametrize("gravity", [(0.0, 0.0, 0.0), (0.4, -1.0, 0.25)])
+def test_boundary_kinds_and_source_bit_identical(nd, n, lo, hi, gravity):
+    pb = _mixed(nd, n, sum(n) + nd, lo, hi, gravity)
+    for flux in ("roe", "ausm"):
+        Lo, flo, _, np_o, _ = O.euler_rhs(ora_cfg(pb, flux), pb.U0, want_flags=True)
+        Lg, flg, np_g = gpu_rhs(pb, pb.U0, flux)
+        assert np.array_equal(Lg, Lo), (flux, np.max(np.abs(Lg - Lo)))
+        assert np.array_equal(flg, flo) and np_g == np_o
+
+
+def test_boundary_kinds_with_eq5_bit_identical():
+    pb = _mixed(2, (23, 17), 5, (R, F), (F, R), (0.0, 1.0, 0.0))
+    Lo = O.euler_rhs(ora_cfg(pb, "vanleer", O.DIFF_MND), pb.U0)[0]
+    Lg = gpu_rhs(pb, pb.U0, "vanleer", diff=wcns.DIFF_MND)[0]
+    assert np.array_equal(Lg, Lo)
+
+
+def test_rayleigh_taylor_run_bit_identical_to_oracle():
+    pb = inputs.rayleigh_taylor(16)
+    cfg = ora_cfg(pb, "roe")
+    Uo = pb.U0.copy()
+    t_o, steps_o, np_o = O.euler_run(cfg, Uo, 0.5, 0.2)
+    s = wcns.Solver.for_problem(pb, cfl=0.5)
+    Ud = torch.from_numpy(pb.U0.copy()).to(DEV)
+    t_g, steps_g = s.advance(Ud, 0.2, check_every=16)
+    assert (t_g, steps_g) == (t_o, steps_o)
+    assert np.array_equal(Ud.cpu().numpy(), Uo)
+    assert s.fallback_count() == np_o
+    s.close()
+
+
+def test_rayleigh_taylor_fp32_close_to_fp64_and_symmetric():
+    pb = inputs.rayleigh_taylor(32)
+    out = {}
+    for prec in (wcns.FP64, wcns.FP32):
+        s = wcns.Solver.for_problem(pb, precision=prec, cfl=0.5)
+        Ud = torch.from_numpy(pb.U0.copy()).to(DEV)
+        s.advance(Ud, 0.3, check_every=16)
+        out[prec] = Ud.cpu().numpy()
+        s.close()
+    a, b = out[wcns.FP64], out[wcns.FP32]
+    rel = np.sum(np.abs(b - a), axis=(1, 2)) / np.sum(np.abs(a), axis=(1, 2))
+    assert rel[0] <= 1e-5 and rel[3] <= 1e-5, rel
+    # the x -> 1/4 - x mirror image of the density stays close in FP32
+    assert np.max(np.abs(b[0] - b[0][:, ::-1])) <= 1e-4
+
+
+def test_batches_and_server_reject_single_grid_features():
+    pb = inputs.rayleigh_taylor(8)
+    b = wcns.Batch(2, max_nodes=pb.cells, max_instances=1)
+    with pytest.raises(wcns.WcnsError):
+        b.add(pb, t_end=0.1)
+    b.close()
