@@ -9,7 +9,7 @@ RHS evaluations; value = nodes x 3 x steps x ranks / max-over-ranks time.
 The FP64 plain path is timed on the same workload and reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload tgv256|quad1024|sod400|batch1d|serve|scalar]
+                  [--workload tgv256|tgv192|quad1024|sod400|rt1024|batch1d|serve|scalar]
 
 With N > 1 (torchrun) every rank advances its own replica (weak scaling,
 no data-path collective: the instances are independent).
@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tgv256",
-                    choices=["tgv256", "quad1024", "sod400", "rt1024", "batch1d", "serve", "scalar"])
+                    choices=["tgv256", "tgv192", "quad1024", "sod400", "rt1024", "batch1d", "serve", "scalar"])
     ap.add_argument("--requests", type=int, default=32, help="serve: requests replayed from the trace")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrival rate (1/s)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain-path line")
@@ -68,6 +68,10 @@ def workload(name):
     if name == "tgv256":
         pb = inputs.taylor_green(256)
         return pb, dict(workload="taylor_green_3d_256^3_periodic", nodes=pb.cells, nv=5,
+                        precision="fp32 bulk (fp64 reductions + accumulation)", flux="roe", cfl=0.5), True
+    if name == "tgv192":   # the same flow on a smaller grid (profiler captures: state still > L2)
+        pb = inputs.taylor_green(192)
+        return pb, dict(workload="taylor_green_3d_192^3_periodic", nodes=pb.cells, nv=5,
                         precision="fp32 bulk (fp64 reductions + accumulation)", flux="roe", cfl=0.5), True
     if name == "rt1024":
         pb = inputs.rayleigh_taylor(256)

@@ -243,6 +243,60 @@ __device__ __forceinline__ T interp_row(int flags, const T s[5])
 }
 
 // ------------------------------------------------------------------------
+// Paired FP32 arithmetic (Blackwell packed f32x2 instructions).  The left-
+// and right-biased halves of a face, and mirrored node pairs (m, 5 - m), run
+// the same operations on different data; carrying them in the two lanes of
+// a float2 halves the instructions issued for that work.
+// ------------------------------------------------------------------------
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 swap2(float2 a) { return make_float2(a.y, a.x); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, bc2(-1.f), a); }
+
+// Both biased selections and interpolations of one characteristic field,
+// paired: S0 = (w_{j-2}, w_{j+3}), S1 = (w_{j-1}, w_{j+2}), S2 = (w_j, w_{j+1})
+// are the left stencil's s0..s2 in .x and the mirrored right stencil's in
+// .y (s3, s4 are the swapped S2, S1).  Same rescaling and cutoff as
+// select_pair_fp32; returns (u_L, u_R) and the two flag words.
+__device__ __forceinline__ float2 select_interp_x2(float2 S0, float2 S1, float2 S2, float sqrt_eps,
+                                                   const SchemeConst& K, int& fL, int& fR)
+{
+    float sc = fmaxf(fmaxf(fmaxf(fabsf(S0.x), fabsf(S0.y)), fmaxf(fabsf(S1.x), fabsf(S1.y))),
+                     fmaxf(fabsf(S2.x), fabsf(S2.y)));
+    sc = fmaxf(sc, 1.17549435e-38f);
+    const float inv = __frcp_rn(sc);
+    const float e = sqrt_eps * inv;
+    const float eps_s = fmaxf(e * e, 1.17549435e-38f);
+    const float2 iv = bc2(inv);
+    const float2 T0 = mul2(S0, iv), T1 = mul2(S1, iv), T2 = mul2(S2, iv);
+    const float2 T3 = swap2(T2), T4 = swap2(T1);
+    // second differences (left a2, b2, c2 / right d2, c2, b2) and first (Eq. 10-11)
+    const float2 D20 = add2(fma2(bc2(-2.f), T1, T0), T2);
+    const float2 D21 = add2(fma2(bc2(-2.f), T2, T1), T3);
+    const float2 D22 = add2(fma2(bc2(-2.f), T3, T2), T4);
+    const float2 D10 = mul2(bc2(0.5f), fma2(bc2(3.f), T2, fma2(bc2(-4.f), T1, T0)));
+    const float2 D11 = mul2(bc2(0.5f), sub2(T3, T1));
+    const float2 D12 = mul2(bc2(0.5f), sub2(fma2(bc2(4.f), T3, mul2(bc2(-3.f), T2)), T4));
+    const float2 B0 = fma2(D10, D10, mul2(D20, D20));   // Eq. 15
+    const float2 B1 = fma2(D11, D11, mul2(D21, D21));
+    const float2 B2 = fma2(D12, D12, mul2(D22, D22));
+    fL = cut_fp32(B0.x, B1.x, B2.x, eps_s, K);
+    fR = cut_fp32(B0.y, B1.y, B2.y, eps_s, K);
+    if ((fL & fR) == 7) {                                 // Eq. 7 on both sides
+        float2 u = mul2(bc2(3.0f / 128), S0);
+        u = fma2(bc2(-5.0f / 32), S1, u);
+        u = fma2(bc2(45.0f / 64), S2, u);
+        u = fma2(bc2(15.0f / 32), swap2(S2), u);
+        return fma2(bc2(-5.0f / 128), swap2(S1), u);
+    }
+    const float sl[5] = {S0.x, S1.x, S2.x, S2.y, S1.y};
+    const float sr[5] = {S0.y, S1.y, S2.y, S2.x, S1.x};
+    return make_float2(interp_row<float>(fL, sl), interp_row<float>(fR, sr));
+}
+
+// ------------------------------------------------------------------------
 // Euler primitives and midpoint fluxes (any evaluation order).
 // ------------------------------------------------------------------------
 template <int ND, typename T>

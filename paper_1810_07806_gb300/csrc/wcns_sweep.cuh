@@ -184,48 +184,91 @@ __device__ __forceinline__ void face_flux(float (&u)[6][ND + 2], const SweepArgs
     float Uj[NV], Uj1[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) { Uj[v] = Ua[v]; Uj1[v] = Ub[v]; }
+    float UL[NV], UR[NV];
+    if constexpr (WT == W_TENO) {
+        // mirrored node pairs (m, 5 - m) in the two lanes: W2[m][k] =
+        // (W_m[k], W_{5-m}[k]), i.e. the left stencil's value in .x and the
+        // mirrored right stencil's in .y
+        float2 W2[3][NV];
+        const float2 hq = bc2(0.5f * q2), hb = bc2(hb1), qa = bc2(0.5f * ic * un), qb = bc2(-0.5f * ic);
 #pragma unroll
-    for (int m = 0; m < 6; ++m) {
-        float* U = u[m];
-        float vm = vel[0] * U[1];
+        for (int m = 0; m < 3; ++m) {
+            float2 U2[NV];
 #pragma unroll
-        for (int d = 1; d < ND; ++d) vm = fmaf(vel[d], U[1 + d], vm);
-        const float Ph = hb1 * (fmaf(0.5f * q2, U[0], U[ND + 1]) - vm);   // P/2
-        const float Qh = 0.5f * ic * fmaf(un, U[0], -U[1 + DIR]);         // Q/2
-        float W[NV];
-        W[0] = Ph + Qh;
-        W[1] = fmaf(-2.f, Ph, U[0]);
+            for (int v = 0; v < NV; ++v) U2[v] = make_float2(u[m][v], u[5 - m][v]);
+            float2 vm = mul2(bc2(vel[0]), U2[1]);
+#pragma unroll
+            for (int d = 1; d < ND; ++d) vm = fma2(bc2(vel[d]), U2[1 + d], vm);
+            const float2 Ph = mul2(hb, sub2(fma2(hq, U2[0], U2[ND + 1]), vm));   // P/2
+            const float2 Qh = fma2(qa, U2[0], mul2(qb, U2[1 + DIR]));            // Q/2
+            W2[m][0] = add2(Ph, Qh);
+            W2[m][1] = fma2(bc2(-2.f), Ph, U2[0]);
+            int k = 2;
+#pragma unroll
+            for (int t = 0; t < ND; ++t) {
+                if (t == DIR) continue;
+                W2[m][k++] = fma2(bc2(-vel[t]), U2[0], U2[1 + t]);
+            }
+            W2[m][NV - 1] = sub2(Ph, Qh);
+        }
+        float2 w2[NV];   // (u_L, u_R) of each characteristic field
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            int fL, fR;
+            w2[k] = select_interp_x2(W2[0][k], W2[1][k], W2[2][k], a.sqrt_eps_f, a.K, fL, fR);
+            fl[k] = (uint8_t)(fL | (fR << 3));
+        }
+        // U = R w for both sides at once
+        const float2 r = add2(add2(w2[0], w2[1]), w2[NV - 1]);
+        const float2 dw = sub2(w2[NV - 1], w2[0]);
+        float2 U2[NV];
+        U2[0] = r;
+        float2 e = fma2(bc2(H), add2(w2[0], w2[NV - 1]), fma2(bc2(un * c), dw, mul2(hq, w2[1])));
         int k = 2;
 #pragma unroll
         for (int t = 0; t < ND; ++t) {
-            if (t == DIR) continue;
-            W[k++] = fmaf(-vel[t], U[0], U[1 + t]);
+            if (t == DIR) {
+                U2[1 + t] = fma2(bc2(vel[t]), r, mul2(bc2(c), dw));
+            } else {
+                U2[1 + t] = fma2(bc2(vel[t]), r, w2[k]);
+                e = fma2(bc2(vel[t]), w2[k], e);
+                ++k;
+            }
         }
-        W[NV - 1] = Ph - Qh;
+        U2[NV - 1] = e;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) U[v] = W[v];
-    }
-    float wL[NV], wR[NV];
+        for (int v = 0; v < NV; ++v) { UL[v] = U2[v].x; UR[v] = U2[v].y; }
+    } else {
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        float sl[5], sr[5], s6[6];
+        for (int m = 0; m < 6; ++m) {
+            float* U = u[m];
+            float vm = vel[0] * U[1];
 #pragma unroll
-        for (int m = 0; m < 6; ++m) s6[m] = u[m][k];
+            for (int d = 1; d < ND; ++d) vm = fmaf(vel[d], U[1 + d], vm);
+            const float Ph = hb1 * (fmaf(0.5f * q2, U[0], U[ND + 1]) - vm);   // P/2
+            const float Qh = 0.5f * ic * fmaf(un, U[0], -U[1 + DIR]);         // Q/2
+            float W[NV];
+            W[0] = Ph + Qh;
+            W[1] = fmaf(-2.f, Ph, U[0]);
+            int k = 2;
 #pragma unroll
-        for (int m = 0; m < 5; ++m) { sl[m] = u[m][k]; sr[m] = u[5 - m][k]; }
-        if constexpr (WT == W_TENO) {
-            int fL, fR;
-            select_pair_fp32(s6, a.sqrt_eps_f, a.K, fL, fR);
-            wL[k] = interp_row<float>(fL, sl);
-            wR[k] = interp_row<float>(fR, sr);
-            fl[k] = (uint8_t)(fL | (fR << 3));
-        } else {
+            for (int t = 0; t < ND; ++t) {
+                if (t == DIR) continue;
+                W[k++] = fmaf(-vel[t], U[0], U[1 + t]);
+            }
+            W[NV - 1] = Ph - Qh;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) U[v] = W[v];
+        }
+        float wL[NV], wR[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            float s6[6];
+#pragma unroll
+            for (int m = 0; m < 6; ++m) s6[m] = u[m][k];
             weights_pair_fp32<WT>(s6, a.sqrt_eps_f, a.K, wL[k], wR[k]);
             fl[k] = 0x3F;
         }
-    }
-    float UL[NV], UR[NV];
-    {
         const float rl = wL[0] + wL[1] + wL[NV - 1], rr = wR[0] + wR[1] + wR[NV - 1];
         const float dl = wL[NV - 1] - wL[0], dr = wR[NV - 1] - wR[0];
         UL[0] = rl;
