@@ -255,6 +255,50 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, bc2(-1.f), a); }
 
+// The cutoff of cut_fp32 for both sides at once: the no-cut test per lane,
+// and, when either side may cut, the ratio form of Eq. 16-18 in packed
+// arithmetic (a side that passed the test keeps its 7).
+__device__ __forceinline__ void cut_x2(float2 B0, float2 B1, float2 B2, float eps_s, const SchemeConst& K,
+                                       int& fL, int& fR)
+{
+    const float2 d02 = sub2(B0, B2);
+    const float tauL = fabsf(d02.x), tauR = fabsf(d02.y);
+    const float bmL = fminf(fminf(B0.x, B1.x), B2.x) + eps_s;
+    const float bmR = fminf(fminf(B0.y, B1.y), B2.y) + eps_s;
+    const bool cutL = tauL >= K.Kf * bmL, cutR = tauR >= K.Kf * bmR;
+    fL = fR = 7;
+    if (!(cutL || cutR)) return;
+    const float2 tau = make_float2(tauL, tauR), bm = make_float2(bmL, bmR);
+    const float2 e2 = bc2(eps_s), C2 = bc2(K.Cf);
+    const float2 b[3] = {add2(B0, e2), add2(B1, e2), add2(B2, e2)};
+    const float2 den = make_float2(__frcp_rn(fmaf(K.Cf, bmL, tauL)), __frcp_rn(fmaf(K.Cf, bmR, tauR)));
+    float2 sk[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float2 rb = make_float2(__frcp_rn(b[k].x), __frcp_rn(b[k].y));
+        float2 r = mul2(mul2(bm, rb), mul2(fma2(C2, b[k], tau), den));
+        r = make_float2(fminf(1.0f, r.x), fminf(1.0f, r.y));
+        float2 pw;
+        if (K.q == 6) {
+            const float2 r2 = mul2(r, r);
+            pw = mul2(mul2(r2, r2), r2);
+        } else {
+            pw = r;
+            for (int e = 1; e < K.q; ++e) pw = mul2(pw, r);
+        }
+        sk[k] = pw;
+    }
+    const float2 lim = mul2(bc2(K.CTf), add2(add2(sk[0], sk[1]), sk[2]));
+    int l = 0, rr = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (!(sk[k].x < lim.x)) l |= 1 << k;
+        if (!(sk[k].y < lim.y)) rr |= 1 << k;
+    }
+    if (cutL) fL = l;
+    if (cutR) fR = rr;
+}
+
 // Both biased selections and interpolations of one characteristic field,
 // paired: S0 = (w_{j-2}, w_{j+3}), S1 = (w_{j-1}, w_{j+2}), S2 = (w_j, w_{j+1})
 // are the left stencil's s0..s2 in .x and the mirrored right stencil's in
@@ -282,8 +326,7 @@ __device__ __forceinline__ float2 select_interp_x2(float2 S0, float2 S1, float2 
     const float2 B0 = fma2(D10, D10, mul2(D20, D20));   // Eq. 15
     const float2 B1 = fma2(D11, D11, mul2(D21, D21));
     const float2 B2 = fma2(D12, D12, mul2(D22, D22));
-    fL = cut_fp32(B0.x, B1.x, B2.x, eps_s, K);
-    fR = cut_fp32(B0.y, B1.y, B2.y, eps_s, K);
+    cut_x2(B0, B1, B2, eps_s, K, fL, fR);
     if ((fL & fR) == 7) {                                 // Eq. 7 on both sides
         float2 u = mul2(bc2(3.0f / 128), S0);
         u = fma2(bc2(-5.0f / 32), S1, u);
