@@ -409,6 +409,7 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) swee
     // fused stage combination (FP32 x sweep): prefetched base state and increment
     double* sU0 = reinterpret_cast<double*>(sL + (G::PREFETCH_L ? NV * TL * TS : 0));
     float* sD = reinterpret_cast<float*>(sU0 + (G::FUSE ? NV * TL * TS : 0));
+    float* sUf = reinterpret_cast<float*>(sU0);   // stage 2: float(U0) in the same space
 
     long long sd;
     int lcount;
@@ -504,7 +505,12 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) swee
                     const long long g = base0 + l * lstride + (long long)(pos0 + t) * sd;
 #pragma unroll
                     for (int v = 0; v < NV; ++v) {
-                        cp_async8(&sU0[sidx<DIR, TL, TS>(v, l, t)], U0b + v * N + g);
+                        // stage 1 needs float(U0) = its own staged input; stage 2 reads
+                        // float(U0) from the output buffer it then overwrites; stage 3
+                        // accumulates into the FP64 state
+                        if (a.fuse_stage == 3) cp_async8(&sU0[sidx<DIR, TL, TS>(v, l, t)], U0b + v * N + g);
+                        else if (a.fuse_stage == 2)
+                            cp_async4(&sUf[sidx<DIR, TL, TS>(v, l, t)], Sob + v * N + g);
                         if (a.fuse_stage > 1) cp_async4(&sD[sidx<DIR, TL, TS>(v, l, t)], Db + v * N + g);
                     }
                 }
@@ -628,18 +634,21 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) swee
                         if (a.fuse_stage) {
                             // SSP-RK3 stage on U = U0 + D (FP64 base, FP32 increment):
                             //   D1 = dt L;  D2 = (D1 + dt L)/4;  U0 += 2/3 (D2 + dt L)
+                            // The next stage's input is float(U0) + D; float(U0) is
+                            // this stage's staged input in stage 1 and the prefetched
+                            // output buffer in stage 2 (the step starts from float(U0)).
                             const float dt = (float)*dtp;
-                            const double u0 = sU0[sidx<DIR, TL, TS>(v, l, t)];
                             const long long gi = v * N + g;
                             if (a.fuse_stage == 1) {
                                 const float dd = dt * lv;
                                 Db[gi] = dd;
-                                Sob[gi] = __double2float_rn(u0) + dd;
+                                Sob[gi] = sS[sidx<DIR, TL, P>(v, l, t + GHOST)] + dd;
                             } else if (a.fuse_stage == 2) {
                                 const float dd = 0.25f * fmaf(dt, lv, sD[sidx<DIR, TL, TS>(v, l, t)]);
                                 Db[gi] = dd;
-                                Sob[gi] = __double2float_rn(u0) + dd;
+                                Sob[gi] = sUf[sidx<DIR, TL, TS>(v, l, t)] + dd;
                             } else {
+                                const double u0 = sU0[sidx<DIR, TL, TS>(v, l, t)];
                                 const float dd = (2.0f / 3.0f) * fmaf(dt, lv, sD[sidx<DIR, TL, TS>(v, l, t)]);
                                 const double un = u0 + (double)dd;
                                 U0b[gi] = un;
