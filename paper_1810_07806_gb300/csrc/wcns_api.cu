@@ -269,7 +269,9 @@ wcns_status wcns_rhs(wcns_handle* h, const void* U, void* L, uint8_t* flags, voi
 
 // The three stages of one step after dt has been placed in h->sc.  In FP32
 // mode the first stage reads float(U), converted here.
-static cudaError_t run_stages(wcns_handle* h, double* U, cudaStream_t s)
+// converted: the FP32 first-stage input float(U) is already in place (the
+// time-step pass wrote it).
+static cudaError_t run_stages(wcns_handle* h, double* U, cudaStream_t s, bool converted = false)
 {
     const long long M = (long long)h->nv * h->N;
     const double* dtp = &h->sc->dt;
@@ -289,7 +291,7 @@ static cudaError_t run_stages(wcns_handle* h, double* U, cudaStream_t s)
     float* A = (float*)h->U1;
     float* B = h->S2;
     float* L = (float*)h->L;
-    if ((e = launch_to_fp32(U, A, M, h->sc, s)) != cudaSuccess) return e;
+    if (!converted && (e = launch_to_fp32(U, A, M, h->sc, s)) != cudaSuccess) return e;
     if ((e = run_rhs(h, A, L, nullptr, dtp, s, 1, U, B)) != cudaSuccess) return e;
     if ((e = run_rhs(h, B, L, nullptr, dtp, s, 2, U, A)) != cudaSuccess) return e;
     return run_rhs(h, A, L, nullptr, dtp, s, 3, U, B);
@@ -300,8 +302,8 @@ static cudaError_t run_stages(wcns_handle* h, double* U, cudaStream_t s)
 // for the FP32 path.
 static cudaError_t step_cfl(wcns_handle* h, const double* U, int clip, cudaStream_t s)
 {
-    if (h->p.precision == WCNS_FP32)
-        return launch_cfl_fast(h->ndim, U, h->N, h->h, h->gamma, h->p.cfl, clip, h->sc, s);
+    if (h->p.precision == WCNS_FP32)   // also writes float(U), the first stage's input
+        return launch_cfl_fast(h->ndim, U, h->N, h->h, h->gamma, h->p.cfl, clip, h->sc, s, (float*)h->U1);
     return launch_cfl(h->ndim, U, h->N, h->h, h->gamma, h->p.cfl, clip, h->sc, s);
 }
 
@@ -319,7 +321,7 @@ wcns_status wcns_step_rk3(wcns_handle* h, void* U, double dt, double* dt_used, v
     CK(reset_clock(h, INFINITY, s), "reset clock");
     if (dt > 0.0) CK(launch_set_dt(dt, 0, h->sc, s), "set dt");
     else CK(step_cfl(h, (const double*)U, 0, s), "cfl");
-    CK(run_stages(h, (double*)U, s), "rk3 stages");
+    CK(run_stages(h, (double*)U, s, !(dt > 0.0)), "rk3 stages");
     if (dt_used) {
         CK(cudaMemcpyAsync(dt_used, &h->sc->dt, sizeof(double), cudaMemcpyDeviceToHost, s), "dt copy");
         CK(cudaStreamSynchronize(s), "sync");
@@ -344,7 +346,7 @@ wcns_status wcns_advance(wcns_handle* h, void* U, double t_end, int max_steps, i
         const int batch = left < check ? (int)left : check;
         for (int k = 0; k < batch; ++k) {
             CK(step_cfl(h, (const double*)U, 1, s), "cfl");
-            CK(run_stages(h, (double*)U, s), "rk3 stages");
+            CK(run_stages(h, (double*)U, s, true), "rk3 stages");
         }
         issued += batch;
         CK(cudaMemcpyAsync(&cur, h->sc, sizeof cur, cudaMemcpyDeviceToHost, s), "clock copy");
@@ -422,9 +424,11 @@ int wcns_launches_per_step(const wcns_handle* h, int cfl_step)
 {
     if (!h) return 0;
     // clock reset + (CFL reduction and finalize | set dt) + stages: FP64 3 x
-    // (sweeps + stage combine); FP32 one state conversion + 3 x sweeps (the
-    // last sweep of each stage applies the combination)
-    const int stages = h->p.precision == WCNS_FP32 ? 1 + 3 * h->ndim : 3 * (h->ndim + 1);
+    // (sweeps + stage combine); FP32 3 x sweeps (the last sweep of each stage
+    // applies the combination) plus a state conversion when dt is given (the
+    // CFL pass converts the state otherwise)
+    const int stages =
+        h->p.precision == WCNS_FP32 ? (cfl_step ? 0 : 1) + 3 * h->ndim : 3 * (h->ndim + 1);
     return 1 + (cfl_step ? 2 : 1) + stages;
 }
 

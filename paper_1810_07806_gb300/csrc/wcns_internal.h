@@ -184,9 +184,10 @@ struct StepScalars {      // device-resident
 
 cudaError_t launch_cfl(int nd, const double* U, long long N, const double* h, double gamma,
                        double cfl, int clip, StepScalars* sc, cudaStream_t s);
-// FP32-path variant: per-node speeds in FP32 (rounded upward), FP64 max and dt.
+// FP32-path variant: per-node speeds in FP32 (rounded upward), FP64 max and
+// dt; S (nullable) receives float(U) from the same pass.
 cudaError_t launch_cfl_fast(int nd, const double* U, long long N, const double* h, double gamma,
-                            double cfl, int clip, StepScalars* sc, cudaStream_t s);
+                            double cfl, int clip, StepScalars* sc, cudaStream_t s, float* S = nullptr);
 cudaError_t launch_set_dt(double dt, int clip, StepScalars* sc, cudaStream_t s);
 cudaError_t launch_reset_clock(double t_end, StepScalars* sc, cudaStream_t s);
 // FP64 stage combinations (Shu-Osher SSP-RK3) over M = nv*N values.

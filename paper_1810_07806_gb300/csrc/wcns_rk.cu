@@ -66,10 +66,11 @@ __global__ void __launch_bounds__(256) cfl_reduce_kernel(const double* __restric
 // in FP32 from the FP64 state and multiplied by (1 + 2^-16), an upper bound of
 // its rounding error, so the step never exceeds the FP64 CFL bound; the
 // maximum and dt stay FP64.  One pass over the state, no FP64 divisions.
+// S (nullable) receives float(U), the first stage's input, from the same pass.
 template <int ND>
 __global__ void __launch_bounds__(256) cfl_reduce_fast_kernel(const double* __restrict__ U, long long N,
                                                               InvH hh, float gamma, StepScalars* sc,
-                                                              int clip)
+                                                              int clip, float* __restrict__ S)
 {
     if (clip && !(sc->t < sc->t_end)) return;
     float m = 0.f;
@@ -83,13 +84,22 @@ __global__ void __launch_bounds__(256) cfl_reduce_fast_kernel(const double* __re
         const float ir = __frcp_rn(rho);
         float m2 = 0.f, s = 0.f, c = 0.f;
         float vel[ND];
+        float mvs[ND];
 #pragma unroll
         for (int a = 0; a < ND; ++a) {
             const float mv = (float)U[(1 + a) * N + i];
+            mvs[a] = mv;
             m2 = fmaf(mv, mv, m2);
             vel[a] = fabsf(mv) * ir;
         }
-        const float p = gm1 * ((float)U[(ND + 1) * N + i] - 0.5f * m2 * ir);
+        const float E = (float)U[(ND + 1) * N + i];
+        if (S != nullptr) {
+            S[i] = rho;
+#pragma unroll
+            for (int a = 0; a < ND; ++a) S[(1 + a) * N + i] = mvs[a];
+            S[(ND + 1) * N + i] = E;
+        }
+        const float p = gm1 * (E - 0.5f * m2 * ir);
         c = sqrtf(gamma * p * ir);
 #pragma unroll
         for (int a = 0; a < ND; ++a) s = fmaf(vel[a] + c, ih[a], s);
@@ -167,13 +177,13 @@ cudaError_t launch_cfl(int nd, const double* U, long long N, const double* h, do
 }
 
 cudaError_t launch_cfl_fast(int nd, const double* U, long long N, const double* h, double gamma,
-                            double cfl, int clip, StepScalars* sc, cudaStream_t s)
+                            double cfl, int clip, StepScalars* sc, cudaStream_t s, float* S)
 {
     InvH hh{{h[0], h[1], h[2]}};
     const int nb = reduce_blocks(N);
-    if (nd == 1) cfl_reduce_fast_kernel<1><<<nb, 256, 0, s>>>(U, N, hh, (float)gamma, sc, clip);
-    else if (nd == 2) cfl_reduce_fast_kernel<2><<<nb, 256, 0, s>>>(U, N, hh, (float)gamma, sc, clip);
-    else cfl_reduce_fast_kernel<3><<<nb, 256, 0, s>>>(U, N, hh, (float)gamma, sc, clip);
+    if (nd == 1) cfl_reduce_fast_kernel<1><<<nb, 256, 0, s>>>(U, N, hh, (float)gamma, sc, clip, S);
+    else if (nd == 2) cfl_reduce_fast_kernel<2><<<nb, 256, 0, s>>>(U, N, hh, (float)gamma, sc, clip, S);
+    else cfl_reduce_fast_kernel<3><<<nb, 256, 0, s>>>(U, N, hh, (float)gamma, sc, clip, S);
     cfl_finalize_kernel<<<1, 1, 0, s>>>(sc, cfl, clip);
     return cudaGetLastError();
 }
