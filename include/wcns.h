@@ -143,14 +143,18 @@ size_t wcns_flags_bytes(const wcns_handle* h);
  * combination).  dt > 0 uses that step; dt <= 0 computes
  * dt = cfl / max_i sum_d (|u_d| + c)/h_d in FP64 on the device.  If dt_used
  * is non-NULL the call copies the step to the host and synchronises the
- * stream; otherwise nothing is synchronised. */
+ * stream; otherwise nothing is synchronised.  With dt <= 0 (and profiling
+ * off) the step's launches are captured once per state pointer U as a CUDA
+ * graph on an internal stream and replayed on `stream` afterwards; passing
+ * another U, or changing the tile configuration, captures again. */
 wcns_status wcns_step_rk3(wcns_handle* h, void* U, double dt, double* dt_used, void* stream);
 
 /* Advance U (FP64 device state) from t = 0 to t_end with CFL steps, the
  * last one clipped to land on t_end, or until max_steps.  The time and step
  * size stay on the device; the host loop checks completion every `check`
  * steps (one small device-to-host read).  Writes the reached time and the
- * number of steps.  Synchronises the stream before returning. */
+ * number of steps.  Synchronises the stream before returning.  Each step
+ * replays a captured CUDA graph (per state pointer, as for wcns_step_rk3). */
 wcns_status wcns_advance(wcns_handle* h, void* U, double t_end, int max_steps, int check,
                          double* t_out, int* steps_out, void* stream);
 

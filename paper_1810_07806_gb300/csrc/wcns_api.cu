@@ -36,6 +36,12 @@ struct wcns_handle {
     size_t bytes = 0;
     // tile configuration of each direction's FP32 sweep (set by wcns_autotune)
     int tile_cfg[3] = {0, 0, 0};
+    // one RK3 step with the CFL rule as a CUDA graph, per state pointer:
+    // [0] clock reset + step (wcns_step_rk3), [1] clipped step (wcns_advance);
+    // captured on an internal stream, replayed on the caller's
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    const void* graph_U[2] = {nullptr, nullptr};
     // optional sweep timing
     bool profiling = false;
     std::vector<cudaEvent_t> ev;    // pairs (start, end)
@@ -168,9 +174,20 @@ wcns_status wcns_create(const wcns_grid* g, double gamma, const wcns_scheme_para
     return WCNS_OK;
 }
 
+static void drop_graphs(wcns_handle* h)
+{
+    for (int k = 0; k < 2; ++k) {
+        if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
+        h->graph[k] = nullptr;
+        h->graph_U[k] = nullptr;
+    }
+}
+
 wcns_status wcns_destroy(wcns_handle* h)
 {
     if (!h) return WCNS_OK;
+    drop_graphs(h);
+    if (h->cap) cudaStreamDestroy(h->cap);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     cudaError_t e = cudaFree(h->L);
     delete h;
@@ -312,16 +329,54 @@ static cudaError_t reset_clock(wcns_handle* h, double t_end, cudaStream_t s)
     return launch_reset_clock(t_end, h->sc, s);
 }
 
+// The graph of one CFL step on state U (kind 0: with the clock reset of
+// wcns_step_rk3; kind 1: the clipped step of wcns_advance), captured on
+// first use for this U.  Returns false (and leaves no error pending) when
+// capture is not possible; the caller then launches directly.
+static bool step_graph(wcns_handle* h, int kind, void* U)
+{
+    if (h->graph[kind] && h->graph_U[kind] == U) return true;
+    if (h->graph[kind]) cudaGraphExecDestroy(h->graph[kind]);
+    h->graph[kind] = nullptr;
+    h->graph_U[kind] = nullptr;
+    if (!h->cap && cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaError_t e = kind == 0 ? reset_clock(h, INFINITY, h->cap) : cudaSuccess;
+    if (e == cudaSuccess) e = step_cfl(h, (const double*)U, kind, h->cap);
+    if (e == cudaSuccess) e = run_stages(h, (double*)U, h->cap, true);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
+    if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&h->graph[kind], g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        h->graph[kind] = nullptr;
+        cudaGetLastError();
+        return false;
+    }
+    h->graph_U[kind] = U;
+    return true;
+}
+
 wcns_status wcns_step_rk3(wcns_handle* h, void* U, double dt, double* dt_used, void* stream)
 {
     g_err.clear();
     if (!h || !U) return fail(WCNS_ERR_INVALID, "wcns_step_rk3: null argument");
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaGetLastError(), "pending CUDA error");
-    CK(reset_clock(h, INFINITY, s), "reset clock");
-    if (dt > 0.0) CK(launch_set_dt(dt, 0, h->sc, s), "set dt");
-    else CK(step_cfl(h, (const double*)U, 0, s), "cfl");
-    CK(run_stages(h, (double*)U, s, !(dt > 0.0)), "rk3 stages");
+    if (!(dt > 0.0) && !h->profiling && step_graph(h, 0, U)) {
+        CK(cudaGraphLaunch(h->graph[0], s), "step graph");
+    } else {
+        CK(reset_clock(h, INFINITY, s), "reset clock");
+        if (dt > 0.0) CK(launch_set_dt(dt, 0, h->sc, s), "set dt");
+        else CK(step_cfl(h, (const double*)U, 0, s), "cfl");
+        CK(run_stages(h, (double*)U, s, !(dt > 0.0)), "rk3 stages");
+    }
     if (dt_used) {
         CK(cudaMemcpyAsync(dt_used, &h->sc->dt, sizeof(double), cudaMemcpyDeviceToHost, s), "dt copy");
         CK(cudaStreamSynchronize(s), "sync");
@@ -344,9 +399,14 @@ wcns_status wcns_advance(wcns_handle* h, void* U, double t_end, int max_steps, i
     while (issued < max_steps) {
         const long long left = max_steps - issued;
         const int batch = left < check ? (int)left : check;
+        const bool use_graph = !h->profiling && step_graph(h, 1, U);
         for (int k = 0; k < batch; ++k) {
-            CK(step_cfl(h, (const double*)U, 1, s), "cfl");
-            CK(run_stages(h, (double*)U, s, true), "rk3 stages");
+            if (use_graph) {
+                CK(cudaGraphLaunch(h->graph[1], s), "step graph");
+            } else {
+                CK(step_cfl(h, (const double*)U, 1, s), "cfl");
+                CK(run_stages(h, (double*)U, s, true), "rk3 stages");
+            }
         }
         issued += batch;
         CK(cudaMemcpyAsync(&cur, h->sc, sizeof cur, cudaMemcpyDeviceToHost, s), "clock copy");
@@ -449,6 +509,7 @@ extern "C" wcns_status wcns_autotune(wcns_handle* h, const void* U, int* chosen,
     set_last_error(nullptr);
     if (!h || !U) return fail(WCNS_ERR_INVALID, "wcns_autotune: null argument");
     cudaStream_t s = (cudaStream_t)stream;
+    drop_graphs(h);   // captured steps hold the old tile shapes
     // the comparison weights have one tile configuration; TENO has three
     if (h->p.precision == WCNS_FP32 && h->ndim >= 2 && h->p.weights == WCNS_W_TENO) {
         const long long M = (long long)h->nv * h->N;
@@ -507,6 +568,7 @@ extern "C" wcns_status wcns_tile_config(wcns_handle* h, const int* set, int* get
             if (set[d] < 0 || set[d] > 2) return fail(WCNS_ERR_INVALID, "tile configuration must be 0, 1 or 2");
         if (h->p.precision == WCNS_FP32 && h->ndim >= 2)
             for (int d = 0; d < h->ndim; ++d) h->tile_cfg[d] = set[d];
+        drop_graphs(h);   // captured steps hold the old tile shapes
     }
     if (get)
         for (int d = 0; d < 3; ++d) get[d] = d < h->ndim ? h->tile_cfg[d] : 0;
