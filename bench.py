@@ -199,15 +199,32 @@ def cpu_oracle_rate(pb, budget_s=12.0):
 
 
 # ---------------------------------------------------------------- main arms
-def dist_setup():
+def dist_setup(backend="nccl"):
     import torch
     import torch.distributed as dist
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
-        dist.init_process_group("nccl", init_method="env://")
+        dist.init_process_group(backend, init_method="env://")
     return world, rank, local
+
+
+def max_over_ranks(seconds, world, device):
+    """The slowest rank's time (every rank gets it): the replicas are
+    independent, so this timing reduction is the only collective."""
+    import torch
+    t = torch.tensor([float(seconds)], device=device, dtype=torch.float64)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(cells_per_rank, evals, world, seconds):
+    """Cell-updates per second of all ranks together (weak scaling: every
+    rank advances its own replica of the same size)."""
+    return cells_per_rank * evals * world / seconds
 
 
 def reference_arm(args, world, rank):
@@ -300,12 +317,9 @@ def ours_arm(args, world, rank, local):
     solver.profile(False)
     clk = clocks.stop()
 
-    t = torch.tensor([el], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    el = float(t.item())
+    el = max_over_ranks(el, world, dev)
     evals = 3 * args.steps
-    value = nodes * evals * world / el
+    value = whole_job_rate(nodes, evals, world, el)
 
     # dominant kernel: the fused sweep (all directions)
     nd = pb.ndim
@@ -338,12 +352,9 @@ def ours_arm(args, world, rank, local):
     ev1.record()
     torch.cuda.synchronize()
     e2e_el = ev0.elapsed_time(ev1) / 1e3
-    et = torch.tensor([e2e_el], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(et, op=dist.ReduceOp.MAX)
-    e2e_el = float(et.item())
+    e2e_el = max_over_ranks(e2e_el, world, dev)
     nbytes = U.numel() * U.element_size()
-    e2e = {"value": nodes * 3 * e2e_steps * world / e2e_el, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+    e2e = {"value": whole_job_rate(nodes, 3 * e2e_steps, world, e2e_el), "unit": UNIT, "h2d_bytes_per_step": nbytes,
            "d2h_bytes_per_step": nbytes, "steps": e2e_steps}
 
     # the FP64 plain path on the same workload
