@@ -140,3 +140,28 @@ def test_batches_and_server_reject_single_grid_features():
     with pytest.raises(wcns.WcnsError):
         b.add(pb, t_end=0.1)
     b.close()
+
+
+def test_full_size_rayleigh_taylor_rhs_sampled_against_oracle():
+    """The paper's finer grid (256 x 1024) in the benchmark's launch
+    configuration: sampled nodes (with the walls, the fixed ends and the
+    interface) are bit-identical to the oracle's pointwise RHS, which applies
+    the same boundary rules and source."""
+    pb = inputs.rayleigh_taylor(256)
+    s = wcns.Solver.for_problem(pb)
+    Ud = torch.from_numpy(pb.U0).to(DEV)
+    for _ in range(2):
+        s.step(Ud)
+    U = Ud.cpu().numpy()
+    Ld = torch.empty_like(Ud)
+    s.rhs(Ud, Ld)
+    Lg = Ld.cpu().numpy().reshape(pb.nv, -1)
+    nx, ny = pb.n
+    rng = np.random.default_rng(11)
+    idx = rng.choice(pb.cells, 3000, replace=False)
+    rows = [0, 1, 2, ny // 2 - 1, ny // 2, ny - 3, ny - 2, ny - 1]
+    cols = [0, 1, 2, nx // 2, nx - 3, nx - 2, nx - 1]
+    extra = [j * nx + i for j in rows for i in cols]
+    idx = np.unique(np.concatenate([idx, extra]))
+    Lo = O.euler_rhs_at(ora_cfg(pb), U, idx)
+    assert np.array_equal(Lg[:, idx], Lo)

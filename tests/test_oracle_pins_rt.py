@@ -139,3 +139,17 @@ def test_fixed_state_ghosts_are_the_given_state():
     cfgp = O.make_cfg(ndim=1, n=(n + 20,), h=(0.1,))
     Lp = O.euler_rhs(cfgp, P)[0][:, 10:10 + n]
     assert np.array_equal(L, Lp)
+
+
+@pytest.mark.parametrize("diff", [O.DIFF_MD, O.DIFF_HWCNS, O.DIFF_MND])
+def test_pointwise_rhs_equals_full_rhs_with_boundaries_and_source(diff):
+    """The oracle's pointwise RHS (used for sampled parity at full size)
+    applies the same boundary rules, differences and source as the full
+    RHS: equal at every node."""
+    pb = inputs.rayleigh_taylor(16)
+    cfg = ora_cfg(pb, diff=diff)
+    U = pb.U0.copy()
+    O.rk3_step(cfg, U, 2e-3)
+    L = O.euler_rhs(cfg, U)[0].reshape(pb.nv, -1)
+    La = O.euler_rhs_at(cfg, U, np.arange(pb.cells))
+    assert np.array_equal(La, L)
