@@ -303,15 +303,15 @@ static cudaError_t run_stages(wcns_handle* h, double* U, cudaStream_t s, bool co
         if ((e = run_rhs(h, U1, L, nullptr, dtp, s)) != cudaSuccess) return e;
         return launch_rk_fp64(3, U, U1, L, M, h->sc, s);
     }
-    // FP32: stage inputs alternate A -> B -> A; the x sweep of each stage
-    // writes the next one (and, in stage 3, the FP64 state)
+    // FP32: stage inputs A -> B -> A; the x sweep of stages 1 and 2 writes
+    // the next one, stage 3 the FP64 state (the next step converts A anew)
     float* A = (float*)h->U1;
     float* B = h->S2;
     float* L = (float*)h->L;
     if (!converted && (e = launch_to_fp32(U, A, M, h->sc, s)) != cudaSuccess) return e;
     if ((e = run_rhs(h, A, L, nullptr, dtp, s, 1, U, B)) != cudaSuccess) return e;
     if ((e = run_rhs(h, B, L, nullptr, dtp, s, 2, U, A)) != cudaSuccess) return e;
-    return run_rhs(h, A, L, nullptr, dtp, s, 3, U, B);
+    return run_rhs(h, A, L, nullptr, dtp, s, 3, U, nullptr);
 }
 
 // The time step of a step: the fixed-order FP64 rule for the FP64 path (bit

@@ -402,14 +402,15 @@ cudaError_t step_sequence(wcns_batch* b, cudaStream_t s)
         batch_rk_fp64_kernel<3><<<b->nech, 256, 0, s>>>(b->U, U1, L, b->d_ech, b->sc);
     } else {
         // stage inputs A -> B -> A; the x sweep of each stage applies the
-        // stage combination (stage 3 also updates the FP64 state)
+        // stage combination (stage 3 updates the FP64 state, from which the
+        // next step converts A again)
         float* A = (float*)b->S;
         float* B = b->S2;
         float* L = (float*)b->L;
         batch_to_fp32_kernel<<<b->nech, 256, 0, s>>>(b->U, A, b->d_ech, b->sc);
         if ((e = sweeps(b, A, L, s, 1, B)) != cudaSuccess) return e;
         if ((e = sweeps(b, B, L, s, 2, A)) != cudaSuccess) return e;
-        if ((e = sweeps(b, A, L, s, 3, B)) != cudaSuccess) return e;
+        if ((e = sweeps(b, A, L, s, 3, nullptr)) != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }

@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) swee
         if (a.fuse_stage) {
             U0b += I.off;
             Db += I.off;
-            Sob += I.off;
+            if (Sob != nullptr) Sob += I.off;   // stages 1 and 2 only
         }
         N = I.N;
         nx = I.n[0];
@@ -648,11 +648,11 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) swee
                                 Db[gi] = dd;
                                 Sob[gi] = sUf[sidx<DIR, TL, TS>(v, l, t)] + dd;
                             } else {
+                                // the next step's first input float(U) comes from its
+                                // time-step pass, so stage 3 writes the FP64 state only
                                 const double u0 = sU0[sidx<DIR, TL, TS>(v, l, t)];
                                 const float dd = (2.0f / 3.0f) * fmaf(dt, lv, sD[sidx<DIR, TL, TS>(v, l, t)]);
-                                const double un = u0 + (double)dd;
-                                U0b[gi] = un;
-                                Sob[gi] = __double2float_rn(un);
+                                U0b[gi] = u0 + (double)dd;
                             }
                             continue;
                         }
