@@ -64,6 +64,8 @@ struct SchemeConst {
     int diff;            // DIFF_MD | DIFF_HWCNS | DIFF_MND
     float sqrt_eps_jsf;  // sqrt(eps of Eq. 14) in float, for the FP32 rescaled JS eps
     double keep_all_K;   // tau < K * (min beta + eps) guarantees no cut (exact test)
+    double screen_lo;    // (C_T (1 - 1e-9))^(1/q) (1 - 1e-9): g_k / g_max below it cuts
+    double screen_hi;    // (3 C_T (1 + 1e-9))^(1/q) (1 + 1e-9): at or above it keeps
     float Cf, CTf, Kf;
     float gammaf, gm1f;  // gamma, gamma - 1 in float
 };

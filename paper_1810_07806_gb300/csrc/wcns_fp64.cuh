@@ -131,6 +131,28 @@ __device__ __forceinline__ int select_fp64(const double s[5], const SchemeConst&
     // stencils skip the divisions while deciding exactly as the full test.
     const double bmin = fmin(fmin(beta[0], beta[1]), beta[2]) + K.eps;
     if (tau < K.keep_all_K * bmin) return 7;
+    // Division-free screen.  With b_k = beta_k + eps and b_m the smallest,
+    // r_k = g_k / g_max = (C b_k + tau) b_m / (b_k (C b_m + tau)), and since
+    // 1 <= sum_j r_j^q <= 3, r_k^q < C_T (1 - 1e-9) cuts stencil k and
+    // r_k^q >= 3 C_T (1 + 1e-9) keeps it, whatever the other stencils.  The
+    // 1e-9 margins dwarf the rounding of both this test and the exact form
+    // below (a few ulps), so a decision taken here is the one the exact form
+    // takes; a stencil inside the band, or a product out of range, goes to
+    // the exact form.
+    {
+        const double cb = K.C * bmin + tau;
+        int screened = 7;
+        bool open = false;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const double bk = beta[k] + K.eps;
+            const double x = (K.C * bk + tau) * bmin, y = bk * cb;
+            if (!(isfinite(x) && isfinite(y))) open = true;
+            else if (x < K.screen_lo * y) screened &= ~(1 << k);
+            else if (!(x >= K.screen_hi * y)) open = true;
+        }
+        if (!open) return screened;
+    }
     double g[3], gmax = 0.0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {

@@ -135,6 +135,8 @@ inline SchemeConst make_scheme_const(const wcns_scheme_params* p, double gamma)
     // max g / min g <= 1 + tau / (C (min beta + eps)), tau below
     // 0.98 (ratio - 1) C (min beta + eps) keeps all three.
     K.keep_all_K = 0.98 * (pow(3.0 * p->CT, -1.0 / p->q) - 1.0) * p->C;
+    K.screen_lo = pow(p->CT * (1.0 - 1e-9), 1.0 / p->q) * (1.0 - 1e-9);
+    K.screen_hi = pow(3.0 * p->CT * (1.0 + 1e-9), 1.0 / p->q) * (1.0 + 1e-9);
     K.Cf = (float)p->C;
     K.CTf = (float)p->CT;
     K.Kf = (float)K.keep_all_K;

@@ -230,3 +230,49 @@ def test_sod_end_state_with_other_weights_matches_oracle(name):
     t_g, steps_g = s.advance(Ud, 0.2, check_every=16)
     assert t_g == t_o and steps_g == steps_o
     assert np.array_equal(Ud.cpu().numpy(), Uo)
+
+
+def _stencils_at_the_cutoff(cfg, count, seed):
+    """Stencils whose TENO decision (Eq. 18) sits at, and at relative
+    distances 1e-15 .. 1e-3 on either side of, the point where a flag flips:
+    a smooth stencil plus a jump of amplitude alpha, alpha bisected to the
+    flip."""
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < count * 13:
+        base = np.polyval(rng.normal(size=3), np.arange(5) - 2.0)
+        jump = np.where(np.arange(5) >= rng.integers(1, 5), 1.0, 0.0)
+        f = lambda al: O.teno_chi(cfg, base + al * jump)[0]
+        lo, hi = 0.0, 10.0 ** rng.uniform(-3, 3)
+        if f(lo) == f(hi):
+            continue
+        for _ in range(80):
+            mid = 0.5 * (lo + hi)
+            if f(mid) == f(lo):
+                lo = mid
+            else:
+                hi = mid
+        for e in (0.0, 1e-15, -1e-15, 1e-12, -1e-12, 1e-10, -1e-10, 1e-8, -1e-8, 1e-6, -1e-6, 1e-3, -1e-3):
+            out.append(base + hi * (1 + e) * jump)
+    return out
+
+
+@pytest.mark.parametrize("name", ["tcns"])
+def test_cutoff_decisions_at_the_threshold_bit_identical(name):
+    """The FP64 path decides most stencils with a division-free screen and
+    sends those within a thin band around the cutoff to the exact form; both
+    must give the oracle's flags and values bit for bit, right at the
+    threshold and on either side of it."""
+    wg, wo = WEIGHTS[name]
+    cfg = O.make_cfg(weights=wo)
+    st = _stencils_at_the_cutoff(cfg, 60, 5)
+    # each stencil is the left-biased stencil of the face at its centre
+    u = np.concatenate(st)
+    n = u.size
+    h = 1.0 / n
+    for kind in (wcns.SCALAR_ADVECTION, wcns.SCALAR_BURGERS):
+        Lg = _gpu_rhs(kind, u, h, wg)
+        assert np.array_equal(Lg, O.scalar_rhs(cfg, kind, u, h))
+    # the set reaches every outcome: stencils cut and kept near the flip
+    flags = {O.teno_chi(cfg, s)[0] for s in st}
+    assert len(flags) >= 3
