@@ -278,7 +278,11 @@ typedef struct {
     size_t hbm_budget_bytes;      /* device memory the server may reserve      */
     int max_instances_per_class;  /* slots of each class's batch               */
     long long max_nodes_per_class;/* arena cap per class (0: budget share)     */
-    int steps_per_tick;           /* RK3 steps between admission/retirement    */
+    int steps_per_tick;           /* RK3 steps of the most expensive class per
+                                     tick (admission and retirement happen
+                                     between ticks); cheaper classes take as
+                                     many more steps as fit in the same GPU
+                                     time, at most 64 times as many           */
 } wcns_server_config;
 
 typedef struct {

@@ -15,6 +15,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -55,7 +56,14 @@ struct ClassBatch {
     wcns_batch* b = nullptr;
     size_t bytes = 0;
     std::map<int, Running> running;   // slot -> request
+    // GPU time of one RK3 step of the class (smoothed), from events around
+    // its steps in the last tick
+    double ms_per_step = 0.0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int stepped = 0;                  // steps issued in the current tick
 };
+
+constexpr int kMaxTickScale = 64;     // a cheap class takes at most 64x the base steps
 
 ClassKey key_of(const wcns_request& r)
 {
@@ -271,20 +279,47 @@ void worker_main(wcns_server* sv)
             sv->max_queue = std::max<int>(sv->max_queue, (int)sv->pending.size());
         }
         admit(sv);
+        // Time-fair ticks: the most expensive class advances steps_per_tick
+        // steps, a cheaper class as many more as fit in the same GPU time (at
+        // most kMaxTickScale times as many), so cheap requests are not held
+        // to the step rate of expensive ones.  Results do not depend on how
+        // the steps are grouped.
+        double slowest = 0.0;
+        for (auto& kv : sv->classes)
+            if (!kv.second.running.empty()) slowest = std::max(slowest, kv.second.ms_per_step);
         int running = 0;
         for (auto& kv : sv->classes) {
             ClassBatch& cb = kv.second;
+            cb.stepped = 0;
             if (cb.running.empty()) continue;
             running += (int)cb.running.size();
-            if (wcns_batch_step(cb.b, sv->cfg.steps_per_tick, nullptr, sv->stream) != WCNS_OK) {
-                sv->worker_status = WCNS_ERR_CUDA;
+            const int base = sv->cfg.steps_per_tick;
+            int n = base;
+            if (cb.ms_per_step > 0.0 && slowest > 0.0) {
+                const double want = base * slowest / cb.ms_per_step;
+                n = (int)std::min<double>(std::max<double>(want, base), (double)base * kMaxTickScale);
             }
+            if (!cb.ev0 && (cudaEventCreate(&cb.ev0) != cudaSuccess || cudaEventCreate(&cb.ev1) != cudaSuccess))
+                sv->worker_status = WCNS_ERR_CUDA;
+            if (cb.ev0) cudaEventRecord(cb.ev0, sv->stream);
+            if (wcns_batch_step(cb.b, n, nullptr, sv->stream) != WCNS_OK) sv->worker_status = WCNS_ERR_CUDA;
+            if (cb.ev1) cudaEventRecord(cb.ev1, sv->stream);
+            cb.stepped = n;
+            sv->steps += n;
         }
         sv->max_running = std::max(sv->max_running, running);
         if (running) {
             ++sv->ticks;
-            sv->steps += sv->cfg.steps_per_tick;
             retire(sv);
+            for (auto& kv : sv->classes) {
+                ClassBatch& cb = kv.second;
+                float ms = 0.f;
+                if (cb.stepped > 0 && cb.ev1 && cudaEventSynchronize(cb.ev1) == cudaSuccess &&
+                    cudaEventElapsedTime(&ms, cb.ev0, cb.ev1) == cudaSuccess) {
+                    const double per = ms / cb.stepped;
+                    cb.ms_per_step = cb.ms_per_step > 0.0 ? 0.5 * (cb.ms_per_step + per) : per;
+                }
+            }
         }
         if (sv->worker_status != WCNS_OK) break;
     }
@@ -339,6 +374,17 @@ wcns_status wcns_batch_submit(wcns_server* sv, const wcns_request* req, uint64_t
     for (int a = 0; a < g.ndim; ++a)
         if (g.n[a] < 1) return sfail(WCNS_ERR_INVALID, "bad node count");
     if (!(req->t_end >= 0.0)) return sfail(WCNS_ERR_INVALID, "t_end must be >= 0");
+    if (!(req->gamma > 1.0)) return sfail(WCNS_ERR_INVALID, "gamma must exceed 1");
+    if (const char* why = scheme_params_error(&req->params)) return sfail(WCNS_ERR_INVALID, "%s", why);
+    if (req->params.precision == WCNS_FP32 && req->params.weights != WCNS_W_TENO)
+        return sfail(WCNS_ERR_INVALID, "served FP32 requests take TENO weights only");
+    if (grid_has_single_grid_features(&g))
+        return sfail(WCNS_ERR_INVALID,
+                     "served requests take periodic and transmissive boundaries without a body force");
+    for (int a = 0; a < g.ndim; ++a)
+        for (int sd = 0; sd < 2; ++sd)
+            if (g.bc[a][sd] != WCNS_BC_PERIODIC && g.bc[a][sd] != WCNS_BC_TRANSMISSIVE)
+                return sfail(WCNS_ERR_INVALID, "unknown boundary kind");
     Pending p;
     p.req = *req;
     const long long N = nodes_of(g);
@@ -405,7 +451,11 @@ wcns_status wcns_server_destroy(wcns_server* sv)
     }
     sv->cv_work.notify_all();
     if (sv->worker.joinable()) sv->worker.join();
-    for (auto& kv : sv->classes) wcns_batch_destroy(kv.second.b);
+    for (auto& kv : sv->classes) {
+        wcns_batch_destroy(kv.second.b);
+        if (kv.second.ev0) cudaEventDestroy(kv.second.ev0);
+        if (kv.second.ev1) cudaEventDestroy(kv.second.ev1);
+    }
     for (auto& r : sv->done) wcns_result_free(&r);
     if (sv->stream) cudaStreamDestroy(sv->stream);
     delete sv;

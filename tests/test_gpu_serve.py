@@ -101,3 +101,21 @@ def test_request_larger_than_the_budget_is_rejected():
     got = _drain(sv, 1, timeout_s=30)
     assert got[7]["status"] == wcns.ERR_NOMEM and got[7]["U"] is None
     sv.close()
+
+
+def test_unservable_requests_are_rejected_at_submit():
+    """Requests the batched engine cannot run fail at submit, with a reason:
+    single-grid features (reflecting or fixed boundaries, a body force) and
+    FP32 with the comparison weights."""
+    sv = wcns.Server(hbm_budget_bytes=1 << 28, max_instances_per_class=4, steps_per_tick=2)
+    with pytest.raises(wcns.WcnsError):
+        sv.submit(inputs.rayleigh_taylor(8), tag=1, t_end=0.01)
+    with pytest.raises(wcns.WcnsError):
+        sv.submit(inputs.four_quadrant(32, t_end=0.01), tag=2, precision=wcns.FP32, weights=wcns.W_JS)
+    with pytest.raises(wcns.WcnsError):
+        sv.submit(inputs.four_quadrant(32, t_end=0.01), tag=3, flux=9)
+    # the same problem with FP64 JS weights is served
+    sv.submit(inputs.four_quadrant(32, t_end=0.01), tag=4, weights=wcns.W_JS)
+    got = _drain(sv, 1, timeout_s=60)
+    assert got[4]["status"] == wcns.OK
+    sv.close()
