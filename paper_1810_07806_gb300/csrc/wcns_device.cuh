@@ -70,82 +70,6 @@ struct SchemeConst {
     float gammaf, gm1f;  // gamma, gamma - 1 in float
 };
 
-// FP32 cutoff decision from the three rescaled indicators of one stencil.
-// chi_k is invariant under s -> s/sc except through eps, so the stencil is
-// rescaled (beta, tau become O(1) and cannot underflow) and eps becomes
-// max(eps/sc^2, FLT_MIN).  With b_k = beta_k + eps and m = argmin b (the
-// largest gamma), g_k / g_m is formed as (b_m / b_k)(C b_k + tau)/(C b_m + tau),
-// where every factor is bounded (the literal tau / b_k overflows FP32 when b_k
-// sits at the eps floor), and chi_k < C_T is tested as s_k < C_T sum s with
-// s_k = (g_k / g_m)^q.  tau = 0 keeps every stencil without dividing.
-__device__ __forceinline__ int cut_fp32(float b0, float b1, float b2, float eps_s, const SchemeConst& K)
-{
-    const float tau = fabsf(b0 - b2);
-    const float bm = fminf(fminf(b0, b1), b2) + eps_s;
-    if (!(tau >= K.Kf * bm)) return 7;           // no cut possible (also tau == 0)
-    b0 += eps_s;
-    b1 += eps_s;
-    b2 += eps_s;
-    const float den = __frcp_rn(fmaf(K.Cf, bm, tau));
-    const float bb[3] = {b0, b1, b2};
-    float sk[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const float r = fminf(1.0f, (bm * __frcp_rn(bb[k])) * (fmaf(K.Cf, bb[k], tau) * den));
-        float p;
-        if (K.q == 6) {              // the paper's q: three multiplies, no loop
-            const float r2 = r * r;
-            p = r2 * r2 * r2;
-        } else {
-            p = r;
-            for (int e = 1; e < K.q; ++e) p *= r;
-        }
-        sk[k] = p;
-    }
-    const float lim = K.CTf * (sk[0] + sk[1] + sk[2]);
-    int flags = 0;
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-        if (!(sk[k] < lim)) flags |= 1 << k;
-    return flags;
-}
-
-// Both biased selections of one characteristic field of a face from its six
-// values s[0..5] = w_{j-2} .. w_{j+3}: the left-biased stencil is s[0..4], the
-// right-biased one the mirror s[5..1].  The values are rescaled once by
-// 1/sc, sc = max |s| (floored at FLT_MIN so an all-zero field keeps every
-// stencil without a branch), and the two second differences the mirrored
-// stencils share are formed once.
-__device__ __forceinline__ void select_pair_fp32(const float s[6], float sqrt_eps, const SchemeConst& K,
-                                                 int& fL, int& fR)
-{
-    float sc = 0.f;
-#pragma unroll
-    for (int m = 0; m < 6; ++m) sc = fmaxf(sc, fabsf(s[m]));
-    sc = fmaxf(sc, 1.17549435e-38f);
-    const float inv = __frcp_rn(sc);
-    const float e = sqrt_eps * inv;
-    const float eps_s = fmaxf(e * e, 1.17549435e-38f);
-    float t[6];
-#pragma unroll
-    for (int m = 0; m < 6; ++m) t[m] = s[m] * inv;
-    // second differences: (t0 t1 t2), (t1 t2 t3), (t2 t3 t4), (t3 t4 t5)
-    const float a2 = t[0] - 2.0f * t[1] + t[2];
-    const float b2 = t[1] - 2.0f * t[2] + t[3];
-    const float c2 = t[2] - 2.0f * t[3] + t[4];
-    const float d2 = t[3] - 2.0f * t[4] + t[5];
-    // left-biased: centre t2
-    const float l0 = 0.5f * (t[0] - 4.0f * t[1] + 3.0f * t[2]);
-    const float l1 = 0.5f * (t[3] - t[1]);
-    const float l2 = 0.5f * (-3.0f * t[2] + 4.0f * t[3] - t[4]);
-    // right-biased (mirror): centre t3
-    const float r0 = 0.5f * (t[5] - 4.0f * t[4] + 3.0f * t[3]);
-    const float r1 = 0.5f * (t[2] - t[4]);
-    const float r2 = 0.5f * (-3.0f * t[3] + 4.0f * t[2] - t[1]);
-    fL = cut_fp32(l0 * l0 + a2 * a2, l1 * l1 + b2 * b2, l2 * l2 + c2 * c2, eps_s, K);
-    fR = cut_fp32(r0 * r0 + d2 * d2, r1 * r1 + c2 * c2, r2 * r2 + b2 * b2, eps_s, K);
-}
-
 // Eq. 12 with the comparison weights (FP32), both biased values of one
 // characteristic field from its six values s[0..5] = w_{j-2} .. w_{j+3}.
 // The values are rescaled by sc = max |s| (floored at FLT_MIN) as for the
@@ -257,9 +181,17 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, bc2(-1.f), a); }
 
-// The cutoff of cut_fp32 for both sides at once: the no-cut test per lane,
-// and, when either side may cut, the ratio form of Eq. 16-18 in packed
-// arithmetic (a side that passed the test keeps its 7).
+// FP32 cutoff (Eq. 16-18) of both biased stencils of a field at once, from
+// their rescaled indicators (lane x: left, lane y: right).  chi_k is
+// invariant under s -> s/sc except through eps, so the stencil values are
+// rescaled (beta, tau become O(1) and cannot underflow) and eps becomes
+// max(eps/sc^2, FLT_MIN).  Per lane: the exact no-cut test first (also tau ==
+// 0); if either side may cut, the ratio form runs for both lanes in packed
+// arithmetic.  With b_k = beta_k + eps and m = argmin b (the largest gamma),
+// g_k / g_m = (b_m / b_k)(C b_k + tau)/(C b_m + tau), every factor bounded (the
+// literal tau / b_k overflows FP32 when b_k sits at the eps floor), and
+// chi_k < C_T is tested as s_k < C_T sum s with s_k = (g_k / g_m)^q.  A side
+// that passed the no-cut test keeps its 7.
 __device__ __forceinline__ void cut_x2(float2 B0, float2 B1, float2 B2, float eps_s, const SchemeConst& K,
                                        int& fL, int& fR)
 {
@@ -304,8 +236,10 @@ __device__ __forceinline__ void cut_x2(float2 B0, float2 B1, float2 B2, float ep
 // Both biased selections and interpolations of one characteristic field,
 // paired: S0 = (w_{j-2}, w_{j+3}), S1 = (w_{j-1}, w_{j+2}), S2 = (w_j, w_{j+1})
 // are the left stencil's s0..s2 in .x and the mirrored right stencil's in
-// .y (s3, s4 are the swapped S2, S1).  Same rescaling and cutoff as
-// select_pair_fp32; returns (u_L, u_R) and the two flag words.
+// .y (s3, s4 are the swapped S2, S1).  The six values are rescaled once by
+// 1/sc, sc = max |s| (floored at FLT_MIN so an all-zero field keeps every
+// stencil without a branch), and the second differences the mirrored
+// stencils share are formed once.  Returns (u_L, u_R) and the two flag words.
 __device__ __forceinline__ float2 select_interp_x2(float2 S0, float2 S1, float2 S2, float sqrt_eps,
                                                    const SchemeConst& K, int& fL, int& fR)
 {
