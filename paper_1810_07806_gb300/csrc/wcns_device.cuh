@@ -70,6 +70,17 @@ struct SchemeConst {
     float gammaf, gm1f;  // gamma, gamma - 1 in float
 };
 
+// FP32 reciprocal: the hardware approximation (PTX rcp.approx.ftz.f32, at
+// most 1 ulp from 1/x over the full range).  Every argument in the FP32 path
+// is a normal number (rescaled indicators are floored at FLT_MIN, densities
+// and sound speeds are positive), so flushing subnormals changes nothing.
+__device__ __forceinline__ float rcpf(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Eq. 12 with the comparison weights (FP32), both biased values of one
 // characteristic field from its six values s[0..5] = w_{j-2} .. w_{j+3}.
 // The values are rescaled by sc = max |s| (floored at FLT_MIN) as for the
@@ -88,7 +99,7 @@ __device__ __forceinline__ void weights_pair_fp32(const float s[6], float sqrt_e
 #pragma unroll
     for (int m = 0; m < 6; ++m) sc = fmaxf(sc, fabsf(s[m]));
     sc = fmaxf(sc, 1.17549435e-38f);
-    const float inv = __frcp_rn(sc);
+    const float inv = rcpf(sc);
     float t[6];
 #pragma unroll
     for (int m = 0; m < 6; ++m) t[m] = s[m] * inv;
@@ -123,17 +134,17 @@ __device__ __forceinline__ void weights_pair_fp32(const float s[6], float sqrt_e
             const float bm = fminf(fminf(b[0], b[1]), b[2]);
             if constexpr (WT == W_Z) {
                 const float tau = fabsf(b[0] - b[2]);
-                const float den = __frcp_rn(bm + tau);
+                const float den = rcpf(bm + tau);
 #pragma unroll
-                for (int k = 0; k < 3; ++k) w[k] = d[k] * (bm * __frcp_rn(b[k])) * ((b[k] + tau) * den);
+                for (int k = 0; k < 3; ++k) w[k] = d[k] * (bm * rcpf(b[k])) * ((b[k] + tau) * den);
             } else {
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
-                    const float r = bm * __frcp_rn(b[k]);
+                    const float r = bm * rcpf(b[k]);
                     w[k] = d[k] * r * r;
                 }
             }
-            const float iw = __frcp_rn(w[0] + w[1] + w[2]);
+            const float iw = rcpf(w[0] + w[1] + w[2]);
 #pragma unroll
             for (int k = 0; k < 3; ++k) w[k] *= iw;
         }
@@ -205,11 +216,11 @@ __device__ __forceinline__ void cut_x2(float2 B0, float2 B1, float2 B2, float ep
     const float2 tau = make_float2(tauL, tauR), bm = make_float2(bmL, bmR);
     const float2 e2 = bc2(eps_s), C2 = bc2(K.Cf);
     const float2 b[3] = {add2(B0, e2), add2(B1, e2), add2(B2, e2)};
-    const float2 den = make_float2(__frcp_rn(fmaf(K.Cf, bmL, tauL)), __frcp_rn(fmaf(K.Cf, bmR, tauR)));
+    const float2 den = make_float2(rcpf(fmaf(K.Cf, bmL, tauL)), rcpf(fmaf(K.Cf, bmR, tauR)));
     float2 sk[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const float2 rb = make_float2(__frcp_rn(b[k].x), __frcp_rn(b[k].y));
+        const float2 rb = make_float2(rcpf(b[k].x), rcpf(b[k].y));
         float2 r = mul2(mul2(bm, rb), mul2(fma2(C2, b[k], tau), den));
         r = make_float2(fminf(1.0f, r.x), fminf(1.0f, r.y));
         float2 pw;
@@ -246,7 +257,7 @@ __device__ __forceinline__ float2 select_interp_x2(float2 S0, float2 S1, float2 
     float sc = fmaxf(fmaxf(fmaxf(fabsf(S0.x), fabsf(S0.y)), fmaxf(fabsf(S1.x), fabsf(S1.y))),
                      fmaxf(fabsf(S2.x), fabsf(S2.y)));
     sc = fmaxf(sc, 1.17549435e-38f);
-    const float inv = __frcp_rn(sc);
+    const float inv = rcpf(sc);
     const float e = sqrt_eps * inv;
     const float eps_s = fmaxf(e * e, 1.17549435e-38f);
     const float2 iv = bc2(inv);

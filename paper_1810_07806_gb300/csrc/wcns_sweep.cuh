@@ -166,8 +166,8 @@ __device__ __forceinline__ void face_flux(float (&u)[6][ND + 2], const SweepArgs
     const float* Ua = u[2];
     const float* Ub = u[3];
     const float sa = sqrtf(Ua[0]), sb = sqrtf(Ub[0]);
-    const float ia = __frcp_rn(Ua[0]), ib = __frcp_rn(Ub[0]);
-    const float wsum = __frcp_rn(sa + sb);
+    const float ia = rcpf(Ua[0]), ib = rcpf(Ub[0]);
+    const float wsum = rcpf(sa + sb);
     float vel[ND], q2 = 0.f;
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
@@ -178,8 +178,8 @@ __device__ __forceinline__ void face_flux(float (&u)[6][ND + 2], const SweepArgs
     const float H = (sa * (Ua[ND + 1] + pa) * ia + sb * (Ub[ND + 1] + pb) * ib) * wsum;
     const float c2 = gm1 * (H - 0.5f * q2);
     const float c = sqrtf(c2);
-    const float ic = __frcp_rn(c);
-    const float hb1 = 0.5f * gm1 * __frcp_rn(c2);   // b1 / 2
+    const float ic = rcpf(c);
+    const float hb1 = 0.5f * gm1 * rcpf(c2);   // b1 / 2
     const float un = vel[DIR];
     float Uj[NV], Uj1[NV];
 #pragma unroll
