@@ -81,6 +81,15 @@ __device__ __forceinline__ float rcpf(float x)
     return r;
 }
 
+// FP32 reciprocal square root: PTX rsqrt.approx.ftz.f32 (relative error
+// below 2^-22).  sqrt(x) is formed as x * rsqrtf_a(x) where both are needed.
+__device__ __forceinline__ float rsqrtf_a(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Eq. 12 with the comparison weights (FP32), both biased values of one
 // characteristic field from its six values s[0..5] = w_{j-2} .. w_{j+3}.
 // The values are rescaled by sc = max |s| (floored at FLT_MIN) as for the
@@ -289,19 +298,27 @@ __device__ __forceinline__ float2 select_interp_x2(float2 S0, float2 S1, float2 
 // ------------------------------------------------------------------------
 // Euler primitives and midpoint fluxes (any evaluation order).
 // ------------------------------------------------------------------------
-template <int ND, typename T>
-__device__ __forceinline__ T pressure_of(const T* U, T gm1)
+// (These are the FP32 path's; the FP64 path has its own in the oracle's
+// operation order.)  pressure_ir takes 1 / rho.
+template <int ND>
+__device__ __forceinline__ float pressure_ir(const float* U, float ir, float gm1)
 {
-    T m2 = U[1] * U[1];
+    float m2 = U[1] * U[1];
 #pragma unroll
-    for (int a = 1; a < ND; ++a) m2 = fma(U[1 + a], U[1 + a], m2);
-    return gm1 * (U[ND + 1] - T(0.5) * m2 / U[0]);
+    for (int a = 1; a < ND; ++a) m2 = fmaf(U[1 + a], U[1 + a], m2);
+    return gm1 * fmaf(-0.5f * m2, ir, U[ND + 1]);
 }
 
-template <int ND, int D, typename T>
-__device__ __forceinline__ void phys_flux(const T* U, T p, T* F)
+template <int ND>
+__device__ __forceinline__ float pressure_of(const float* U, float gm1)
 {
-    const T un = U[1 + D] / U[0];
+    return pressure_ir<ND>(U, rcpf(U[0]), gm1);
+}
+
+template <int ND, int D>
+__device__ __forceinline__ void phys_flux(const float* U, float p, float* F)
+{
+    const float un = U[1 + D] * rcpf(U[0]);
     F[0] = U[1 + D];
 #pragma unroll
     for (int a = 0; a < ND; ++a) F[1 + a] = U[1 + a] * un;
@@ -310,49 +327,62 @@ __device__ __forceinline__ void phys_flux(const T* U, T p, T* F)
 }
 
 // Roe (1981) flux difference splitting, F = (F_L + F_R - sum |lam_k| alpha_k r_k)/2
-// with the wave strengths alpha_k of the Roe-averaged state.
-template <int ND, int D, typename T>
-__device__ __forceinline__ void roe_flux(const T* UL, const T* UR, T pL, T pR, T gm1, T* F)
+// with the wave strengths alpha_k of the Roe-averaged state.  rL, rR are
+// 1 / sqrt(rho) of the two states: sqrt(rho) = rho r, 1 / rho = r^2, and the
+// Roe weights sqrt(rho)/rho are r itself.
+template <int ND, int D>
+__device__ __forceinline__ void roe_flux(const float* UL, const float* UR, float pL, float pR, float rL,
+                                         float rR, float gm1, float* F)
 {
     constexpr int NV = ND + 2;
-    T FL[NV], FR[NV];
-    phys_flux<ND, D>(UL, pL, FL);
-    phys_flux<ND, D>(UR, pR, FR);
-    const T sL = sqrt(UL[0]), sR = sqrt(UR[0]);
-    const T iL = T(1) / UL[0], iR = T(1) / UR[0];
-    const T w = T(1) / (sL + sR);
-    T vel[ND], dv[ND], q2 = 0;
+    const float iL = rL * rL, iR = rR * rR;
+    const float unL = UL[1 + D] * iL, unR = UR[1 + D] * iR;
+    float FL[NV], FR[NV];
+    FL[0] = UL[1 + D];
+    FR[0] = UR[1 + D];
 #pragma unroll
     for (int a = 0; a < ND; ++a) {
-        const T uL = UL[1 + a] * iL, uR = UR[1 + a] * iR;
-        vel[a] = (sL * uL + sR * uR) * w;
-        dv[a] = uR - uL;
-        q2 = fma(vel[a], vel[a], q2);
+        FL[1 + a] = UL[1 + a] * unL;
+        FR[1 + a] = UR[1 + a] * unR;
     }
-    const T H = (sL * (UL[ND + 1] + pL) * iL + sR * (UR[ND + 1] + pR) * iR) * w;
-    const T c2 = gm1 * (H - T(0.5) * q2);
-    const T c = sqrt(c2);
-    const T rho = sL * sR;
-    const T un = vel[D];
-    const T drho = UR[0] - UL[0], dp = pR - pL;
-    const T ic2 = T(1) / c2;
-    const T a0 = T(0.5) * (dp - rho * c * dv[D]) * ic2;
-    const T aN = T(0.5) * (dp + rho * c * dv[D]) * ic2;
-    const T a1 = drho - dp * ic2;
-    const T l0 = fabs(un - c) * a0, l1 = fabs(un) * a1, lN = fabs(un + c) * aN;
-    const T lt = fabs(un) * rho;
+    FL[1 + D] += pL;
+    FR[1 + D] += pR;
+    FL[ND + 1] = (UL[ND + 1] + pL) * unL;
+    FR[ND + 1] = (UR[ND + 1] + pR) * unR;
+    const float sL = UL[0] * rL, sR = UR[0] * rR;
+    const float w = rcpf(sL + sR);
+    float vel[ND], dv[ND], q2 = 0.f;
+#pragma unroll
+    for (int a = 0; a < ND; ++a) {
+        vel[a] = fmaf(UL[1 + a], rL, UR[1 + a] * rR) * w;
+        dv[a] = fmaf(UR[1 + a], iR, -UL[1 + a] * iL);
+        q2 = fmaf(vel[a], vel[a], q2);
+    }
+    const float H = fmaf(UL[ND + 1] + pL, rL, (UR[ND + 1] + pR) * rR) * w;
+    const float c2 = gm1 * fmaf(-0.5f, q2, H);
+    const float rc = rsqrtf_a(c2);
+    const float c = c2 * rc;
+    const float ic2 = rc * rc;
+    const float rho = sL * sR;
+    const float un = vel[D];
+    const float drho = UR[0] - UL[0], dp = pR - pL;
+    const float a0 = 0.5f * (dp - rho * c * dv[D]) * ic2;
+    const float aN = 0.5f * (dp + rho * c * dv[D]) * ic2;
+    const float a1 = drho - dp * ic2;
+    const float l0 = fabsf(un - c) * a0, l1 = fabsf(un) * a1, lN = fabsf(un + c) * aN;
+    const float lt = fabsf(un) * rho;
     // sum of |lam_k| alpha_k r_k
-    T Dm[NV];
+    float Dm[NV];
     Dm[0] = l0 + l1 + lN;
 #pragma unroll
     for (int a = 0; a < ND; ++a) Dm[1 + a] = vel[a] * Dm[0] + (a == D ? c * (lN - l0) : lt * dv[a]);
-    T e = H * (l0 + lN) + un * c * (lN - l0) + T(0.5) * q2 * l1;
+    float e = H * (l0 + lN) + un * c * (lN - l0) + 0.5f * q2 * l1;
 #pragma unroll
     for (int a = 0; a < ND; ++a)
-        if (a != D) e = fma(vel[a], lt * dv[a], e);
+        if (a != D) e = fmaf(vel[a], lt * dv[a], e);
     Dm[ND + 1] = e;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) F[v] = T(0.5) * (FL[v] + FR[v] - Dm[v]);
+    for (int v = 0; v < NV; ++v) F[v] = 0.5f * (FL[v] + FR[v] - Dm[v]);
 }
 
 // AUSM (Liou and Steffen 1993): interface Mach number M_L^+ + M_R^- and

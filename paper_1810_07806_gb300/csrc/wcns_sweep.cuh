@@ -165,21 +165,21 @@ __device__ __forceinline__ void face_flux(float (&u)[6][ND + 2], const SweepArgs
     //   w_0 = (P + Q)/2, w_1 = rho - P, w_t = m_t - vel_t rho, w_N = (P - Q)/2.
     const float* Ua = u[2];
     const float* Ub = u[3];
-    const float sa = sqrtf(Ua[0]), sb = sqrtf(Ub[0]);
-    const float ia = rcpf(Ua[0]), ib = rcpf(Ub[0]);
-    const float wsum = rcpf(sa + sb);
+    // (ra = 1 / sqrt(rho_j): sqrt(rho_j) = rho_j ra, 1 / rho_j = ra^2)
+    const float ra = rsqrtf_a(Ua[0]), rb = rsqrtf_a(Ub[0]);
+    const float wsum = rcpf(fmaf(Ua[0], ra, Ub[0] * rb));
     float vel[ND], q2 = 0.f;
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
-        vel[d] = (sa * Ua[1 + d] * ia + sb * Ub[1 + d] * ib) * wsum;
+        vel[d] = fmaf(Ua[1 + d], ra, Ub[1 + d] * rb) * wsum;
         q2 = fmaf(vel[d], vel[d], q2);
     }
-    const float pa = pressure_of<ND>(Ua, gm1), pb = pressure_of<ND>(Ub, gm1);
-    const float H = (sa * (Ua[ND + 1] + pa) * ia + sb * (Ub[ND + 1] + pb) * ib) * wsum;
-    const float c2 = gm1 * (H - 0.5f * q2);
-    const float c = sqrtf(c2);
-    const float ic = rcpf(c);
-    const float hb1 = 0.5f * gm1 * rcpf(c2);   // b1 / 2
+    const float pa = pressure_ir<ND>(Ua, ra * ra, gm1), pb = pressure_ir<ND>(Ub, rb * rb, gm1);
+    const float H = fmaf(Ua[ND + 1] + pa, ra, (Ub[ND + 1] + pb) * rb) * wsum;
+    const float c2 = gm1 * fmaf(-0.5f, q2, H);
+    const float ic = rsqrtf_a(c2);
+    const float c = c2 * ic;
+    const float hb1 = 0.5f * gm1 * (ic * ic);   // b1 / 2
     const float un = vel[DIR];
     float Uj[NV], Uj1[NV];
 #pragma unroll
@@ -292,16 +292,19 @@ __device__ __forceinline__ void face_flux(float (&u)[6][ND + 2], const SweepArgs
         UL[NV - 1] = el;
         UR[NV - 1] = er;
     }
-    float pL = pressure_of<ND>(UL, gm1), pR = pressure_of<ND>(UR, gm1);
+    float rL = rsqrtf_a(UL[0]), rR = rsqrtf_a(UR[0]);
+    float pL = pressure_ir<ND>(UL, rL * rL, gm1), pR = pressure_ir<ND>(UR, rR * rR, gm1);
     if (!(UL[0] > 0.f) || !(UR[0] > 0.f) || !(pL > 0.f) || !(pR > 0.f)) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) { UL[v] = Uj[v]; UR[v] = Uj1[v]; }
-        pL = pressure_of<ND>(UL, gm1);
-        pR = pressure_of<ND>(UR, gm1);
+        pL = pa;
+        pR = pb;
+        rL = ra;
+        rR = rb;
         fell_back = true;
     }
     if (FLUX == FLUX_ROE) {
-        roe_flux<ND, DIR>(UL, UR, pL, pR, gm1, F);
+        roe_flux<ND, DIR>(UL, UR, pL, pR, rL, rR, gm1, F);
     } else if (FLUX == FLUX_AUSM) {
         ausm_flux<ND, DIR>(UL, UR, pL, pR, a.K.gammaf, F);
     } else {
