@@ -48,12 +48,14 @@ __device__ __forceinline__ double bwarp_max(double x)
 // Per-instance maximum wave-speed sum.  FP64 batches evaluate every node in
 // the same fixed order as the single-grid rule (so a batched instance takes
 // the same steps as the instance alone); FP32 batches use FP32 speeds rounded
-// upward, with an FP64 maximum.
+// upward, with an FP64 maximum, and write float(U) of the instances that
+// advance (the first stage's input) from the same pass.
 template <int ND, bool FAST>
 __global__ void __launch_bounds__(256) batch_cfl_kernel(const double* __restrict__ U,
                                                         const BatchInst* __restrict__ insts,
                                                         const NodeChunk* __restrict__ chunks,
-                                                        double gamma, double gm1, StepScalars* sc)
+                                                        double gamma, double gm1, StepScalars* sc,
+                                                        float* __restrict__ S)
 {
     const NodeChunk ch = chunks[blockIdx.x];
     StepScalars* s = sc + ch.inst;
@@ -62,25 +64,30 @@ __global__ void __launch_bounds__(256) batch_cfl_kernel(const double* __restrict
     const double* Ui = U + I.off;
     const long long N = I.N;
     double m = 0.0;
+    float mf = 0.f;
+    const float gf = (float)gamma;
     for (int k = threadIdx.x; k < ch.count; k += blockDim.x) {
         const long long i = ch.begin + k;
         if constexpr (FAST) {
-            const float rho = (float)Ui[i];
-            const float ir = __frcp_rn(rho);
+            // the same FP32 expressions as the single-grid rule
+            float Uf[ND + 2];
+#pragma unroll
+            for (int v = 0; v < ND + 2; ++v) {
+                Uf[v] = f64_to_f32_ftz(Ui[v * N + i]);
+                S[I.off + v * N + i] = Uf[v];
+            }
+            const float ir = __frcp_rn(Uf[0]);
             float m2 = 0.f, sum = 0.f, vel[ND];
 #pragma unroll
             for (int a = 0; a < ND; ++a) {
-                const float mv = (float)Ui[(1 + a) * N + i];
-                m2 = fmaf(mv, mv, m2);
-                vel[a] = fabsf(mv) * ir;
+                m2 = fmaf(Uf[1 + a], Uf[1 + a], m2);
+                vel[a] = fabsf(Uf[1 + a]) * ir;
             }
-            // the same FP32 expressions as the single-grid rule
-            const float gf = (float)gamma;
-            const float p = (gf - 1.f) * ((float)Ui[(ND + 1) * N + i] - 0.5f * m2 * ir);
+            const float p = (gf - 1.f) * (Uf[ND + 1] - 0.5f * m2 * ir);
             const float c = sqrtf(gf * p * ir);
 #pragma unroll
             for (int a = 0; a < ND; ++a) sum = fmaf(vel[a] + c, I.inv_hf[a], sum);
-            m = fmax(m, (double)sum * (1.0 + 1.0 / 65536.0));
+            mf = fmaxf(mf, sum);
         } else {
             double Uv[ND + 2];
 #pragma unroll
@@ -95,6 +102,8 @@ __global__ void __launch_bounds__(256) batch_cfl_kernel(const double* __restrict
             m = fmax(m, sum);
         }
     }
+    // (scaling by 1 + 2^-16 is exact on a float and commutes with the max)
+    if constexpr (FAST) m = (double)mf * (1.0 + 1.0 / 65536.0);
     m = bwarp_max(m);
     __shared__ double red[8];
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
@@ -142,15 +151,6 @@ __global__ void __launch_bounds__(256) batch_rk_fp64_kernel(double* __restrict__
         else if (STAGE == 2) U1[i] = add_(mul_(0.75, U0[i]), mul_(0.25, add_(U1[i], mul_(dt, l))));
         else U0[i] = add_(div_(U0[i], 3.0), mul_(2.0 / 3.0, add_(U1[i], mul_(dt, l))));
     }
-}
-
-__global__ void __launch_bounds__(256) batch_to_fp32_kernel(const double* __restrict__ U, float* __restrict__ S,
-                                                            const ElemChunk* __restrict__ chunks,
-                                                            const StepScalars* __restrict__ sc)
-{
-    const ElemChunk ch = chunks[blockIdx.x];
-    if (sc[ch.inst].dt == 0.0) return;
-    for (int k = threadIdx.x; k < ch.count; k += blockDim.x) S[ch.begin + k] = __double2float_rn(U[ch.begin + k]);
 }
 
 __global__ void set_clock_kernel(StepScalars* sc, double t_end)
@@ -376,15 +376,16 @@ cudaError_t step_sequence(wcns_batch* b, cudaStream_t s)
     if (e != cudaSuccess) return e;
     if (b->nnch > 0) {
         const double gm1 = b->gamma - 1.0;
+        float* S0 = fp32 ? (float*)b->S : nullptr;   // FP32: the first stage's input
         if (b->ndim == 1)
-            fp32 ? batch_cfl_kernel<1, true><<<b->nnch, 256, 0, s>>>(b->U, b->d_insts, b->d_nch, b->gamma, gm1, b->sc)
-                 : batch_cfl_kernel<1, false><<<b->nnch, 256, 0, s>>>(b->U, b->d_insts, b->d_nch, b->gamma, gm1, b->sc);
+            fp32 ? batch_cfl_kernel<1, true><<<b->nnch, 256, 0, s>>>(b->U, b->d_insts, b->d_nch, b->gamma, gm1, b->sc, S0)
+                 : batch_cfl_kernel<1, false><<<b->nnch, 256, 0, s>>>(b->U, b->d_insts, b->d_nch, b->gamma, gm1, b->sc, S0);
         else if (b->ndim == 2)
-            fp32 ? batch_cfl_kernel<2, true><<<b->nnch, 256, 0, s>>>(b->U, b->d_insts, b->d_nch, b->gamma, gm1, b->sc)
-                 : batch_cfl_kernel<2, false><<<b->nnch, 256, 0, s>>>(b->U, b->d_insts, b->d_nch, b->gamma, gm1, b->sc);
+            fp32 ? batch_cfl_kernel<2, true><<<b->nnch, 256, 0, s>>>(b->U, b->d_insts, b->d_nch, b->gamma, gm1, b->sc, S0)
+                 : batch_cfl_kernel<2, false><<<b->nnch, 256, 0, s>>>(b->U, b->d_insts, b->d_nch, b->gamma, gm1, b->sc, S0);
         else
-            fp32 ? batch_cfl_kernel<3, true><<<b->nnch, 256, 0, s>>>(b->U, b->d_insts, b->d_nch, b->gamma, gm1, b->sc)
-                 : batch_cfl_kernel<3, false><<<b->nnch, 256, 0, s>>>(b->U, b->d_insts, b->d_nch, b->gamma, gm1, b->sc);
+            fp32 ? batch_cfl_kernel<3, true><<<b->nnch, 256, 0, s>>>(b->U, b->d_insts, b->d_nch, b->gamma, gm1, b->sc, S0)
+                 : batch_cfl_kernel<3, false><<<b->nnch, 256, 0, s>>>(b->U, b->d_insts, b->d_nch, b->gamma, gm1, b->sc, S0);
     }
     if (b->nslots_active > 0)
         batch_finalize_kernel<<<(b->nslots_active + 127) / 128, 128, 0, s>>>(b->sc, b->d_slots, b->nslots_active,
@@ -401,13 +402,12 @@ cudaError_t step_sequence(wcns_batch* b, cudaStream_t s)
         if ((e = sweeps(b, U1, L, s)) != cudaSuccess) return e;
         batch_rk_fp64_kernel<3><<<b->nech, 256, 0, s>>>(b->U, U1, L, b->d_ech, b->sc);
     } else {
-        // stage inputs A -> B -> A; the x sweep of each stage applies the
-        // stage combination (stage 3 updates the FP64 state, from which the
-        // next step converts A again)
+        // stage inputs A -> B -> A (A = float(U) from the time-step pass);
+        // the x sweep of each stage applies the stage combination, stage 3
+        // to the FP64 state
         float* A = (float*)b->S;
         float* B = b->S2;
         float* L = (float*)b->L;
-        batch_to_fp32_kernel<<<b->nech, 256, 0, s>>>(b->U, A, b->d_ech, b->sc);
         if ((e = sweeps(b, A, L, s, 1, B)) != cudaSuccess) return e;
         if ((e = sweeps(b, B, L, s, 2, A)) != cudaSuccess) return e;
         if ((e = sweeps(b, A, L, s, 3, nullptr)) != cudaSuccess) return e;

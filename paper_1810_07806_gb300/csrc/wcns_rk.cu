@@ -80,19 +80,19 @@ __global__ void __launch_bounds__(256) cfl_reduce_fast_kernel(const double* __re
     for (int a = 0; a < ND; ++a) ih[a] = (float)(1.0 / hh.v[a]);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
          i += (long long)gridDim.x * blockDim.x) {
-        const float rho = (float)U[i];
+        const float rho = f64_to_f32_ftz(U[i]);
         const float ir = __frcp_rn(rho);
         float m2 = 0.f, s = 0.f, c = 0.f;
         float vel[ND];
         float mvs[ND];
 #pragma unroll
         for (int a = 0; a < ND; ++a) {
-            const float mv = (float)U[(1 + a) * N + i];
+            const float mv = f64_to_f32_ftz(U[(1 + a) * N + i]);
             mvs[a] = mv;
             m2 = fmaf(mv, mv, m2);
             vel[a] = fabsf(mv) * ir;
         }
-        const float E = (float)U[(ND + 1) * N + i];
+        const float E = f64_to_f32_ftz(U[(ND + 1) * N + i]);
         if (S != nullptr) {
             S[i] = rho;
 #pragma unroll
@@ -237,10 +237,10 @@ cudaError_t launch_rk_fp64(int stage, double* U0, double* U1, const double* L, l
 __global__ void __launch_bounds__(256) to_fp32_kernel(const double* __restrict__ U, float* __restrict__ S,
                                                       long long M, const StepScalars* sc)
 {
-    if (sc != nullptr && sc->dt == 0.0) return;   // a finished run (sc may be null: always convert)
+    if (sc != nullptr && f64_is_zero(sc->dt)) return;   // a finished run (sc may be null: always convert)
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M;
          i += (long long)gridDim.x * blockDim.x)
-        S[i] = __double2float_rn(U[i]);
+        S[i] = f64_to_f32_ftz(U[i]);
 }
 
 cudaError_t launch_to_fp32(const double* U, float* S, long long M, const StepScalars* sc, cudaStream_t s)

@@ -343,6 +343,14 @@ __device__ __forceinline__ void node_flux_diff(const T* sS, int l, int s, int k,
 }
 
 // ---------------------------------------------------------------- kernel
+// A staged value in the sweep's type (FP64 -> FP32 by the integer rounding).
+template <typename T, typename LT>
+__device__ __forceinline__ T stage_cvt(LT x)
+{
+    if constexpr (sizeof(T) == 4 && sizeof(LT) == 8) return f64_to_f32_ftz(x);
+    else return (T)x;
+}
+
 template <typename T, typename LT, int ND, int DIR, int FLUX, bool BATCH = false, int CFG = 0, int WT = 0>
 __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) sweep_kernel(const SweepArgs a)
 {
@@ -403,7 +411,7 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) swee
     // A finished run (dt == 0) skips the work.  The FP32 sweep reads the flag
     // after its staging copies are in flight, so the read costs no latency.
     if constexpr (!kAsyncStage) {
-        if (dtp != nullptr && *dtp == 0.0) return;
+        if (dtp != nullptr && f64_is_zero(*dtp)) return;
     }
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sS = reinterpret_cast<T*>(smem_raw);
@@ -457,7 +465,7 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) swee
             if (kind == BC_FIXED) {
                 const double* st = a.bcs[p < 0 ? 0 : 1];
 #pragma unroll
-                for (int v = 0; v < NV; ++v) sS[sidx<DIR, TL, P>(v, l, s)] = (T)st[v];
+                for (int v = 0; v < NV; ++v) sS[sidx<DIR, TL, P>(v, l, s)] = stage_cvt<T>(st[v]);
                 continue;
             }
             if (kind == BC_REFLECTING) {
@@ -465,7 +473,7 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) swee
                 const LT* src = U + base0 + l * lstride + (long long)q * sd;
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
-                    const T val = (T)src[v * N];
+                    const T val = stage_cvt<T>(src[v * N]);
                     sS[sidx<DIR, TL, P>(v, l, s)] = v == 1 + DIR ? -val : val;
                 }
                 continue;
@@ -478,12 +486,12 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) swee
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             if constexpr (kAsyncStage) cp_async4(&sS[sidx<DIR, TL, P>(v, l, s)], src + v * N);
-            else sS[sidx<DIR, TL, P>(v, l, s)] = (T)src[v * N];
+            else sS[sidx<DIR, TL, P>(v, l, s)] = stage_cvt<T>(src[v * N]);
         }
     }
     if constexpr (kAsync) cp_async_commit();   // group: staged nodes
     if constexpr (kAsyncStage) {
-        if (dtp != nullptr && *dtp == 0.0) {
+        if (dtp != nullptr && f64_is_zero(*dtp)) {
             cp_async_wait<0>();
             return;
         }
@@ -563,6 +571,11 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) swee
     // the node fluxes Eq. 4-5 need.
     T* L = Lb;
     const int diff = a.K.diff;
+    // dt of the fused stage in FP32, converted once per thread
+    float dtf = 0.f;
+    if constexpr (G::FUSE) {
+        if (a.fuse_stage) dtf = f64_to_f32_ftz(*dtp);
+    }
     // ALT: Eq. 4-5 and / or the body-force source; the plain Eq. 3 instance
     // carries neither
     auto node_phase = [&](auto alt_tag) {
@@ -640,7 +653,7 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) swee
                             // The next stage's input is float(U0) + D; float(U0) is
                             // this stage's staged input in stage 1 and the prefetched
                             // output buffer in stage 2 (the step starts from float(U0)).
-                            const float dt = (float)*dtp;
+                            const float dt = dtf;
                             const long long gi = v * N + g;
                             if (a.fuse_stage == 1) {
                                 const float dd = dt * lv;
@@ -655,7 +668,7 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) swee
                                 // time-step pass, so stage 3 writes the FP64 state only
                                 const double u0 = sU0[sidx<DIR, TL, TS>(v, l, t)];
                                 const float dd = (2.0f / 3.0f) * fmaf(dt, lv, sD[sidx<DIR, TL, TS>(v, l, t)]);
-                                U0b[gi] = u0 + (double)dd;
+                                U0b[gi] = u0 + f32_to_f64_ftz(dd);
                             }
                             continue;
                         }
