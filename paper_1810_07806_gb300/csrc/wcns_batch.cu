@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(256) batch_cfl_kernel(const double* __restrict
             double Uv[ND + 2];
 #pragma unroll
             for (int v = 0; v < ND + 2; ++v) Uv[v] = Ui[v * N + i];
-            const double c = __dsqrt_rn(div_(mul_(gamma, pressure_exact<ND>(Uv, gm1)), Uv[0]));
+            const double c = sqrt_(div_(mul_(gamma, pressure_exact<ND>(Uv, gm1)), Uv[0]));
             double sum = 0.0;
 #pragma unroll
             for (int a = 0; a < ND; ++a) {

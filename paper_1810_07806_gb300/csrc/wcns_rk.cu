@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(256) cfl_reduce_kernel(const double* __restric
         double Ui[ND + 2];
 #pragma unroll
         for (int v = 0; v < ND + 2; ++v) Ui[v] = U[v * N + i];
-        const double c = __dsqrt_rn(div_(mul_(gamma, pressure_exact<ND>(Ui, gm1)), Ui[0]));
+        const double c = sqrt_(div_(mul_(gamma, pressure_exact<ND>(Ui, gm1)), Ui[0]));
         double s = 0.0;
 #pragma unroll
         for (int a = 0; a < ND; ++a) {

@@ -120,9 +120,10 @@ struct TileGeom {
     static constexpr int P = TS + 2 * GHOST;                          // staged nodes
     static constexpr int NF = TS + 5;                                 // faces
     static constexpr int THREADS = 256;
-    // FP32: at most 64 registers so four CTAs share an SM; FP64 is bound by
-    // its pipe and keeps the compiler's choice.
-    static constexpr int MIN_CTAS = sizeof(T) == 4 ? 4 : 1;
+    // FP32: at most 64 registers so four CTAs share an SM.  FP64: at most 128,
+    // two CTAs (the integer division and square root are long dependent
+    // chains that one CTA of eight warps cannot hide).
+    static constexpr int MIN_CTAS = sizeof(T) == 4 ? 4 : 2;
     // FP32 sweeps that accumulate prefetch the TS nodes of L they update
     static constexpr bool PREFETCH_L = sizeof(T) == 4;
     // The FP32 x sweep (the last of a step's stage) can fuse the stage
