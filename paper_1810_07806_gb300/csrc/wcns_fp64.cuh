@@ -29,8 +29,9 @@ __device__ __forceinline__ double sub_(double a, double b) { return __dadd_rn(a,
 // steps, one product for the estimate, one exact remainder test that fixes
 // the estimate to the truncated 54-bit result, and round-to-nearest-even
 // from its last bit and the remainder, as IEEE 754 defines the rounding.
-// Every other case (zero, subnormal, infinite or NaN operand, a quotient
-// outside the normal range) takes the hardware operation.  Either way the
+// A zero numerator or radicand gives the signed zero directly; every other
+// case (zero divisor, subnormal, infinite or NaN operand, a quotient outside
+// the normal range) takes the hardware operation.  Either way the
 // result is the IEEE result, bit for bit.
 // ------------------------------------------------------------------------
 typedef unsigned long long u64;
@@ -65,8 +66,10 @@ __device__ __forceinline__ double ddiv_int(double a, double b)
     const unsigned hb = (unsigned)__double2hiint(b), lb = (unsigned)__double2loint(b);
     const int ea = (int)((ha >> 20) & 0x7ffu), eb = (int)((hb >> 20) & 0x7ffu);
     int e = ea - eb + 1023;   // biased exponent of the quotient for ma >= mb
-    if ((unsigned)(ea - 1) >= 2046u || (unsigned)(eb - 1) >= 2046u || (unsigned)(e - 2) >= 2044u)
-        return __ddiv_rn(a, b);
+    const bool b_normal = (unsigned)(eb - 1) < 2046u;
+    // 0 / b = signed zero (constant data makes many zero numerators)
+    if (b_normal && ((ha & 0x7fffffffu) | la) == 0u) return __hiloint2double((int)((ha ^ hb) & 0x80000000u), 0);
+    if (!b_normal || (unsigned)(ea - 1) >= 2046u || (unsigned)(e - 2) >= 2044u) return __ddiv_rn(a, b);
     u64 ma = mant53(ha, la);
     const u64 mb = mant53(hb, lb);
     if (ma < mb) { ma <<= 1; --e; }   // ma in [mb, 2 mb): quotient in [1, 2)
@@ -88,6 +91,7 @@ __device__ __forceinline__ double dsqrt_int(double a)
 {
     const unsigned ha = (unsigned)__double2hiint(a), la = (unsigned)__double2loint(a);
     const int ea = (int)(ha >> 20);   // with the sign bit: positive normal iff 1 <= ea <= 2046
+    if (((ha & 0x7fffffffu) | la) == 0u) return a;   // sqrt(+-0) = +-0
     if ((unsigned)(ea - 1) >= 2046u) return __dsqrt_rn(a);
     const unsigned frac23 = ((ha & 0xfffffu) << 3) | (la >> 29);
     u64 m = mant53(ha, la);
@@ -118,7 +122,12 @@ __device__ __forceinline__ double dsqrt_int(double a)
     return __hiloint2double((int)hi, (int)(unsigned)M);
 }
 
+// The integer forms have about 2.5x the throughput of the hardware sequences
+// but a longer dependent chain: code that every face runs takes them, the
+// rarely taken exact cutoff (a few lanes of a warp, latency-bound) keeps the
+// hardware division (div_lat_).  Both give the IEEE result.
 __device__ __forceinline__ double div_(double a, double b) { return ddiv_int(a, b); }
+__device__ __forceinline__ double div_lat_(double a, double b) { return __ddiv_rn(a, b); }
 __device__ __forceinline__ double sqrt_(double a) { return dsqrt_int(a); }
 
 // p = (gamma-1) (E - (0.5 * sum m_a^2) / rho), sum taken in axis order.
@@ -257,13 +266,13 @@ __device__ __forceinline__ int select_fp64(const double s[5], const SchemeConst&
     double g[3], gmax = 0.0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        g[k] = add_(K.C, div_(tau, add_(beta[k], K.eps)));
+        g[k] = add_(K.C, div_lat_(tau, add_(beta[k], K.eps)));
         if (g[k] > gmax) gmax = g[k];
     }
     double sk[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const double r = div_(g[k], gmax);
+        const double r = div_lat_(g[k], gmax);
         double p = r;
         for (int e = 1; e < K.q; ++e) p = mul_(p, r);
         sk[k] = p;
@@ -272,7 +281,7 @@ __device__ __forceinline__ int select_fp64(const double s[5], const SchemeConst&
     int flags = 0;
 #pragma unroll
     for (int k = 0; k < 3; ++k)
-        if (!(div_(sk[k], ssum) < K.CT)) flags |= 1 << k;
+        if (!(div_lat_(sk[k], ssum) < K.CT)) flags |= 1 << k;
     return flags;
 }
 
