@@ -151,7 +151,7 @@ def profile_traffic(kernel_tag):
 def kernel_source_hash():
     d = os.path.join(ROOT, "paper_1810_07806_gb300", "csrc")
     sha = hashlib.sha256()
-    for f in ("wcns_device.cuh", "wcns_sweep.cuh", "sweep_fp32.cu"):
+    for f in ("wcns_device.cuh", "wcns_cvt.cuh", "wcns_sweep.cuh", "sweep_fp32.cu"):
         sha.update(open(os.path.join(d, f), "rb").read())
     return sha.hexdigest()[:16]
 
