@@ -149,10 +149,13 @@ def profile_traffic(kernel_tag):
 
 
 def kernel_source_hash():
+    """Hash of the FP32 sweep's code: its source files without // comments
+    and blank lines, so that a comment edit keeps a profile valid."""
     d = os.path.join(ROOT, "paper_1810_07806_gb300", "csrc")
     sha = hashlib.sha256()
     for f in ("wcns_device.cuh", "wcns_cvt.cuh", "wcns_sweep.cuh", "sweep_fp32.cu"):
-        sha.update(open(os.path.join(d, f), "rb").read())
+        lines = (ln.split("//", 1)[0].rstrip() for ln in open(os.path.join(d, f)).read().splitlines())
+        sha.update(("\n".join(ln for ln in lines if ln.strip()) + "\n").encode())
     return sha.hexdigest()[:16]
 
 

@@ -20,13 +20,15 @@ __device__ __forceinline__ double mul_(double a, double b) { return __dmul_rn(a,
 __device__ __forceinline__ double add_(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double sub_(double a, double b) { return __dadd_rn(a, -b); }
 
-// The integer forms have about 2.5x the throughput of the hardware sequences
-// but a longer dependent chain: code that every face runs takes them, the
-// rarely taken exact cutoff (a few lanes of a warp, latency-bound) keeps the
-// hardware division (div_lat_).  Both give the IEEE result.
-__device__ __forceinline__ double div_(double a, double b) { return ddiv_int(a, b); }
-__device__ __forceinline__ double div_lat_(double a, double b) { return __ddiv_rn(a, b); }
-__device__ __forceinline__ double sqrt_(double a) { return dsqrt_int(a); }
+// Division and square root of the face code: the hardware operations.  The
+// integer forms of wcns_f64int.cuh have 2.5x the throughput in isolation and
+// make the first steps from initial data 1.36x faster, but on developed 2D
+// flow the sweep was 1.23x slower with them (cause not identified yet); they
+// serve the per-node code of the scalar solver, where every lane runs the
+// same operations (div_int_).  Every form gives the IEEE result.
+__device__ __forceinline__ double div_(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ double sqrt_(double a) { return __dsqrt_rn(a); }
+__device__ __forceinline__ double div_int_(double a, double b) { return ddiv_int(a, b); }
 
 // p = (gamma-1) (E - (0.5 * sum m_a^2) / rho), sum taken in axis order.
 template <int ND>
@@ -164,13 +166,13 @@ __device__ __forceinline__ int select_fp64(const double s[5], const SchemeConst&
     double g[3], gmax = 0.0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        g[k] = add_(K.C, div_lat_(tau, add_(beta[k], K.eps)));
+        g[k] = add_(K.C, div_(tau, add_(beta[k], K.eps)));
         if (g[k] > gmax) gmax = g[k];
     }
     double sk[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const double r = div_lat_(g[k], gmax);
+        const double r = div_(g[k], gmax);
         double p = r;
         for (int e = 1; e < K.q; ++e) p = mul_(p, r);
         sk[k] = p;
@@ -179,7 +181,7 @@ __device__ __forceinline__ int select_fp64(const double s[5], const SchemeConst&
     int flags = 0;
 #pragma unroll
     for (int k = 0; k < 3; ++k)
-        if (!(div_lat_(sk[k], ssum) < K.CT)) flags |= 1 << k;
+        if (!(div_(sk[k], ssum) < K.CT)) flags |= 1 << k;
     return flags;
 }
 

@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(SC_THREADS) scalar_kernel(const ScalarArgs a)
                     ? add_(add_(mul_(MD_A1, sub_(f[3], f[2])), mul_(MD_A2, sub_(f[4], f[1]))),
                            mul_(MD_A3, sub_(f[5], f[0])))
                     : diff_alt_fp64(diff, f[1], f[2], f[3], f[4], sub_(fn[3], fn[1]), sub_(fn[4], fn[0]));
-            const double Li = div_(-fp, a.h);
+            const double Li = div_int_(-fp, a.h);
             if (!RUN) {
                 a.L[line * a.ld + lo + l] = Li;
                 continue;
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(SC_THREADS) scalar_kernel(const ScalarArgs a)
             } else if (stage == 1) {
                 ue[2 + l] = add_(mul_(0.75, u0[l]), mul_(0.25, v));
             } else {
-                const double un = add_(div_(u0[l], 3.0), mul_(2.0 / 3.0, v));
+                const double un = add_(div_int_(u0[l], 3.0), mul_(2.0 / 3.0, v));
                 u0[l] = un;
                 ue[2 + l] = un;
             }

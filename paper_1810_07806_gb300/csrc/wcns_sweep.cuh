@@ -121,8 +121,7 @@ struct TileGeom {
     static constexpr int NF = TS + 5;                                 // faces
     static constexpr int THREADS = 256;
     // FP32: at most 64 registers so four CTAs share an SM.  FP64: at most 128,
-    // two CTAs (the integer division and square root are long dependent
-    // chains that one CTA of eight warps cannot hide).
+    // two CTAs (measured a little faster than one CTA with 175 registers).
     static constexpr int MIN_CTAS = sizeof(T) == 4 ? 4 : 2;
     // FP32 sweeps that accumulate prefetch the TS nodes of L they update
     static constexpr bool PREFETCH_L = sizeof(T) == 4;
