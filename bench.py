@@ -31,8 +31,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "WCNS RHS cell-updates/s"
 UNIT = "cell-updates/s"
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12     # SMs x FP64 FMA/clk x FMA x max SM clock
+# Unit counts of the GB300 SM: 128 FP32 lanes, 2 FP64 FMA per clock; an FMA
+# is 2 flops.  The SM count and the maximum clock are read at run time.
+FP32_LANES_PER_SM, FP64_FMA_PER_SM = 128, 2
+DEFAULT_SMS, DEFAULT_SM_MHZ, FALLBACK_HBM_GBS = 152, 2070.0, 6800.0
 
 # Flops per face and per node of one sweep direction of the FP32 kernel,
 # counted from its arithmetic (FMA = 2, add/mul/min/max/abs = 1, one MUFU
@@ -58,6 +60,8 @@ def parse():
                     choices=["tgv256", "tgv192", "quad1024", "sod400", "rt1024", "batch1d", "serve", "scalar"])
     ap.add_argument("--requests", type=int, default=32, help="serve: requests replayed from the trace")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrival rate (1/s)")
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "fp64"],
+                    help="single-grid workloads: the path timed (auto: the workload's default)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain-path line")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     return ap.parse_args()
@@ -85,6 +89,37 @@ def workload(name):
     pb = inputs.shock_tube(400)
     return pb, dict(workload="sod_1d_400", nodes=pb.cells, nv=3, precision="fp64", flux="roe",
                     cfl=0.5), False
+
+
+def measured_peaks():
+    """MEASURED_PEAKS.json at the repository root (copy bandwidth and clocks
+    measured on this GPU model), or an empty dict."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def device_peaks(dev_index=0):
+    """ALU peaks derived from unit counts, this device's SM count and the
+    maximum SM clock, and the HBM peak: the measured copy bandwidth when
+    MEASURED_PEAKS.json is present, else the fallback figure."""
+    mp = measured_peaks()
+    sms = DEFAULT_SMS
+    try:
+        import torch
+        if torch.cuda.is_available():
+            sms = torch.cuda.get_device_properties(dev_index).multi_processor_count
+    except Exception:
+        pass
+    mhz = float(mp.get("sm_max_mhz", DEFAULT_SM_MHZ))
+    hbm = mp.get("hbm_gbs")
+    return {"sms": sms, "sm_max_mhz": mhz,
+            "fp32_tflops": sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12,
+            "fp64_tflops": sms * FP64_FMA_PER_SM * 2 * mhz * 1e6 / 1e12,
+            "hbm_gbs": float(hbm) if hbm else FALLBACK_HBM_GBS,
+            "hbm_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback 6.8 TB/s"}
 
 
 # ---------------------------------------------------------------- clocks
@@ -293,6 +328,9 @@ def ours_arm(args, world, rank, local):
 
     torch.cuda.set_device(local)
     pb, cfg, fp32 = workload(args.workload)
+    if args.precision != "auto":
+        fp32 = args.precision == "fp32"
+        cfg["precision"] = "fp32 bulk (fp64 reductions + accumulation)" if fp32 else "fp64"
     dev = torch.device("cuda", local)
     solver = wcns.Solver.for_problem(pb, precision=wcns.FP32 if fp32 else wcns.FP64, cfl=0.5)
     U = torch.from_numpy(pb.U0).to(dev)
@@ -324,22 +362,29 @@ def ours_arm(args, world, rank, local):
     evals = 3 * args.steps
     value = whole_job_rate(nodes, evals, world, el)
 
-    # dominant kernel: the fused sweep (all directions)
+    # dominant kernel: the fused sweep of one direction.  Algorithmic work of
+    # one launch: one face and one node difference per node (recomputed halo
+    # faces are implementation work, not counted), and 1/ndim of an RHS
+    # evaluation's bytes (read U once, write L once: 2 nv w per cell).
     nd = pb.ndim
+    pk = device_peaks(local)
     avg_ms = sweep_ms / max(1, sweep_n)
-    flops_launch = nodes * (FACE_FLOPS[nd] * (1.0 + 5.0 / 59.0) + NODE_FLOPS[nd])
+    flops_launch = nodes * (FACE_FLOPS[nd] + NODE_FLOPS[nd])
     achieved_tflops = flops_launch / (avg_ms / 1e3) / 1e12
-    peak = FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS
+    peak = pk["fp32_tflops"] if fp32 else pk["fp64_tflops"]
     traffic = profile_traffic("sweep") if fp32 else None
     w = 4 if fp32 else 8
+    bytes_launch = nodes * pb.nv * w * 2 / nd
     roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved_tflops / peak, "traffic": traffic,
                 "kernel": "sweep_kernel (fused interpolation+flux+MD, one direction)",
-                "peak_source": "derived: 152 SMs x %s x 2 x 2070 MHz" % ("128 FP32 lanes" if fp32 else "2 FP64 FMA/clk"),
-                "avg_launch_ms": avg_ms, "launches": sweep_n,
-                "hbm": {"algorithmic_bytes_per_launch": nodes * pb.nv * w * 2,
-                        "achieved_gbs": nodes * pb.nv * w * 2 / (avg_ms / 1e3) / 1e9,
-                        "peak_gbs": 6782.1, "frac": nodes * pb.nv * w * 2 / (avg_ms / 1e3) / 1e9 / 6782.1}}
+                "peak_source": "derived: %d SMs x %s x 2 flops x %.0f MHz" % (
+                    pk["sms"], "128 FP32 lanes" if fp32 else "2 FP64 FMA/clk", pk["sm_max_mhz"]),
+                "flops_per_launch": flops_launch, "avg_launch_ms": avg_ms, "launches": sweep_n,
+                "hbm": {"algorithmic_bytes_per_launch": bytes_launch,
+                        "achieved_gbs": bytes_launch / (avg_ms / 1e3) / 1e9,
+                        "peak_gbs": pk["hbm_gbs"], "peak_source": pk["hbm_source"],
+                        "frac": bytes_launch / (avg_ms / 1e3) / 1e9 / pk["hbm_gbs"]}}
 
     # e2e: public API with host buffers, copies inside the timed region
     Uh = torch.from_numpy(pb.U0.copy()).pin_memory()
@@ -620,6 +665,7 @@ def scalar_arm(args):
     t2_ms = e0.elapsed_time(e1)
     t2_err = float(np.max(np.abs(one.cpu().numpy() - u0)))
     achieved = value * SCALAR_NODE_FLOPS / 1e12
+    pk = device_peaks(0)
     cpu = None
     if not args.no_cpu:
         rate, secs, work = scalar_oracle_rate(h, u0, 10.0)
@@ -634,12 +680,13 @@ def scalar_arm(args):
                    "weights": "tcns", "rk3_steps_per_bench_step": k, "dt": "0.01 h",
                    "l2": "flushed (256 MiB write) between timed steps",
                    "launch": "one cluster launch per bench step (16-CTA clusters, line resident in DSMEM)"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
+                     "frac": achieved / pk["fp64_tflops"], "traffic": None,
                      "kernel": "scalar_kernel (whole run on chip)",
                      "flops_per_node_rhs": SCALAR_NODE_FLOPS,
-                     "peak_note": "FP64 FMA peak derived from 152 SMs x 2 FP64 FMA/clk x 2070 MHz; "
-                                  "the fixed-order path issues no FMA, so 0.5 is its ceiling"},
+                     "peak_note": "FP64 FMA peak derived from %d SMs x 2 FP64 FMA/clk x 2 flops x %.0f MHz; "
+                                  "the fixed-order path issues no FMA, so 0.5 is its ceiling" % (
+                                      pk["sms"], pk["sm_max_mhz"])},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
         "gpu_launches": args.steps, "clocks": clk,
@@ -696,8 +743,7 @@ def main():
             reference_arm(args, int(os.environ.get("WORLD_SIZE", "1")), 0)
         return
     world, rank, local = dist_setup()
-    if True:
-        ours_arm(args, world, rank, local)
+    ours_arm(args, world, rank, local)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

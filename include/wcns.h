@@ -204,8 +204,12 @@ wcns_status wcns_profile_read(wcns_handle* h, double* sweep_ms, long long* sweep
  * wcns_step_rk3, with the same results.  The stage state and right-hand
  * side live in one library-owned static device buffer of
  * WCNS_NOALLOC_SCRATCH_BYTES bytes, which every GPU that loads the library
- * holds until the process exits; grids needing more than
- * 2 * nv * N * 8 + 512 bytes of it are rejected with WCNS_ERR_INVALID.
+ * holds until the process exits.  The buffer holds a 512-byte header and
+ * two state-sized parts, each rounded up to 256 bytes, so a grid of N nodes
+ * fits when 512 + 2 * round_up(8 * nv * N, 256) <= WCNS_NOALLOC_SCRATCH_BYTES:
+ * at most 349,514 nodes in 1D, 262,136 in 2D and 209,708 in 3D.  Larger
+ * grids are rejected with WCNS_ERR_INVALID before any device work (the
+ * node count is checked axis by axis, so no product can overflow).
  * The first call on each device performs a one-time set-up there (the
  * buffer's device address, kernel attributes, a constant table); make that
  * first call before any stream capture.  All calls on one device share

@@ -9,6 +9,9 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <atomic>
+#include <mutex>
+
 #include "../../include/wcns.h"
 #include "wcns_internal.h"
 
@@ -23,8 +26,23 @@ namespace {
 
 constexpr size_t kHead = 512;   // StepScalars (256) + fallback counter (256)
 constexpr int kMaxDevices = 64;
-unsigned char* g_base[kMaxDevices];   // device address of the scratch, per device
-bool g_ready[kMaxDevices];
+// Per device: the scratch's device address, published by g_ready (release
+// store after the set-up, acquire load before use); g_setup serialises the
+// set-up itself, so host threads making their first call at once neither
+// race nor repeat it.
+unsigned char* g_base[kMaxDevices];
+std::atomic<bool> g_ready[kMaxDevices];
+std::mutex g_setup;
+
+size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Largest node count whose two state-sized parts fit behind the header:
+// kHead + 2 * round256(8 nv N) <= WCNS_NOALLOC_SCRATCH_BYTES.
+long long max_nodes(int nv)
+{
+    const size_t part = ((size_t)WCNS_NOALLOC_SCRATCH_BYTES - kHead) / 2 & ~(size_t)255;
+    return (long long)(part / ((size_t)nv * sizeof(double)));
+}
 
 wcns_status fail(wcns_status s, const char* msg)
 {
@@ -44,14 +62,16 @@ wcns_status cuda_fail(cudaError_t e, const char* where)
 // and the kernels' launch attributes.
 cudaError_t setup_device(int dev)
 {
-    if (g_ready[dev]) return cudaSuccess;
+    if (g_ready[dev].load(std::memory_order_acquire)) return cudaSuccess;
+    std::lock_guard<std::mutex> lock(g_setup);
+    if (g_ready[dev].load(std::memory_order_relaxed)) return cudaSuccess;
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
     e = prepare_sweeps_fp64();
     if (e != cudaSuccess) return e;
     g_base[dev] = static_cast<unsigned char*>(p);
-    g_ready[dev] = true;
+    g_ready[dev].store(true, std::memory_order_release);
     return cudaSuccess;
 }
 
@@ -72,6 +92,7 @@ extern "C" wcns_status wcns_step_rk3_noalloc(const wcns_grid* g, double gamma,
         return fail(WCNS_ERR_INVALID, "wcns_step_rk3_noalloc: periodic and transmissive boundaries only, no body force");
 
     const int nd = g->ndim, nv = nd + 2;
+    const long long cap = max_nodes(nv);
     int n[3] = {1, 1, 1}, periodic[3] = {0, 0, 0};
     double h[3] = {1, 1, 1}, inv_h[3] = {0, 0, 0};
     long long N = 1;
@@ -88,20 +109,19 @@ extern "C" wcns_status wcns_step_rk3_noalloc(const wcns_grid* g, double gamma,
         periodic[a] = per;
         h[a] = (g->hi[a] - g->lo[a]) / (per ? g->n[a] : g->n[a] - 1);
         inv_h[a] = 1.0 / h[a];
+        // checked before the product, so that no node count can overflow
+        if (N > cap / g->n[a]) {
+            char buf[256];
+            snprintf(buf, sizeof buf,
+                     "wcns_step_rk3_noalloc: the grid does not fit the static scratch buffer of %u bytes "
+                     "(at most %lld nodes for %d variables)",
+                     WCNS_NOALLOC_SCRATCH_BYTES, cap, nv);
+            return fail(WCNS_ERR_INVALID, buf);
+        }
         N *= g->n[a];
     }
     if (nd == 3 && (n[1] > 65535 || n[2] > 65535)) return fail(WCNS_ERR_INVALID, "grid too large");
     const size_t state_bytes = (size_t)nv * (size_t)N * sizeof(double);
-    const size_t need = kHead + 2 * ((state_bytes + 255) & ~(size_t)255);
-    if (need > WCNS_NOALLOC_SCRATCH_BYTES) {
-        char buf[256];
-        snprintf(buf, sizeof buf,
-                 "wcns_step_rk3_noalloc: grid needs %zu bytes of scratch, the static buffer holds %u "
-                 "(at most %lld nodes for %d variables)",
-                 need, WCNS_NOALLOC_SCRATCH_BYTES,
-                 (long long)((WCNS_NOALLOC_SCRATCH_BYTES - kHead - 512) / (2 * nv * sizeof(double))), nv);
-        return fail(WCNS_ERR_INVALID, buf);
-    }
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -116,7 +136,7 @@ extern "C" wcns_status wcns_step_rk3_noalloc(const wcns_grid* g, double gamma,
     StepScalars* sc = reinterpret_cast<StepScalars*>(base);
     long long* fallback = reinterpret_cast<long long*>(base + 256);
     double* L = reinterpret_cast<double*>(base + kHead);
-    double* U1 = reinterpret_cast<double*>(base + kHead + ((state_bytes + 255) & ~(size_t)255));
+    double* U1 = reinterpret_cast<double*>(base + kHead + round256(state_bytes));
     double* U0 = static_cast<double*>(U);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
 

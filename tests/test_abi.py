@@ -139,3 +139,20 @@ def test_noalloc_step_rejects_single_grid_features_without_a_gpu():
         else:
             g.bc[0][0] = g.bc[0][1] = wcns.BC_REFLECTING
         assert fn(C.byref(g), 1.4, C.byref(p), C.c_void_p(16), 0.0, None, None) == wcns.ERR_INVALID
+
+
+def test_noalloc_step_rejects_oversized_grids_without_a_gpu():
+    """The node count is checked axis by axis against the static buffer, so a
+    grid whose byte count would wrap around 2^64 is rejected, as is one node
+    more than fits (349,514 nodes in 1D, 262,136 in 2D, 209,708 in 3D)."""
+    L = wcns.lib()
+    fn = L.wcns_step_rk3_noalloc
+    fn.argtypes = [C.POINTER(wcns.Grid), C.c_double, C.POINTER(wcns.SchemeParams), C.c_void_p, C.c_double,
+                   C.POINTER(C.c_double), C.c_void_p]
+    p = wcns.default_params()
+    cases = [(2, (2 ** 30, 2 ** 29)), (3, (2 ** 21, 2 ** 21, 2 ** 21)), (3, (65536, 65536, 65536)),
+             (1, (349515,)), (2, (262137, 1)), (3, (209709, 1, 1))]
+    for nd, n in cases:
+        g = wcns.make_grid(nd, n + (1,) * (3 - nd), (0, 0, 0), (1, 1, 1), (0, 0, 0))
+        assert fn(C.byref(g), 1.4, C.byref(p), C.c_void_p(16), 0.0, None, None) == wcns.ERR_INVALID, n
+        assert b"scratch" in wcns.lib().wcns_last_error()
