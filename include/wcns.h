@@ -131,19 +131,25 @@ size_t wcns_handle_bytes(const wcns_handle* h);
  * same for the right-biased value; layout [d][k][line][j + 3], where lines
  * of direction d enumerate the other axes in (z, y, x) order, x fastest.
  * Faces whose interpolated state had rho <= 0 or p <= 0 use first-order
- * values and are counted (wcns_fallback_count).  Stream-ordered. */
+ * values and are counted (wcns_fallback_count).  Stream-ordered: the call
+ * does not wait for the device, so it cannot report such faces itself and
+ * returns WCNS_OK; read the count with wcns_fallback_count. */
 wcns_status wcns_rhs(wcns_handle* h, const void* U, void* L, uint8_t* flags, void* stream);
 
 /* Size in bytes of the flags array of wcns_rhs. */
 size_t wcns_flags_bytes(const wcns_handle* h);
 
 /* One SSP-RK3 step (Shu-Osher form) in place on the FP64 device state U
- * (double, nv * N; in FP32 mode the right-hand sides run in single precision
- * with compensated single-precision stage values and an FP64 final
- * combination).  dt > 0 uses that step; dt <= 0 computes
- * dt = cfl / max_i sum_d (|u_d| + c)/h_d in FP64 on the device.  If dt_used
- * is non-NULL the call copies the step to the host and synchronises the
- * stream; otherwise nothing is synchronised.  With dt <= 0 (and profiling
+ * (double, nv * N).  In FP32 mode the right-hand sides run in single
+ * precision and each stage value is the FP64 base state U^n plus an FP32
+ * increment (D1 = dt L, D2 = (D1 + dt L)/4, U^(n+1) = U^n + 2/3 (D2 + dt L),
+ * the last sum accumulated in FP64).  dt > 0 uses that step; dt <= 0
+ * computes dt = cfl / max_i sum_d (|u_d| + c)/h_d on the device (FP64
+ * maximum).  If dt_used is non-NULL the call copies the step to the host,
+ * synchronises the stream and returns WCNS_ERR_NONPHYSICAL (with the step
+ * completed) when faces fell back to first-order values during it;
+ * otherwise nothing is synchronised and the status does not report such
+ * faces (see wcns_fallback_count).  With dt <= 0 (and profiling
  * off) the step's launches are captured once per state pointer U as a CUDA
  * graph on an internal stream and replayed on `stream` afterwards; passing
  * another U, or changing the tile configuration, captures again. */
@@ -153,7 +159,10 @@ wcns_status wcns_step_rk3(wcns_handle* h, void* U, double dt, double* dt_used, v
  * last one clipped to land on t_end, or until max_steps.  The time and step
  * size stay on the device; the host loop checks completion every `check`
  * steps (one small device-to-host read).  Writes the reached time and the
- * number of steps.  Synchronises the stream before returning.  Each step
+ * number of steps.  Synchronises the stream before returning.  Returns
+ * WCNS_ERR_NONPHYSICAL, with the run completed and the outputs written, when
+ * faces had rho <= 0 or p <= 0 and used first-order values during the call
+ * (wcns_fallback_count gives the number).  Each step
  * replays a captured CUDA graph (per state pointer, as for wcns_step_rk3). */
 wcns_status wcns_advance(wcns_handle* h, void* U, double t_end, int max_steps, int check,
                          double* t_out, int* steps_out, void* stream);
@@ -261,7 +270,10 @@ wcns_status wcns_batch_step(wcns_batch* b, int nsteps, int* active, void* stream
 wcns_status wcns_batch_run(wcns_batch* b, int max_steps, int check, int* steps, void* stream);
 
 /* Copy an instance's FP64 state (host pointer, or device when out_on_device;
- * nullable) and return its time and step count.  Synchronises the stream. */
+ * nullable) and return its time and step count.  Synchronises the stream.
+ * Returns WCNS_ERR_NONPHYSICAL, with every output written, when faces of
+ * this instance had rho <= 0 or p <= 0 and used first-order values since
+ * it was added (each instance has its own counter). */
 wcns_status wcns_batch_read(wcns_batch* b, int slot, double* U_out, int out_on_device, double* t,
                             int* steps, void* stream);
 
@@ -300,7 +312,10 @@ typedef struct {
 
 typedef struct {
     uint64_t ticket, tag;
-    wcns_status status;           /* WCNS_OK, or why the request failed         */
+    wcns_status status;           /* WCNS_OK; WCNS_ERR_NONPHYSICAL when faces of
+                                     this request fell back to first-order values
+                                     (the state is still returned); otherwise
+                                     why the request failed                    */
     int ndim, n[3], precision;
     double t;                     /* time reached (t_end)                      */
     int steps;                    /* RK3 steps taken                           */

@@ -369,6 +369,12 @@ wcns_status wcns_step_rk3(wcns_handle* h, void* U, double dt, double* dt_used, v
     if (!h || !U) return fail(WCNS_ERR_INVALID, "wcns_step_rk3: null argument");
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaGetLastError(), "pending CUDA error");
+    // a synchronising step reports faces that fell back during it
+    long long before = 0;
+    if (dt_used) {
+        CK(cudaMemcpyAsync(&before, h->fallback, sizeof before, cudaMemcpyDeviceToHost, s), "counter copy");
+        CK(cudaStreamSynchronize(s), "sync");
+    }
     if (!(dt > 0.0) && !h->profiling && step_graph(h, 0, U)) {
         CK(cudaGraphLaunch(h->graph[0], s), "step graph");
     } else {
@@ -378,8 +384,13 @@ wcns_status wcns_step_rk3(wcns_handle* h, void* U, double dt, double* dt_used, v
         CK(run_stages(h, (double*)U, s, !(dt > 0.0)), "rk3 stages");
     }
     if (dt_used) {
+        long long after = 0;
         CK(cudaMemcpyAsync(dt_used, &h->sc->dt, sizeof(double), cudaMemcpyDeviceToHost, s), "dt copy");
+        CK(cudaMemcpyAsync(&after, h->fallback, sizeof after, cudaMemcpyDeviceToHost, s), "counter copy");
         CK(cudaStreamSynchronize(s), "sync");
+        if (after > before)
+            return fail(WCNS_ERR_NONPHYSICAL, "wcns_step_rk3: %lld faces had rho <= 0 or p <= 0 and used "
+                        "first-order values", after - before);
     }
     return WCNS_OK;
 }
@@ -394,6 +405,9 @@ wcns_status wcns_advance(wcns_handle* h, void* U, double t_end, int max_steps, i
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaGetLastError(), "pending CUDA error");
     CK(reset_clock(h, t_end, s), "reset clock");
+    long long before = 0, after = 0;
+    CK(cudaMemcpyAsync(&before, h->fallback, sizeof before, cudaMemcpyDeviceToHost, s), "counter copy");
+    CK(cudaStreamSynchronize(s), "sync");
     long long issued = 0;
     StepScalars cur{};
     while (issued < max_steps) {
@@ -410,11 +424,15 @@ wcns_status wcns_advance(wcns_handle* h, void* U, double t_end, int max_steps, i
         }
         issued += batch;
         CK(cudaMemcpyAsync(&cur, h->sc, sizeof cur, cudaMemcpyDeviceToHost, s), "clock copy");
+        CK(cudaMemcpyAsync(&after, h->fallback, sizeof after, cudaMemcpyDeviceToHost, s), "counter copy");
         CK(cudaStreamSynchronize(s), "sync");
         if (cur.t >= t_end) break;
     }
     if (t_out) *t_out = cur.t;
     if (steps_out) *steps_out = (int)cur.steps;
+    if (after > before)
+        return fail(WCNS_ERR_NONPHYSICAL, "wcns_advance: %lld faces had rho <= 0 or p <= 0 and used "
+                    "first-order values", after - before);
     return WCNS_OK;
 }
 

@@ -461,7 +461,7 @@ wcns_status wcns_batch_create(int ndim, double gamma, const wcns_scheme_params* 
     const size_t w = fp32 ? 4 : 8;
     const size_t M = (size_t)b->cap_elems;
     b->bytes = M * 8 + M * w * 2 + (fp32 ? M * 8 : 0) + sizeof(StepScalars) * max_instances +
-               (sizeof(BatchInst) + sizeof(int)) * max_instances + 64;
+               (sizeof(BatchInst) + sizeof(int) + sizeof(long long)) * max_instances + 64;
     e = cudaMalloc((void**)&b->U, M * 8);
     if (e == cudaSuccess) e = cudaMalloc(&b->S, M * w);
     if (e == cudaSuccess) e = cudaMalloc(&b->L, M * w);
@@ -469,11 +469,11 @@ wcns_status wcns_batch_create(int ndim, double gamma, const wcns_scheme_params* 
     if (e == cudaSuccess && fp32) e = cudaMalloc((void**)&b->S2, M * 4);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->sc, sizeof(StepScalars) * max_instances);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->active, 64);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->fallback, 64);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->fallback, sizeof(long long) * max_instances);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_insts, sizeof(BatchInst) * max_instances);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_slots, sizeof(int) * max_instances);
     if (e == cudaSuccess) e = cudaMemset(b->sc, 0, sizeof(StepScalars) * max_instances);
-    if (e == cudaSuccess) e = cudaMemset(b->fallback, 0, 64);
+    if (e == cudaSuccess) e = cudaMemset(b->fallback, 0, sizeof(long long) * max_instances);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         const size_t need = b->bytes;
@@ -561,6 +561,7 @@ wcns_status wcns_batch_add(wcns_batch* b, const wcns_grid* g, const double* U0, 
                         u0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st), "initial state copy");
     set_clock_kernel<<<1, 1, 0, st>>>(b->sc + slot, t_end);
     BCK(cudaGetLastError(), "clock set");
+    BCK(cudaMemsetAsync(b->fallback + slot, 0, sizeof(long long), st), "fallback counter reset");
     b->slots[slot] = s;
     b->dirty = true;
     *slot_out = slot;
@@ -646,10 +647,15 @@ wcns_status wcns_batch_read(wcns_batch* b, int slot, double* U_out, int out_on_d
         BCK(cudaMemcpyAsync(U_out, b->U + s.off, sizeof(double) * b->nv * s.N,
                             out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st), "state copy");
     StepScalars sc;
+    long long fell = 0;
     BCK(cudaMemcpyAsync(&sc, b->sc + slot, sizeof sc, cudaMemcpyDeviceToHost, st), "clock copy");
+    BCK(cudaMemcpyAsync(&fell, b->fallback + slot, sizeof fell, cudaMemcpyDeviceToHost, st), "counter copy");
     BCK(cudaStreamSynchronize(st), "sync");
     if (t_out) *t_out = sc.t;
     if (steps_out) *steps_out = (int)sc.steps;
+    if (fell > 0)
+        return bfail(WCNS_ERR_NONPHYSICAL, "instance %d: %lld faces had rho <= 0 or p <= 0 and used first-order values",
+                     slot, fell);
     return WCNS_OK;
 }
 

@@ -55,7 +55,8 @@ struct SweepArgs {
     double inv_h;             // 1 / h_DIR
     int accumulate;           // 0: L = -f'   1: L -= f'
     uint8_t* flags;           // nullable debug output, block of this direction
-    long long* fallback;      // count of first-order fallback faces
+    long long* fallback;      // count of first-order fallback faces (batched
+                              // mode: one counter per instance, indexed by it)
     const double* dt;         // nullable: skip all work when *dt == 0 (finished)
     SchemeConst K;
     float sqrt_eps_f;         // sqrt(eps) in float, for the FP32 rescaled eps
@@ -368,6 +369,7 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) swee
     int nx, ny, nd, periodic, pos0, lfirst;
     long long outer;
     const double* dtp;
+    long long* fbp = a.fallback;
     T ih;
     double* U0b = a.U0;
     float* Db = a.D;
@@ -393,6 +395,7 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) swee
         lfirst = bt.lfirst;
         outer = bt.outer;
         dtp = a.inst_dt + (long long)bt.inst * a.dt_stride;
+        fbp = a.fallback + bt.inst;
     } else {
         Ub = reinterpret_cast<const LT*>(a.U);
         Lb = reinterpret_cast<T*>(a.L);
@@ -562,7 +565,7 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) swee
                 a.flags[((long long)k * lines + line0 + l) * (nd + 5) + j3] = fl[k];
         }
     }
-    if (fb) atomicAdd((unsigned long long*)a.fallback, (unsigned long long)fb);
+    if (fb) atomicAdd((unsigned long long*)fbp, (unsigned long long)fb);
     if constexpr (kPre) cp_async_wait<0>();    // prefetched L has landed
     __syncthreads();
 

@@ -83,6 +83,15 @@ def check(status):
         raise WcnsError(status, lib().wcns_last_error().decode())
 
 
+def check_physical(status):
+    """Like check(), but WCNS_ERR_NONPHYSICAL (the call completed; some faces
+    used first-order values) is returned as True instead of raised."""
+    if status == ERR_NONPHYSICAL:
+        return True
+    check(status)
+    return False
+
+
 def default_params(**kw):
     p = SchemeParams()
     lib().wcns_default_params(C.byref(p))
@@ -148,6 +157,8 @@ class Solver:
         h = C.c_void_p()
         check(lib().wcns_create(C.byref(self.grid), gamma, C.byref(self.params), C.byref(h)))
         self.h = h
+        # set when a synchronising step or advance reported first-order faces
+        self.nonphysical = False
 
     @classmethod
     def for_problem(cls, pb, **params):
@@ -178,15 +189,19 @@ class Solver:
 
     def step(self, U, dt=0.0, want_dt=False, stream=None):
         d = C.c_double()
-        check(lib().wcns_step_rk3(self.h, _ptr(U), float(dt), C.byref(d) if want_dt else None,
-                                  _stream(stream)))
+        st = lib().wcns_step_rk3(self.h, _ptr(U), float(dt), C.byref(d) if want_dt else None,
+                                 _stream(stream))
+        self.nonphysical |= check_physical(st)
         return d.value if want_dt else None
 
     def advance(self, U, t_end, max_steps=10 ** 9, check_every=64, stream=None):
+        """Returns (t reached, steps); sets self.nonphysical when faces fell
+        back to first-order values during the run."""
         t = C.c_double()
         s = C.c_int()
-        check(lib().wcns_advance(self.h, _ptr(U), float(t_end), int(min(max_steps, 2 ** 31 - 1)),
-                                 int(check_every), C.byref(t), C.byref(s), _stream(stream)))
+        st = lib().wcns_advance(self.h, _ptr(U), float(t_end), int(min(max_steps, 2 ** 31 - 1)),
+                                int(check_every), C.byref(t), C.byref(s), _stream(stream))
+        self.nonphysical |= check_physical(st)
         return t.value, s.value
 
     def conserved(self, U, stream=None):
@@ -329,6 +344,7 @@ class Batch:
         check(L.wcns_batch_create(ndim, gamma, C.byref(self.params), int(max_nodes), int(max_instances), C.byref(h)))
         self.h = h
         self.grids = {}
+        self.nonphysical = {}   # slot -> True when its read reported first-order faces
 
     def close(self):
         if getattr(self, "h", None):
@@ -386,10 +402,12 @@ class Batch:
         shape = (nd + 2,) + tuple(reversed(n))
         if out is None:
             host = np.empty(shape, dtype=np.float64)
-            check(lib().wcns_batch_read(self.h, int(slot), host.ctypes.data_as(C.c_void_p), 0, C.byref(t),
-                                        C.byref(st), _stream(stream)))
-            return host, t.value, st.value
-        check(lib().wcns_batch_read(self.h, int(slot), _ptr(out), 1, C.byref(t), C.byref(st), _stream(stream)))
+            r = lib().wcns_batch_read(self.h, int(slot), host.ctypes.data_as(C.c_void_p), 0, C.byref(t),
+                                      C.byref(st), _stream(stream))
+            out = host
+        else:
+            r = lib().wcns_batch_read(self.h, int(slot), _ptr(out), 1, C.byref(t), C.byref(st), _stream(stream))
+        self.nonphysical[slot] = check_physical(r)
         return out, t.value, st.value
 
 

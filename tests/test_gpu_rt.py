@@ -114,16 +114,15 @@ def test_rayleigh_taylor_run_bit_identical_to_oracle():
     s.close()
 
 
-def test_rayleigh_taylor_fp32_close_to_fp64_and_symmetric():
+def test_rayleigh_taylor_fp32_close_to_oracle_and_symmetric():
     pb = inputs.rayleigh_taylor(32)
-    out = {}
-    for prec in (wcns.FP64, wcns.FP32):
-        s = wcns.Solver.for_problem(pb, precision=prec, cfl=0.5)
-        Ud = torch.from_numpy(pb.U0.copy()).to(DEV)
-        s.advance(Ud, 0.3, check_every=16)
-        out[prec] = Ud.cpu().numpy()
-        s.close()
-    a, b = out[wcns.FP64], out[wcns.FP32]
+    a = pb.U0.copy()
+    O.euler_run(ora_cfg(pb, "roe"), a, 0.5, 0.3)
+    s = wcns.Solver.for_problem(pb, precision=wcns.FP32, cfl=0.5)
+    Ud = torch.from_numpy(pb.U0.copy()).to(DEV)
+    s.advance(Ud, 0.3, check_every=16)
+    b = Ud.cpu().numpy()
+    s.close()
     rel = np.sum(np.abs(b - a), axis=(1, 2)) / np.sum(np.abs(a), axis=(1, 2))
     assert rel[0] <= 1e-5 and rel[3] <= 1e-5, rel
     # the x -> 1/4 - x mirror image of the density: rounding seeds asymmetry

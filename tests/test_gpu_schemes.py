@@ -1,7 +1,7 @@
 """GPU parity of the alternative schemes through the C ABI: the AUSM midpoint
 flux and the HWCNS / MND differences (Eq. 4-5), alone and combined with the
 other weights, in the FP64 path (bit-identical to the oracle), the FP32 path
-(bounded error against the FP64 path), batches and the scalar solver.
+(bounded error against the oracle), batches and the scalar solver.
 """
 import numpy as np
 import pytest
@@ -91,16 +91,17 @@ def test_fp64_sod_end_state_bit_identical(flux, diff):
 
 
 @pytest.mark.parametrize("flux,diff", [("ausm", "md"), ("roe", "hwcns"), ("roe", "mnd"), ("ausm", "mnd")])
-def test_fp32_rhs_close_to_fp64(flux, diff):
-    """Smooth flow: |L32 - L64| <= 2e-6 (|L64| + S_v), S_v the flux scale of
-    variable v (sum over directions of max (|F_v| + c |U_v|) / h): the MD
-    and node differences subtract fluxes of that size, so FP32 rounding in
-    them appears divided by h (the bound of the default scheme's test)."""
+def test_fp32_rhs_close_to_oracle(flux, diff):
+    """Smooth flow: |L32 - Lo| <= 2e-6 (|Lo| + S_v) against the FP64 oracle,
+    S_v the flux scale of variable v (sum over directions of
+    max (|F_v| + c |U_v|) / h): the MD and node differences subtract fluxes of
+    that size, so FP32 rounding in them appears divided by h (the bound of the
+    default scheme's test)."""
     for pb in (inputs.taylor_green(24), inputs.density_wave_1d(64)):
-        L64 = _gpu_rhs(pb, pb.U0, flux, diff)[0]
+        Lo = O.euler_rhs(_cfg(pb, flux, diff), pb.U0)[0]
         L32 = _gpu_rhs(pb, pb.U0, flux, diff, precision=wcns.FP32)[0]
         S = _flux_scale(pb.U0, pb).reshape((-1,) + (1,) * pb.ndim)
-        rel = np.max(np.abs(L32 - L64) / (np.abs(L64) + S))
+        rel = np.max(np.abs(L32 - Lo) / (np.abs(Lo) + S))
         assert rel < 2e-6, (pb.name, rel)
 
 
@@ -122,16 +123,15 @@ def _flux_scale(U, pb):
 
 
 @pytest.mark.parametrize("flux,diff", [("ausm", "md"), ("roe", "mnd")])
-def test_fp32_sod_end_state_close_to_fp64(flux, diff):
+def test_fp32_sod_end_state_close_to_oracle(flux, diff):
     pb = inputs.shock_tube(400)
-    out = {}
-    for prec in (wcns.FP64, wcns.FP32):
-        s = wcns.Solver.for_problem(pb, flux=FLUX[flux][0], diff=DIFF[diff][0], precision=prec, cfl=0.5)
-        Ud = torch.from_numpy(pb.U0.copy()).to(DEV)
-        s.advance(Ud, 0.2, check_every=16)
-        out[prec] = Ud.cpu().numpy()
-        s.close()
-    rel = np.sum(np.abs(out[wcns.FP32] - out[wcns.FP64]), axis=1) / np.sum(np.abs(out[wcns.FP64]), axis=1)
+    Uo = pb.U0.copy()
+    O.euler_run(_cfg(pb, flux, diff), Uo, 0.5, 0.2)
+    s = wcns.Solver.for_problem(pb, flux=FLUX[flux][0], diff=DIFF[diff][0], precision=wcns.FP32, cfl=0.5)
+    Ud = torch.from_numpy(pb.U0.copy()).to(DEV)
+    s.advance(Ud, 0.2, check_every=16)
+    s.close()
+    rel = np.sum(np.abs(Ud.cpu().numpy() - Uo), axis=1) / np.sum(np.abs(Uo), axis=1)
     assert np.all(rel <= 1e-3), rel
 
 
@@ -150,10 +150,13 @@ def test_batch_with_ausm_and_mnd_equals_batch_of_one(precision):
         b1.run(check_every=32)
         assert np.array_equal(b1.read(k)[0], U)
         b1.close()
+        Uo = pb.U0.copy()
+        O.euler_run(_cfg(pb, "ausm", "mnd"), Uo, 0.5, 0.05)
         if precision == wcns.FP64:
-            Uo = pb.U0.copy()
-            O.euler_run(_cfg(pb, "ausm", "mnd"), Uo, 0.5, 0.05)
             assert np.array_equal(U, Uo)
+        else:
+            rel = np.sum(np.abs(U - Uo), axis=1) / np.sum(np.abs(Uo), axis=1)
+            assert np.all(rel <= 1e-3), rel
 
 
 @pytest.mark.parametrize("diff", ["hwcns", "mnd"])
@@ -174,18 +177,19 @@ def test_scalar_path_with_eq4_eq5_bit_identical(kind, diff):
 
 
 @pytest.mark.parametrize("weights", ["js", "linear", "z"])
-def test_fp32_comparison_weights_close_to_fp64(weights):
+def test_fp32_comparison_weights_close_to_oracle(weights):
     """FP32 single grids with the comparison weights (rescaled indicators):
-    smooth flow within the same flux-scale bound as TENO; flags report
-    all stencils kept."""
+    smooth flow within the same flux-scale bound as TENO against the FP64
+    oracle; flags report all stencils kept."""
     wg = {"z": wcns.W_Z, "js": wcns.W_JS, "linear": wcns.W_LINEAR}[weights]
+    wo = {"z": O.W_Z, "js": O.W_JS, "linear": O.W_LINEAR}[weights]
     for pb in (inputs.taylor_green(24), inputs.density_wave_1d(64), inputs.four_quadrant(40, ny=33)):
         for flux in ("roe", "ausm"):
-            L64 = _gpu_rhs(pb, pb.U0, flux, "md", weights=wg)[0]
+            Lo = O.euler_rhs(_cfg(pb, flux, "md", wo), pb.U0)[0]
             L32, fl32, _ = _gpu_rhs(pb, pb.U0, flux, "md", precision=wcns.FP32, weights=wg)
             assert np.all(fl32 == 0x3F)
             S = _flux_scale(pb.U0, pb).reshape((-1,) + (1,) * pb.ndim)
-            rel = np.max(np.abs(L32 - L64) / (np.abs(L64) + S))
+            rel = np.max(np.abs(L32 - Lo) / (np.abs(Lo) + S))
             bound = 2e-6 if pb.name != "four_quadrant" else 2e-5
             assert rel < bound, (pb.name, flux, rel)
 
@@ -193,15 +197,15 @@ def test_fp32_comparison_weights_close_to_fp64(weights):
 @pytest.mark.parametrize("weights", ["js", "z"])
 def test_fp32_comparison_weights_sod_end_state(weights):
     wg = {"z": wcns.W_Z, "js": wcns.W_JS}[weights]
+    wo = {"z": O.W_Z, "js": O.W_JS}[weights]
     pb = inputs.shock_tube(400)
-    out = {}
-    for prec in (wcns.FP64, wcns.FP32):
-        s = wcns.Solver.for_problem(pb, weights=wg, precision=prec, cfl=0.5)
-        Ud = torch.from_numpy(pb.U0.copy()).to(DEV)
-        s.advance(Ud, 0.2, check_every=16)
-        out[prec] = Ud.cpu().numpy()
-        s.close()
-    rel = np.sum(np.abs(out[wcns.FP32] - out[wcns.FP64]), axis=1) / np.sum(np.abs(out[wcns.FP64]), axis=1)
+    Uo = pb.U0.copy()
+    O.euler_run(_cfg(pb, "roe", "md", wo), Uo, 0.5, 0.2)
+    s = wcns.Solver.for_problem(pb, weights=wg, precision=wcns.FP32, cfl=0.5)
+    Ud = torch.from_numpy(pb.U0.copy()).to(DEV)
+    s.advance(Ud, 0.2, check_every=16)
+    s.close()
+    rel = np.sum(np.abs(Ud.cpu().numpy() - Uo), axis=1) / np.sum(np.abs(Uo), axis=1)
     assert np.all(rel <= 1e-4), rel
 
 

@@ -1,12 +1,14 @@
 """GPU tests of the serving loop (wcns_batch_submit / wcns_serve_poll):
 requests that arrive while others run are admitted as slots and memory free
 up, overlap on the device, and each result equals the same problem solved
-alone (bit for bit, in FP64 and in FP32)."""
+alone (bit for bit, in FP64 and in FP32) and the FP64 oracle's solution
+(FP64: within 1e-10 L1; FP32: within a stated relative L1 bound)."""
 import time
 
 import numpy as np
 import pytest
 
+from oracle import oracle as O
 from paper_1810_07806_gb300 import inputs
 
 torch = pytest.importorskip("torch")
@@ -50,6 +52,26 @@ def _drain(sv, expected, timeout_s=120):
     return got
 
 
+def _check_against_oracle(pb, prec, r):
+    """The served end state against the FP64 oracle's run of the same
+    request: FP64 within 1e-10 mean absolute difference per variable and the
+    same number of steps; FP32 within 1e-4 relative L1 per variable (the
+    momenta measured against the larger momentum total)."""
+    cfg = O.make_cfg(ndim=pb.ndim, n=pb.n, h=pb.h, periodic=pb.periodic, gamma=pb.gamma)
+    Uo = pb.U0.copy()
+    t_o, steps_o, _ = O.euler_run(cfg, Uo, 0.5, pb.t_end)
+    U = r["U"].reshape(pb.nv, -1)
+    Uo = Uo.reshape(pb.nv, -1)
+    if prec == wcns.FP64:
+        assert r["steps"] == steps_o and r["t"] == t_o
+        assert np.all(np.mean(np.abs(U - Uo), axis=1) <= 1e-10)
+    else:
+        tot = np.sum(np.abs(Uo), axis=1)
+        tot[1:-1] = tot[1:-1].max()
+        rel = np.sum(np.abs(U - Uo), axis=1) / tot
+        assert np.all(rel <= 1e-4), rel
+
+
 def test_served_results_equal_each_problem_alone():
     reqs = _requests(1, 10)
     sv = wcns.Server(hbm_budget_bytes=1 << 30, max_instances_per_class=8, steps_per_tick=4)
@@ -67,6 +89,7 @@ def test_served_results_equal_each_problem_alone():
         assert r["t"] == ta == pb.t_end and r["steps"] == sa
         assert np.array_equal(r["U"], Ua)
         assert r["t_submit"] <= r["t_admit"] <= r["t_done"]
+        _check_against_oracle(pb, prec, r)
     st = sv.stats()
     assert st["completed"] == len(reqs) and st["queued"] == 0
     sv.close()
@@ -86,6 +109,7 @@ def test_admission_waits_for_memory_and_slots():
     assert st["max_running"] <= 2
     assert st["max_queue"] >= 1
     Ua, _, _ = _alone(reqs[0][0], wcns.FP64)
+    _check_against_oracle(reqs[0][0], wcns.FP64, got[0])
     for k in range(len(reqs)):
         assert got[k]["status"] == wcns.OK
         assert np.array_equal(got[k]["U"], Ua)
