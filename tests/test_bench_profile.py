@@ -15,17 +15,20 @@ def _copy_tree(tmp_path):
     dst.mkdir(parents=True)
     for f in FILES:
         shutil.copy(os.path.join(src, f), dst / f)
-    prof = tmp_path / "profiles"
-    prof.mkdir()
-    shutil.copy(os.path.join(bench.ROOT, "profiles", "sweep_fp32_tgv.md"), prof / "sweep_fp32_tgv.md")
     return dst
 
 
 def test_comment_edit_keeps_and_code_edit_voids_the_profile(tmp_path, monkeypatch):
+    """A summary written for the current code is used; a comment edit keeps
+    it, a code edit voids it."""
     csrc = _copy_tree(tmp_path)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     h0 = bench.kernel_source_hash()
-    assert bench.profile_traffic("sweep") is not None
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "sweep_fp32_tgv.md").write_text(
+        "kernel_source_sha256: %s\ntraffic_bytes_per_full_launch: 1.5e9\n" % h0)
+    assert bench.profile_traffic("sweep") == 1.5e9
     f = csrc / "wcns_sweep.cuh"
     src = f.read_text()
     f.write_text(src + "\n// a comment\n\n")
