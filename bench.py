@@ -60,6 +60,9 @@ def parse():
                     choices=["tgv256", "tgv192", "quad1024", "sod400", "rt1024", "batch1d", "serve", "scalar"])
     ap.add_argument("--requests", type=int, default=32, help="serve: requests replayed from the trace")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrival rate (1/s)")
+    ap.add_argument("--side-lo", type=int, default=128, help="serve: smallest grid side")
+    ap.add_argument("--side-hi", type=int, default=1024, help="serve: largest grid side")
+    ap.add_argument("--no-serve", action="store_true", help="skip the short serving replay of the default line")
     ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "fp64"],
                     help="single-grid workloads: the path timed (auto: the workload's default)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain-path line")
@@ -386,24 +389,20 @@ def ours_arm(args, world, rank, local):
                         "peak_gbs": pk["hbm_gbs"], "peak_source": pk["hbm_source"],
                         "frac": bytes_launch / (avg_ms / 1e3) / 1e9 / pk["hbm_gbs"]}}
 
-    # e2e: public API with host buffers, copies inside the timed region
+    # e2e: the C-ABI call on a HOST state (wcns_step_rk3_host copies it in,
+    # steps, copies it out and synchronises), one call per step
     Uh = torch.from_numpy(pb.U0.copy()).pin_memory()
     e2e_steps = max(1, min(args.steps, 10))
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
+    solver.step_host(Uh)            # first call: the device copy and the step graph
     torch.cuda.synchronize()
-    ev0.record()
+    t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        U.copy_(Uh, non_blocking=True)
-        solver.step(U)
-        Uh.copy_(U, non_blocking=True)
-    ev1.record()
-    torch.cuda.synchronize()
-    e2e_el = ev0.elapsed_time(ev1) / 1e3
+        solver.step_host(Uh)
+    e2e_el = time.perf_counter() - t0
     e2e_el = max_over_ranks(e2e_el, world, dev)
     nbytes = U.numel() * U.element_size()
     e2e = {"value": whole_job_rate(nodes, 3 * e2e_steps, world, e2e_el), "unit": UNIT, "h2d_bytes_per_step": nbytes,
-           "d2h_bytes_per_step": nbytes, "steps": e2e_steps}
+           "d2h_bytes_per_step": nbytes, "steps": e2e_steps, "call": "wcns_step_rk3_host (pinned host state)"}
 
     # the FP64 plain path on the same workload
     fp64_line = None
@@ -454,6 +453,21 @@ def ours_arm(args, world, rank, local):
                   "mirror_asymmetry_max": float((rho - rho.flip(1)).abs().max())}
         del Ur
 
+    # a short bounded replay of the serving configuration (four-quadrant
+    # requests, Poisson arrivals at 200/s, half FP32), smaller sides than the
+    # full trace so that it takes seconds: served vs the plain path
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serve and args.workload == "tgv256":
+        from paper_1810_07806_gb300 import inputs
+        trace = inputs.serving_trace(SERVE_SHORT["requests"], rate=SERVE_SHORT["rate"],
+                                     side_lo=SERVE_SHORT["side_lo"], side_hi=SERVE_SHORT["side_hi"])
+        served = serve_replay(trace)
+        plain = plain_replay(trace)
+        serving = {"workload": "serving_four_quadrant_2d_trace (bounded sample: %d requests, side log-uniform "
+                               "%d..%d, t_end U[0.1,0.3], 200 req/s, seed 7806, half FP32)" % (
+                                   SERVE_SHORT["requests"], SERVE_SHORT["side_lo"], SERVE_SHORT["side_hi"]),
+                   **serving_summary(trace, served, plain)}
+
     launches = solver.launches_per_step(True) * args.steps
     if rank == 0:
         cfg.update({"global_batch": world, "parallelism": "replicas x%d" % world, "tile_configs": tiles,
@@ -465,6 +479,7 @@ def ours_arm(args, world, rank, local):
             "data": "synthetic", "config": cfg, "roofline": roofline, "cpu_baseline": cpu,
             "e2e": e2e, "gpu_launches": launches, "clocks": clk, "fp64_plain": fp64_line,
             **({"rt_run": rt_run} if rt_run else {}),
+            **({"serving": serving} if serving else {}),
         }))
     solver.close()
 
@@ -532,20 +547,16 @@ def batch_arm(args):
         "batched_fp64": out["fp64"], "plain_fp64_one_instance_per_launch": out["plain_fp64"]}))
 
 
-def serve_arm(args):
-    """Serving: a seeded Poisson trace of four-quadrant Riemann requests (side
-    log-uniform 128..1024, t_end U[0.1, 0.3], half FP32 / half FP64) replayed
-    in real time against one server; latency = result ready - arrival."""
-    import numpy as np
-    from paper_1810_07806_gb300 import inputs, wcns
-    trace = inputs.serving_trace(args.requests, rate=args.rate)
-    sv = wcns.Server(hbm_budget_bytes=64 << 30, max_instances_per_class=64, steps_per_tick=16)
+def serve_replay(trace, steps_per_tick=16):
+    """Replays a serving trace in real time against one server: each request
+    is submitted at its arrival time, results are polled as they finish.
+    Returns per-request results (state, steps, status, latency = result
+    ready - arrival), the wall time, queue depths and server statistics."""
+    from paper_1810_07806_gb300 import wcns
+    sv = wcns.Server(hbm_budget_bytes=64 << 30, max_instances_per_class=64, steps_per_tick=steps_per_tick)
     t0 = time.perf_counter()
-    arrivals = {}
-    work = {}
-    got = {}
+    arrivals, work, got, qdepth = {}, {}, {}, []
     k = 0
-    qdepth = []
     while len(got) < len(trace):
         now = time.perf_counter() - t0
         while k < len(trace) and trace[k].arrival_s <= now:
@@ -557,26 +568,125 @@ def serve_arm(args):
             k += 1
         for res in sv.poll(64, timeout_us=2000):
             res["ready"] = time.perf_counter() - t0
+            res["latency"] = res["ready"] - arrivals[res["tag"]]
             got[res["tag"]] = res
         qdepth.append(sv.stats()["queued"])
     total = time.perf_counter() - t0
-    lat = np.array([got[i]["ready"] - arrivals[i] for i in range(len(trace))])
-    cells = sum(work[i] * 3 * got[i]["steps"] for i in range(len(trace)))
     st = sv.stats()
     sv.close()
+    cells = sum(work[i] * 3 * got[i]["steps"] for i in range(len(trace)))
+    return {"results": [got[i] for i in range(len(trace))], "wall_s": total, "cell_updates": cells,
+            "max_queue": int(max(qdepth) if qdepth else 0), "stats": st}
+
+
+def plain_replay(trace, fp64_reference=True):
+    """The plain baseline on the same trace: one request at a time, in arrival
+    order, each solved alone by the single-grid path in its own precision
+    (host state in, wcns_advance, host state out).  Latencies are those of a
+    first-come first-served queue in front of it: finish_i = max(arrival_i,
+    finish_(i-1)) + solve_i, with the measured solve times.  With
+    fp64_reference, the FP64 solution of every FP32 request (the FP64 path
+    equals the oracle bit for bit) is computed too, for the FP32 error."""
+    import torch
+    from paper_1810_07806_gb300 import wcns
+    out, ref = [], {}
+    finish = 0.0
+    cells = 0
+    busy = 0.0
+    for k, r in enumerate(trace):
+        pb = r.problem()
+        t0 = time.perf_counter()
+        s = wcns.Solver.for_problem(pb, precision=wcns.FP32 if r.fp32 else wcns.FP64, cfl=0.5)
+        U = torch.from_numpy(pb.U0.copy()).cuda()
+        _, steps = s.advance(U, r.t_end, check_every=64)
+        Uh = U.cpu().numpy()
+        solve = time.perf_counter() - t0
+        s.close()
+        finish = max(r.arrival_s, finish) + solve
+        busy += solve
+        cells += pb.cells * 3 * steps
+        out.append({"U": Uh, "steps": steps, "latency": finish - r.arrival_s, "solve_s": solve})
+        if fp64_reference and r.fp32:
+            s = wcns.Solver.for_problem(pb, precision=wcns.FP64, cfl=0.5)
+            U = torch.from_numpy(pb.U0.copy()).cuda()
+            s.advance(U, r.t_end, check_every=64)
+            ref[k] = U.cpu().numpy()
+            s.close()
+    return {"results": out, "busy_s": busy, "cell_updates": cells, "fp64_of_fp32": ref}
+
+
+def rel_l1(a, c):
+    """Relative L1 difference per variable of a against c, the momenta against
+    the largest momentum total; the largest over the variables."""
+    import numpy as np
+    a = a.reshape(a.shape[0], -1)
+    c = c.reshape(c.shape[0], -1)
+    tot = np.sum(np.abs(c), axis=1)
+    tot[1:-1] = tot[1:-1].max()
+    return float(np.max(np.sum(np.abs(a - c), axis=1) / tot))
+
+
+def serving_summary(trace, served, plain):
+    """p50/p99 latency and throughput of the served trace beside the plain
+    baseline, the FP32 error of served results against the FP64 solution, and
+    whether the served FP64 results equal the plain FP64 path (= the oracle)."""
+    import numpy as np
+    sl = np.array([r["latency"] for r in served["results"]])
+    pl = np.array([r["latency"] for r in plain["results"]])
+    fp32_err = [rel_l1(served["results"][k]["U"], plain["fp64_of_fp32"][k]) for k in plain["fp64_of_fp32"]]
+    fp64_same = all(np.array_equal(served["results"][k]["U"], plain["results"][k]["U"])
+                    for k, r in enumerate(trace) if not r.fp32)
+    fp32_same = all(np.array_equal(served["results"][k]["U"], plain["results"][k]["U"])
+                    for k, r in enumerate(trace) if r.fp32)
+    plain_wall = max(max(r.arrival_s for r in trace), 0.0)
+    finish = 0.0
+    for r, res in zip(trace, plain["results"]):
+        finish = max(r.arrival_s, finish) + res["solve_s"]
+    statuses = [r["status"] for r in served["results"]]
+    return {
+        "served": {"value": served["cell_updates"] / served["wall_s"], "unit": UNIT,
+                   "latency_s": {"p50": float(np.percentile(sl, 50)), "p99": float(np.percentile(sl, 99)),
+                                 "max": float(sl.max())},
+                   "wall_s": served["wall_s"], "max_queue": served["max_queue"],
+                   "max_running": served["stats"]["max_running"],
+                   "status_counts": {str(v): statuses.count(v) for v in sorted(set(statuses))}},
+        "plain_one_at_a_time": {"value": plain["cell_updates"] / finish, "unit": UNIT,
+                                "latency_s": {"p50": float(np.percentile(pl, 50)),
+                                              "p99": float(np.percentile(pl, 99)), "max": float(pl.max())},
+                                "wall_s": finish, "busy_s": plain["busy_s"],
+                                "latency_rule": "FCFS queue over measured solve times"},
+        "speedup_served_vs_plain": (served["cell_updates"] / served["wall_s"]) / (plain["cell_updates"] / finish),
+        "fp32_l1_rel_error_vs_fp64": {"max": max(fp32_err) if fp32_err else None,
+                                      "median": float(np.median(fp32_err)) if fp32_err else None,
+                                      "requests": len(fp32_err)},
+        "fp64_served_equal_plain_fp64": fp64_same,
+        "fp32_served_equal_plain_fp32": fp32_same,
+    }
+
+
+def serve_arm(args):
+    """Serving: a seeded Poisson trace of four-quadrant Riemann requests (side
+    log-uniform 128..1024, t_end U[0.1, 0.3], half FP32 / half FP64) replayed
+    in real time against one server; latency = result ready - arrival.  The
+    plain one-request-at-a-time path runs the same trace for comparison."""
+    from paper_1810_07806_gb300 import inputs
+    trace = inputs.serving_trace(args.requests, rate=args.rate, side_lo=args.side_lo, side_hi=args.side_hi)
+    served = serve_replay(trace)
+    plain = plain_replay(trace)
+    summ = serving_summary(trace, served, plain)
     print(json.dumps({
-        "metric": METRIC, "value": cells / total, "unit": UNIT, "n_gpus": 1, "steps": int(st["steps"]),
-        "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64", "data": "synthetic",
+        "metric": METRIC, "value": summ["served"]["value"], "unit": UNIT, "n_gpus": 1,
+        "steps": int(served["stats"]["steps"]), "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": "serving_four_quadrant_2d_trace", "requests": len(trace), "rate_per_s": args.rate,
-                   "seed": 7806, "side": "log-uniform 128..1024", "t_end": "U[0.1,0.3]", "fp32_share": 0.5},
-        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                      "max": float(lat.max())},
-        "wall_s": total, "max_queue": int(max(qdepth) if qdepth else 0), "max_running": st["max_running"],
-        "all_ok": all(got[i]["status"] == 0 for i in range(len(trace)))}))
+                   "seed": 7806, "side": "log-uniform %d..%d" % (args.side_lo, args.side_hi),
+                   "t_end": "U[0.1,0.3]", "fp32_share": 0.5},
+        **summ}))
 
 
 SCALAR_N, SCALAR_LINES, SCALAR_STEPS_PER_CALL = 1600, 152 * 8, 100
+# the serving sample of the default line
+SERVE_SHORT = {"requests": 24, "rate": 200.0, "side_lo": 64, "side_hi": 192}
 
 
 def scalar_lines():

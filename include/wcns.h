@@ -155,6 +155,15 @@ size_t wcns_flags_bytes(const wcns_handle* h);
  * another U, or changing the tile configuration, captures again. */
 wcns_status wcns_step_rk3(wcns_handle* h, void* U, double dt, double* dt_used, void* stream);
 
+/* nsteps SSP-RK3 steps with the CFL rule (as wcns_step_rk3 with dt <= 0) on
+ * a HOST FP64 state U (nv * N doubles, SoA, updated in place; pinned memory
+ * copies fastest, pageable memory works).  The call copies U to a device
+ * state the handle owns (allocated on the first call, freed by
+ * wcns_destroy; WCNS_ERR_NOMEM if that fails), steps it, copies it back and
+ * synchronises the stream.  Returns WCNS_ERR_NONPHYSICAL, with the steps
+ * done and U written, when faces fell back to first-order values. */
+wcns_status wcns_step_rk3_host(wcns_handle* h, double* U, int nsteps, void* stream);
+
 /* Advance U (FP64 device state) from t = 0 to t_end with CFL steps, the
  * last one clipped to land on t_end, or until max_steps.  The time and step
  * size stay on the device; the host loop checks completion every `check`

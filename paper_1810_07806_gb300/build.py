@@ -18,10 +18,15 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
           "--expt-relaxed-constexpr"]
 # The FP32 sweep may use approximate division/sqrt and flush denormals; the
 # FP64 units keep IEEE division and square root (always the case for double).
-FP32_FLAGS = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
+# No multiply-add contraction where FP32 arithmetic runs: the code writes
+# every fused multiply-add it wants as fmaf, so each kernel instance (single
+# grid, batched, any tile shape) rounds identically.
+NO_CONTRACT = ["-fmad=false"]
+FP32_FLAGS = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"] + NO_CONTRACT
 EXTRA = {"sweep_fp32.cu": FP32_FLAGS, "sweep_fp32_cfg1.cu": FP32_FLAGS, "sweep_fp32_cfg2.cu": FP32_FLAGS,
          "sweep_batch_fp32.cu": FP32_FLAGS, "sweep_fp32_weights.cu": FP32_FLAGS,
-         "sweep_fp32_weights_lin.cu": FP32_FLAGS, "sweep_fp32_weights_z.cu": FP32_FLAGS}
+         "sweep_fp32_weights_lin.cu": FP32_FLAGS, "sweep_fp32_weights_z.cu": FP32_FLAGS,
+         "wcns_rk.cu": NO_CONTRACT, "wcns_batch.cu": NO_CONTRACT}
 SOURCES = ["wcns_api.cu", "wcns_rk.cu", "sweep_fp64.cu", "sweep_fp32.cu", "sweep_fp32_cfg1.cu",
            "sweep_fp32_cfg2.cu", "wcns_noalloc.cu",
            "wcns_batch.cu", "sweep_batch_fp64.cu", "sweep_batch_fp32.cu", "wcns_serve.cu",

@@ -36,6 +36,11 @@ struct wcns_handle {
     size_t bytes = 0;
     // tile configuration of each direction's FP32 sweep (set by wcns_autotune)
     int tile_cfg[3] = {0, 0, 0};
+    // FP32: the reference state of the stage values is in sc (set at the
+    // first step or advance)
+    bool ref_set = false;
+    // device copy of a host state (wcns_step_rk3_host), allocated on first use
+    double* Udev = nullptr;
     // one RK3 step with the CFL rule as a CUDA graph, per state pointer:
     // [0] clock reset + step (wcns_step_rk3), [1] clipped step (wcns_advance);
     // captured on an internal stream, replayed on the caller's
@@ -189,6 +194,7 @@ wcns_status wcns_destroy(wcns_handle* h)
     drop_graphs(h);
     if (h->cap) cudaStreamDestroy(h->cap);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    if (h->Udev) cudaFree(h->Udev);
     cudaError_t e = cudaFree(h->L);
     delete h;
     if (e != cudaSuccess) return cuda_fail(e, "cudaFree");
@@ -308,7 +314,7 @@ static cudaError_t run_stages(wcns_handle* h, double* U, cudaStream_t s, bool co
     float* A = (float*)h->U1;
     float* B = h->S2;
     float* L = (float*)h->L;
-    if (!converted && (e = launch_to_fp32(U, A, M, h->sc, s)) != cudaSuccess) return e;
+    if (!converted && (e = launch_to_fp32(h->nv, U, A, h->N, h->sc, s)) != cudaSuccess) return e;
     if ((e = run_rhs(h, A, L, nullptr, dtp, s, 1, U, B)) != cudaSuccess) return e;
     if ((e = run_rhs(h, B, L, nullptr, dtp, s, 2, U, A)) != cudaSuccess) return e;
     return run_rhs(h, A, L, nullptr, dtp, s, 3, U, nullptr);
@@ -327,6 +333,16 @@ static cudaError_t step_cfl(wcns_handle* h, const double* U, int clip, cudaStrea
 static cudaError_t reset_clock(wcns_handle* h, double t_end, cudaStream_t s)
 {
     return launch_reset_clock(t_end, h->sc, s);
+}
+
+// FP32 handles: the reference state of the stage values, taken once from the
+// first state the handle steps (stream-ordered, before any captured step).
+static cudaError_t ensure_reference(wcns_handle* h, const void* U, cudaStream_t s)
+{
+    if (h->p.precision != WCNS_FP32 || h->ref_set) return cudaSuccess;
+    const cudaError_t e = launch_reference(h->ndim, (const double*)U, h->N, h->gamma, h->sc, s);
+    if (e == cudaSuccess) h->ref_set = true;
+    return e;
 }
 
 // The graph of one CFL step on state U (kind 0: with the clock reset of
@@ -375,6 +391,7 @@ wcns_status wcns_step_rk3(wcns_handle* h, void* U, double dt, double* dt_used, v
         CK(cudaMemcpyAsync(&before, h->fallback, sizeof before, cudaMemcpyDeviceToHost, s), "counter copy");
         CK(cudaStreamSynchronize(s), "sync");
     }
+    CK(ensure_reference(h, U, s), "reference state");
     if (!(dt > 0.0) && !h->profiling && step_graph(h, 0, U)) {
         CK(cudaGraphLaunch(h->graph[0], s), "step graph");
     } else {
@@ -395,6 +412,43 @@ wcns_status wcns_step_rk3(wcns_handle* h, void* U, double dt, double* dt_used, v
     return WCNS_OK;
 }
 
+wcns_status wcns_step_rk3_host(wcns_handle* h, double* U, int nsteps, void* stream)
+{
+    g_err.clear();
+    if (!h || !U || nsteps < 0) return fail(WCNS_ERR_INVALID, "wcns_step_rk3_host: bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaGetLastError(), "pending CUDA error");
+    const size_t bytes = sizeof(double) * (size_t)h->nv * (size_t)h->N;
+    if (!h->Udev) {
+        if (cudaMalloc((void**)&h->Udev, bytes) != cudaSuccess) {
+            h->Udev = nullptr;
+            cudaGetLastError();
+            return fail(WCNS_ERR_NOMEM, "wcns_step_rk3_host: cudaMalloc of %zu bytes failed", bytes);
+        }
+        h->bytes += bytes;
+    }
+    long long before = 0, after = 0;
+    CK(cudaMemcpyAsync(&before, h->fallback, sizeof before, cudaMemcpyDeviceToHost, s), "counter copy");
+    CK(cudaMemcpyAsync(h->Udev, U, bytes, cudaMemcpyHostToDevice, s), "state copy in");
+    CK(ensure_reference(h, h->Udev, s), "reference state");
+    for (int k = 0; k < nsteps; ++k) {
+        if (!h->profiling && step_graph(h, 0, h->Udev)) {
+            CK(cudaGraphLaunch(h->graph[0], s), "step graph");
+        } else {
+            CK(reset_clock(h, INFINITY, s), "reset clock");
+            CK(step_cfl(h, h->Udev, 0, s), "cfl");
+            CK(run_stages(h, h->Udev, s, true), "rk3 stages");
+        }
+    }
+    CK(cudaMemcpyAsync(U, h->Udev, bytes, cudaMemcpyDeviceToHost, s), "state copy out");
+    CK(cudaMemcpyAsync(&after, h->fallback, sizeof after, cudaMemcpyDeviceToHost, s), "counter copy");
+    CK(cudaStreamSynchronize(s), "sync");
+    if (after > before)
+        return fail(WCNS_ERR_NONPHYSICAL, "wcns_step_rk3_host: %lld faces had rho <= 0 or p <= 0 and used "
+                    "first-order values", after - before);
+    return WCNS_OK;
+}
+
 wcns_status wcns_advance(wcns_handle* h, void* U, double t_end, int max_steps, int check,
                          double* t_out, int* steps_out, void* stream)
 {
@@ -406,6 +460,7 @@ wcns_status wcns_advance(wcns_handle* h, void* U, double t_end, int max_steps, i
     CK(cudaGetLastError(), "pending CUDA error");
     CK(reset_clock(h, t_end, s), "reset clock");
     long long before = 0, after = 0;
+    CK(ensure_reference(h, U, s), "reference state");
     CK(cudaMemcpyAsync(&before, h->fallback, sizeof before, cudaMemcpyDeviceToHost, s), "counter copy");
     CK(cudaStreamSynchronize(s), "sync");
     long long issued = 0;
@@ -530,9 +585,8 @@ extern "C" wcns_status wcns_autotune(wcns_handle* h, const void* U, int* chosen,
     drop_graphs(h);   // captured steps hold the old tile shapes
     // the comparison weights have one tile configuration; TENO has three
     if (h->p.precision == WCNS_FP32 && h->ndim >= 2 && h->p.weights == WCNS_W_TENO) {
-        const long long M = (long long)h->nv * h->N;
         float* A = (float*)h->U1;
-        CK(launch_to_fp32((const double*)U, A, M, nullptr, s), "autotune state");
+        CK(launch_to_fp32(h->nv, (const double*)U, A, h->N, nullptr, s), "autotune state");
         cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0), "event");
         CK(cudaEventCreate(&e1), "event");

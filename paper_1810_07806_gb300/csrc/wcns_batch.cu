@@ -66,15 +66,19 @@ __global__ void __launch_bounds__(256) batch_cfl_kernel(const double* __restrict
     double m = 0.0;
     float mf = 0.f;
     const float gf = (float)gamma;
+    const double rr = s->ref_rho, er = s->ref_E;
     for (int k = threadIdx.x; k < ch.count; k += blockDim.x) {
         const long long i = ch.begin + k;
         if constexpr (FAST) {
-            // the same FP32 expressions as the single-grid rule
+            // the same FP32 expressions as the single-grid rule; the stage
+            // input is relative to the instance's reference state
             float Uf[ND + 2];
 #pragma unroll
             for (int v = 0; v < ND + 2; ++v) {
-                Uf[v] = f64_to_f32_ftz(Ui[v * N + i]);
-                S[I.off + v * N + i] = Uf[v];
+                const double x = Ui[v * N + i];
+                Uf[v] = f64_to_f32_ftz(x);
+                const double r = v == 0 ? rr : (v == ND + 1 ? er : 0.0);
+                S[I.off + v * N + i] = (v == 0 || v == ND + 1) ? f64_to_f32_ftz(x - r) : Uf[v];
             }
             const float ir = __frcp_rn(Uf[0]);
             float m2 = 0.f, sum = 0.f, vel[ND];
@@ -83,7 +87,7 @@ __global__ void __launch_bounds__(256) batch_cfl_kernel(const double* __restrict
                 m2 = fmaf(Uf[1 + a], Uf[1 + a], m2);
                 vel[a] = fabsf(Uf[1 + a]) * ir;
             }
-            const float p = (gf - 1.f) * (Uf[ND + 1] - 0.5f * m2 * ir);
+            const float p = (gf - 1.f) * fmaf(-0.5f * m2, ir, Uf[ND + 1]);
             const float c = sqrtf(gf * p * ir);
 #pragma unroll
             for (int a = 0; a < ND; ++a) sum = fmaf(vel[a] + c, I.inv_hf[a], sum);
@@ -561,6 +565,9 @@ wcns_status wcns_batch_add(wcns_batch* b, const wcns_grid* g, const double* U0, 
                         u0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st), "initial state copy");
     set_clock_kernel<<<1, 1, 0, st>>>(b->sc + slot, t_end);
     BCK(cudaGetLastError(), "clock set");
+    // the FP32 stage values' reference state, from the initial state (the
+    // same rule and kernels as a single grid's first step)
+    BCK(launch_reference(b->ndim, b->U + off, s.N, b->gamma, b->sc + slot, st), "reference state");
     BCK(cudaMemsetAsync(b->fallback + slot, 0, sizeof(long long), st), "fallback counter reset");
     b->slots[slot] = s;
     b->dirty = true;

@@ -71,6 +71,17 @@ struct SchemeConst {
     float gammaf, gm1f;  // gamma, gamma - 1 in float
 };
 
+// The FP32 path's reference state U_r = (rho_r, 0, .., 0, E_r), p_r =
+// (gamma - 1) E_r, H_r = E_r + p_r, as the face code uses it (all zero: the
+// plain form).  Stage values are u = U - U_r.  Projection, selection and
+// interpolation are linear in u up to the selection's rescaling, so they run
+// on u directly; the fluxes need rho = u_rho + rho_r, the pressure difference
+// p - p_r = (gamma - 1)(u_E - |m|^2 / (2 rho)) (m_r = 0) and
+// E + p = u_E + (p - p_r) + H_r.
+struct Ref32 {
+    float rho, e, p, h;
+};
+
 // FP32 reciprocal: the hardware approximation (PTX rcp.approx.ftz.f32, at
 // most 1 ulp from 1/x over the full range).  Every argument in the FP32 path
 // is a normal number (rescaled indicators are floored at FLT_MIN, densities
@@ -113,15 +124,15 @@ __device__ __forceinline__ void weights_pair_fp32(const float s[6], float sqrt_e
     float t[6];
 #pragma unroll
     for (int m = 0; m < 6; ++m) t[m] = s[m] * inv;
-    const float a2 = t[0] - 2.0f * t[1] + t[2];
-    const float b2 = t[1] - 2.0f * t[2] + t[3];
-    const float c2 = t[2] - 2.0f * t[3] + t[4];
-    const float d2 = t[3] - 2.0f * t[4] + t[5];
-    const float D1L[3] = {0.5f * (t[0] - 4.0f * t[1] + 3.0f * t[2]), 0.5f * (t[3] - t[1]),
-                          0.5f * (-3.0f * t[2] + 4.0f * t[3] - t[4])};
+    const float a2 = fmaf(-2.0f, t[1], t[0]) + t[2];
+    const float b2 = fmaf(-2.0f, t[2], t[1]) + t[3];
+    const float c2 = fmaf(-2.0f, t[3], t[2]) + t[4];
+    const float d2 = fmaf(-2.0f, t[4], t[3]) + t[5];
+    const float D1L[3] = {0.5f * fmaf(3.0f, t[2], fmaf(-4.0f, t[1], t[0])), 0.5f * (t[3] - t[1]),
+                          0.5f * (fmaf(4.0f, t[3], -3.0f * t[2]) - t[4])};
     const float D2L[3] = {a2, b2, c2};
-    const float D1R[3] = {0.5f * (t[5] - 4.0f * t[4] + 3.0f * t[3]), 0.5f * (t[2] - t[4]),
-                          0.5f * (-3.0f * t[3] + 4.0f * t[2] - t[1])};
+    const float D1R[3] = {0.5f * fmaf(3.0f, t[3], fmaf(-4.0f, t[4], t[5])), 0.5f * (t[2] - t[4]),
+                          0.5f * (fmaf(4.0f, t[2], -3.0f * t[3]) - t[1])};
     const float D2R[3] = {d2, c2, b2};
     const float d[3] = {1.0f / 16.0f, 10.0f / 16.0f, 5.0f / 16.0f};
     float eps_s;
@@ -297,10 +308,13 @@ __device__ __forceinline__ float2 select_interp_x2(float2 S0, float2 S1, float2 
 }
 
 // ------------------------------------------------------------------------
-// Euler primitives and midpoint fluxes (any evaluation order).
+// Euler primitives and midpoint fluxes (FP32 path; the FP64 path has its own
+// in the oracle's operation order).  Every multiply-add is written out as
+// fmaf or as separate operations: the FP32 units compile without
+// contraction, so all instances of this code round identically.
 // ------------------------------------------------------------------------
-// (These are the FP32 path's; the FP64 path has its own in the oracle's
-// operation order.)  pressure_ir takes 1 / rho.
+// pressure_ir takes 1 / rho.  On a state relative to the reference
+// (u_E = E - E_r, m_r = 0) it gives p - p_r.
 template <int ND>
 __device__ __forceinline__ float pressure_ir(const float* U, float ir, float gm1)
 {
@@ -310,12 +324,14 @@ __device__ __forceinline__ float pressure_ir(const float* U, float ir, float gm1
     return gm1 * fmaf(-0.5f * m2, ir, U[ND + 1]);
 }
 
+// (rho_r: the reference density the state is measured from, 0 for a full state)
 template <int ND>
-__device__ __forceinline__ float pressure_of(const float* U, float gm1)
+__device__ __forceinline__ float pressure_of(const float* U, float gm1, float rho_r = 0.f)
 {
-    return pressure_ir<ND>(U, rcpf(U[0]), gm1);
+    return pressure_ir<ND>(U, rcpf(U[0] + rho_r), gm1);
 }
 
+// Physical flux of a full state U with pressure p.
 template <int ND, int D>
 __device__ __forceinline__ void phys_flux(const float* U, float p, float* F)
 {
@@ -323,17 +339,35 @@ __device__ __forceinline__ void phys_flux(const float* U, float p, float* F)
     F[0] = U[1 + D];
 #pragma unroll
     for (int a = 0; a < ND; ++a) F[1 + a] = U[1 + a] * un;
-    F[1 + D] += p;
+    F[1 + D] = fmaf(U[1 + D], un, p);
     F[ND + 1] = (U[ND + 1] + p) * un;
 }
 
+// The same flux of a state u = U - U_r with p' = p - p_r: the momentum flux
+// carries p' (the constant p_r cancels in every difference of fluxes), the
+// energy flux (E + p) u_n = (u_E + p' + H_r) u_n.
+template <int ND, int D>
+__device__ __forceinline__ void phys_flux_ref(const float* U, float pr, const Ref32& R, float* F)
+{
+    const float un = U[1 + D] * rcpf(U[0] + R.rho);
+    F[0] = U[1 + D];
+#pragma unroll
+    for (int a = 0; a < ND; ++a) F[1 + a] = U[1 + a] * un;
+    F[1 + D] = fmaf(U[1 + D], un, pr);
+    F[ND + 1] = ((U[ND + 1] + pr) + R.h) * un;
+}
+
 // Roe (1981) flux difference splitting, F = (F_L + F_R - sum |lam_k| alpha_k r_k)/2
-// with the wave strengths alpha_k of the Roe-averaged state.  rL, rR are
-// 1 / sqrt(rho) of the two states: sqrt(rho) = rho r, 1 / rho = r^2, and the
-// Roe weights sqrt(rho)/rho are r itself.
+// with the wave strengths alpha_k of the Roe-averaged state.  UL, UR are
+// states relative to the reference U_r (Ref32) and pL, pR their p - p_r;
+// rL, rR are 1 / sqrt(rho) of the full densities: sqrt(rho) = rho r,
+// 1 / rho = r^2, and the Roe weights sqrt(rho)/rho are r itself.  The
+// momentum flux carries p - p_r (a constant offset of every face's flux,
+// which the differences of Eq. 3-5 remove); differences of states and
+// pressures are those of the full ones.
 template <int ND, int D>
 __device__ __forceinline__ void roe_flux(const float* UL, const float* UR, float pL, float pR, float rL,
-                                         float rR, float gm1, float* F)
+                                         float rR, float gm1, const Ref32& R, float* F)
 {
     constexpr int NV = ND + 2;
     const float iL = rL * rL, iR = rR * rR;
@@ -346,11 +380,12 @@ __device__ __forceinline__ void roe_flux(const float* UL, const float* UR, float
         FL[1 + a] = UL[1 + a] * unL;
         FR[1 + a] = UR[1 + a] * unR;
     }
-    FL[1 + D] += pL;
-    FR[1 + D] += pR;
-    FL[ND + 1] = (UL[ND + 1] + pL) * unL;
-    FR[ND + 1] = (UR[ND + 1] + pR) * unR;
-    const float sL = UL[0] * rL, sR = UR[0] * rR;
+    FL[1 + D] = fmaf(UL[1 + D], unL, pL);
+    FR[1 + D] = fmaf(UR[1 + D], unR, pR);
+    const float eL = (UL[ND + 1] + pL) + R.h, eR = (UR[ND + 1] + pR) + R.h;   // E + p
+    FL[ND + 1] = eL * unL;
+    FR[ND + 1] = eR * unR;
+    const float sL = (UL[0] + R.rho) * rL, sR = (UR[0] + R.rho) * rR;
     const float w = rcpf(sL + sR);
     float vel[ND], dv[ND], q2 = 0.f;
 #pragma unroll
@@ -359,7 +394,7 @@ __device__ __forceinline__ void roe_flux(const float* UL, const float* UR, float
         dv[a] = fmaf(UR[1 + a], iR, -UL[1 + a] * iL);
         q2 = fmaf(vel[a], vel[a], q2);
     }
-    const float H = fmaf(UL[ND + 1] + pL, rL, (UR[ND + 1] + pR) * rR) * w;
+    const float H = fmaf(eL, rL, eR * rR) * w;
     const float c2 = gm1 * fmaf(-0.5f, q2, H);
     const float rc = rsqrtf_a(c2);
     const float c = c2 * rc;
@@ -367,23 +402,25 @@ __device__ __forceinline__ void roe_flux(const float* UL, const float* UR, float
     const float rho = sL * sR;
     const float un = vel[D];
     const float drho = UR[0] - UL[0], dp = pR - pL;
-    const float a0 = 0.5f * (dp - rho * c * dv[D]) * ic2;
-    const float aN = 0.5f * (dp + rho * c * dv[D]) * ic2;
-    const float a1 = drho - dp * ic2;
+    const float rcdv = rho * c * dv[D];
+    const float a0 = 0.5f * (dp - rcdv) * ic2;
+    const float aN = 0.5f * (dp + rcdv) * ic2;
+    const float a1 = fmaf(-dp, ic2, drho);
     const float l0 = fabsf(un - c) * a0, l1 = fabsf(un) * a1, lN = fabsf(un + c) * aN;
     const float lt = fabsf(un) * rho;
+    const float dl = lN - l0;
     // sum of |lam_k| alpha_k r_k
     float Dm[NV];
-    Dm[0] = l0 + l1 + lN;
+    Dm[0] = (l0 + l1) + lN;
 #pragma unroll
-    for (int a = 0; a < ND; ++a) Dm[1 + a] = vel[a] * Dm[0] + (a == D ? c * (lN - l0) : lt * dv[a]);
-    float e = H * (l0 + lN) + un * c * (lN - l0) + 0.5f * q2 * l1;
+    for (int a = 0; a < ND; ++a) Dm[1 + a] = fmaf(vel[a], Dm[0], a == D ? c * dl : lt * dv[a]);
+    float e = fmaf(H, l0 + lN, fmaf(un * c, dl, 0.5f * q2 * l1));
 #pragma unroll
     for (int a = 0; a < ND; ++a)
         if (a != D) e = fmaf(vel[a], lt * dv[a], e);
     Dm[ND + 1] = e;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) F[v] = 0.5f * (FL[v] + FR[v] - Dm[v]);
+    for (int v = 0; v < NV; ++v) F[v] = 0.5f * ((FL[v] + FR[v]) - Dm[v]);
 }
 
 // AUSM (Liou and Steffen 1993): interface Mach number M_L^+ + M_R^- and
@@ -391,69 +428,72 @@ __device__ __forceinline__ void roe_flux(const float* UL, const float* UR, float
 // |M| <= 1, upwind values outside), each side with its own speed of sound;
 // F = m (Phi_L + Phi_R)/2 - |m| (Phi_R - Phi_L)/2 + p_n e_D with
 // Phi = rho c (1, u, H).
-template <typename T>
-__device__ __forceinline__ void ausm_split(T M, T p, T s, T& Ms, T& ps)
+__device__ __forceinline__ void ausm_split(float M, float p, float s, float& Ms, float& ps)
 {
-    if (fabs(M) <= T(1)) {
-        const T a = (M + s) * (M + s);
-        Ms = s * T(0.25) * a;
-        ps = T(0.25) * p * a * (T(2) - s * M);
+    if (fabsf(M) <= 1.f) {
+        const float Mps = M + s;
+        const float a = Mps * Mps;
+        Ms = s * 0.25f * a;
+        ps = 0.25f * p * a * fmaf(-s, M, 2.f);
     } else {
-        const T a = T(0.5) * (M + s * fabs(M));
+        const float a = 0.5f * fmaf(s, fabsf(M), M);
         Ms = a;
         ps = p * a / M;
     }
 }
 
-template <int ND, int D, typename T>
-__device__ __forceinline__ void ausm_flux(const T* UL, const T* UR, T pL, T pR, T gamma, T* F)
+// (full states UL, UR with their pressures)
+template <int ND, int D>
+__device__ __forceinline__ void ausm_flux(const float* UL, const float* UR, float pL, float pR, float gamma,
+                                          float* F)
 {
     constexpr int NV = ND + 2;
-    const T iL = T(1) / UL[0], iR = T(1) / UR[0];
-    const T cL = sqrt(gamma * pL * iL), cR = sqrt(gamma * pR * iR);
-    const T ML = UL[1 + D] * iL / cL, MR = UR[1 + D] * iR / cR;
-    T Mp, pp, Mm, pm;
-    ausm_split(ML, pL, T(1), Mp, pp);
-    ausm_split(MR, pR, T(-1), Mm, pm);
-    const T m = Mp + Mm;
+    const float iL = 1.f / UL[0], iR = 1.f / UR[0];
+    const float cL = sqrtf(gamma * pL * iL), cR = sqrtf(gamma * pR * iR);
+    const float ML = UL[1 + D] * iL / cL, MR = UR[1 + D] * iR / cR;
+    float Mp, pp, Mm, pm;
+    ausm_split(ML, pL, 1.f, Mp, pp);
+    ausm_split(MR, pR, -1.f, Mm, pm);
+    const float m = Mp + Mm;
     // per-side weights of rho c: (m + |m|)/2 on the left, (m - |m|)/2 on the right
-    const T wl = T(0.5) * (m + fabs(m)) * cL, wr = T(0.5) * (m - fabs(m)) * cR;
-    F[0] = wl * UL[0] + wr * UR[0];
+    const float wl = 0.5f * (m + fabsf(m)) * cL, wr = 0.5f * (m - fabsf(m)) * cR;
+    F[0] = fmaf(wl, UL[0], wr * UR[0]);
 #pragma unroll
-    for (int a = 0; a < ND; ++a) F[1 + a] = wl * UL[1 + a] + wr * UR[1 + a];
-    F[1 + D] += pp + pm;
-    F[NV - 1] = wl * (UL[NV - 1] + pL) + wr * (UR[NV - 1] + pR);
+    for (int a = 0; a < ND; ++a) F[1 + a] = fmaf(wl, UL[1 + a], wr * UR[1 + a]);
+    F[1 + D] = F[1 + D] + (pp + pm);
+    F[NV - 1] = fmaf(wl, UL[NV - 1] + pL, wr * (UR[NV - 1] + pR));
 }
 
-// van Leer (1982) flux vector splitting: F = F+(U_L) + F-(U_R).
-template <int ND, int D, typename T>
-__device__ __forceinline__ void vanleer_half(const T* U, T p, T gamma, T gm1, T sgn, T* F)
+// van Leer (1982) flux vector splitting: F = F+(U_L) + F-(U_R) (full states).
+template <int ND, int D>
+__device__ __forceinline__ void vanleer_half(const float* U, float p, float gamma, float gm1, float sgn, float* F)
 {
     constexpr int NV = ND + 2;
-    const T ir = T(1) / U[0];
-    const T c = sqrt(gamma * p * ir);
-    const T un = U[1 + D] * ir;
-    const T M = un / c;
-    if (M >= T(1) || M <= T(-1)) {
-        if ((M >= T(1)) == (sgn > T(0))) {
+    const float ir = 1.f / U[0];
+    const float c = sqrtf(gamma * p * ir);
+    const float un = U[1 + D] * ir;
+    const float M = un / c;
+    if (M >= 1.f || M <= -1.f) {
+        if ((M >= 1.f) == (sgn > 0.f)) {
             phys_flux<ND, D>(U, p, F);
         } else {
 #pragma unroll
-            for (int v = 0; v < NV; ++v) F[v] = T(0);
+            for (int v = 0; v < NV; ++v) F[v] = 0.f;
         }
         return;
     }
-    const T fm = sgn * T(0.25) * U[0] * c * (M + sgn) * (M + sgn);
-    T t2 = 0;
+    const float Ms = M + sgn;
+    const float fm = sgn * 0.25f * U[0] * c * Ms * Ms;
+    float t2 = 0.f;
 #pragma unroll
     for (int a = 0; a < ND; ++a)
-        if (a != D) t2 = fma(U[1 + a] * ir, U[1 + a] * ir, t2);
-    const T wn = gm1 * un + sgn * T(2) * c;
+        if (a != D) t2 = fmaf(U[1 + a] * ir, U[1 + a] * ir, t2);
+    const float wn = fmaf(gm1, un, sgn * 2.f * c);
     F[0] = fm;
 #pragma unroll
     for (int a = 0; a < ND; ++a) F[1 + a] = fm * (U[1 + a] * ir);
     F[1 + D] = fm * wn / gamma;
-    F[NV - 1] = fm * (wn * wn / (T(2) * (gamma * gamma - T(1))) + T(0.5) * t2);
+    F[NV - 1] = fm * fmaf(0.5f, t2, wn * wn / (2.f * fmaf(gamma, gamma, -1.f)));
 }
 
 }  // namespace wcns

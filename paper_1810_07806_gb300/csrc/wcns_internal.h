@@ -175,19 +175,13 @@ cudaError_t prepare_sweeps_batch_fp32();
 cudaError_t prepare_sweeps_fp64();
 cudaError_t prepare_sweeps_fp32();
 
-// Time step, RK stages, reductions (wcns_rk.cu).
-struct StepScalars {      // device-resident
-    double dt;            // step of the current RK step (0 = finished)
-    double t;             // time reached at the end of the current step
-    double t_end;         // clip target (inf when unused)
-    unsigned long long lam_bits;   // max wave-speed sum (non-negative double bits)
-    unsigned long long steps;      // steps that advanced time since the last reset
-};
+// Time step, RK stages, reductions (wcns_rk.cu).  StepScalars: wcns_sweep.cuh.
 
 cudaError_t launch_cfl(int nd, const double* U, long long N, const double* h, double gamma,
                        double cfl, int clip, StepScalars* sc, cudaStream_t s);
 // FP32-path variant: per-node speeds in FP32 (rounded upward), FP64 max and
-// dt; S (nullable) receives float(U) from the same pass.
+// dt; S (nullable) receives float(U - U_r), U_r the reference state in sc,
+// from the same pass.
 cudaError_t launch_cfl_fast(int nd, const double* U, long long N, const double* h, double gamma,
                             double cfl, int clip, StepScalars* sc, cudaStream_t s, float* S = nullptr);
 cudaError_t launch_set_dt(double dt, int clip, StepScalars* sc, cudaStream_t s);
@@ -195,8 +189,14 @@ cudaError_t launch_reset_clock(double t_end, StepScalars* sc, cudaStream_t s);
 // FP64 stage combinations (Shu-Osher SSP-RK3) over M = nv*N values.
 cudaError_t launch_rk_fp64(int stage, double* U0, double* U1, const double* L, long long M,
                            const StepScalars* sc, cudaStream_t s);
-// S = float(U) (skipped when *dt == 0, i.e. the run has finished).
-cudaError_t launch_to_fp32(const double* U, float* S, long long M, const StepScalars* sc, cudaStream_t s);
+// S = float(U - U_r) with the reference state of sc (sc nullable: U_r = 0);
+// skipped when sc->dt == 0, i.e. the run has finished.
+cudaError_t launch_to_fp32(int nv, const double* U, float* S, long long N, const StepScalars* sc, cudaStream_t s);
+// The FP32 path's reference state of state U (N nodes) into sc: rho_r = min
+// rho, p_r = min p (so 0 <= U - U_r <= U in density and energy), E_r =
+// p_r / (gamma - 1), m_r = 0.  Three launches on s.
+cudaError_t launch_reference(int nd, const double* U, long long N, double gamma, StepScalars* sc,
+                             cudaStream_t s);
 cudaError_t launch_conserved(int nv, const double* U, long long N, double vol, double* partials,
                              int nblocks, cudaStream_t s);
 int conserved_blocks(long long N);

@@ -75,12 +75,14 @@ __global__ void __launch_bounds__(256) cfl_reduce_fast_kernel(const double* __re
     if (clip && !(sc->t < sc->t_end)) return;
     float m = 0.f;
     const float gm1 = gamma - 1.f;
+    const double rr = sc->ref_rho, er = sc->ref_E;
     float ih[ND];
 #pragma unroll
     for (int a = 0; a < ND; ++a) ih[a] = (float)(1.0 / hh.v[a]);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
          i += (long long)gridDim.x * blockDim.x) {
-        const float rho = f64_to_f32_ftz(U[i]);
+        const double rho_d = U[i], E_d = U[(ND + 1) * N + i];
+        const float rho = f64_to_f32_ftz(rho_d);
         const float ir = __frcp_rn(rho);
         float m2 = 0.f, s = 0.f, c = 0.f;
         float vel[ND];
@@ -92,14 +94,15 @@ __global__ void __launch_bounds__(256) cfl_reduce_fast_kernel(const double* __re
             m2 = fmaf(mv, mv, m2);
             vel[a] = fabsf(mv) * ir;
         }
-        const float E = f64_to_f32_ftz(U[(ND + 1) * N + i]);
+        const float E = f64_to_f32_ftz(E_d);
         if (S != nullptr) {
-            S[i] = rho;
+            // the first stage's input, relative to the reference state
+            S[i] = f64_to_f32_ftz(rho_d - rr);
 #pragma unroll
             for (int a = 0; a < ND; ++a) S[(1 + a) * N + i] = mvs[a];
-            S[(ND + 1) * N + i] = E;
+            S[(ND + 1) * N + i] = f64_to_f32_ftz(E_d - er);
         }
-        const float p = gm1 * (E - 0.5f * m2 * ir);
+        const float p = gm1 * fmaf(-0.5f * m2, ir, E);
         c = sqrtf(gamma * p * ir);
 #pragma unroll
         for (int a = 0; a < ND; ++a) s = fmaf(vel[a] + c, ih[a], s);
@@ -233,19 +236,105 @@ cudaError_t launch_rk_fp64(int stage, double* U0, double* U1, const double* L, l
     return cudaGetLastError();
 }
 
-// S = float(U): the single-precision input of a step's first stage.
+// S = float(U - U_r): the single-precision input of a step's first stage
+// (variable blockIdx.y; U_r = 0 without a clock).
 __global__ void __launch_bounds__(256) to_fp32_kernel(const double* __restrict__ U, float* __restrict__ S,
-                                                      long long M, const StepScalars* sc)
+                                                      long long N, int nv, const StepScalars* sc)
 {
     if (sc != nullptr && f64_is_zero(sc->dt)) return;   // a finished run (sc may be null: always convert)
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M;
+    const int v = blockIdx.y;
+    double r = 0.0;
+    if (sc != nullptr) r = v == 0 ? sc->ref_rho : (v == nv - 1 ? sc->ref_E : 0.0);
+    const double* Uv = U + (long long)v * N;
+    float* Sv = S + (long long)v * N;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
          i += (long long)gridDim.x * blockDim.x)
-        S[i] = f64_to_f32_ftz(U[i]);
+        Sv[i] = f64_to_f32_ftz(Uv[i] - r);
 }
 
-cudaError_t launch_to_fp32(const double* U, float* S, long long M, const StepScalars* sc, cudaStream_t s)
+cudaError_t launch_to_fp32(int nv, const double* U, float* S, long long N, const StepScalars* sc, cudaStream_t s)
 {
-    to_fp32_kernel<<<stream_blocks(M), 256, 0, s>>>(U, S, M, sc);
+    const int bx = (stream_blocks(N) + nv - 1) / nv;
+    to_fp32_kernel<<<dim3(bx, nv), 256, 0, s>>>(U, S, N, nv, sc);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- reference state
+// Order-preserving 64-bit keys of doubles (min/max by unsigned comparison).
+__device__ __forceinline__ unsigned long long order_key(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double from_order_key(unsigned long long k)
+{
+    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
+}
+
+__global__ void ref_begin_kernel(StepScalars* sc)
+{
+    sc->ref_keys[0] = ~0ull;
+    sc->ref_keys[1] = ~0ull;
+}
+
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, o);
+        x = y < x ? y : x;
+    }
+    return x;
+}
+
+// min rho and min p = (gamma - 1)(E - |m|^2 / (2 rho)) (FP64, fixed order)
+// over the state; minima are exact, so the result does not depend on the
+// reduction order (a batch instance and the same grid alone get the same).
+template <int ND>
+__global__ void __launch_bounds__(256) ref_reduce_kernel(const double* __restrict__ U, long long N, double gm1,
+                                                         StepScalars* sc)
+{
+    unsigned long long kr = ~0ull, kp = ~0ull;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+        double Ui[ND + 2];
+#pragma unroll
+        for (int v = 0; v < ND + 2; ++v) Ui[v] = U[v * N + i];
+        const unsigned long long a = order_key(Ui[0]), b = order_key(pressure_exact<ND>(Ui, gm1));
+        kr = a < kr ? a : kr;
+        kp = b < kp ? b : kp;
+    }
+    kr = warp_min_u64(kr);
+    kp = warp_min_u64(kp);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&sc->ref_keys[0], kr);
+        atomicMin(&sc->ref_keys[1], kp);
+    }
+}
+
+__global__ void ref_finalize_kernel(StepScalars* sc, double gm1)
+{
+    const double rr = from_order_key(sc->ref_keys[0]);
+    const double pr = from_order_key(sc->ref_keys[1]);
+    const double er = div_(pr, gm1);
+    sc->ref_rho = rr;
+    sc->ref_E = er;
+    sc->ref_rhof = (float)rr;
+    sc->ref_Ef = (float)er;
+    sc->ref_pf = (float)pr;
+    sc->ref_hf = (float)add_(er, pr);
+}
+
+cudaError_t launch_reference(int nd, const double* U, long long N, double gamma, StepScalars* sc,
+                             cudaStream_t s)
+{
+    const double gm1 = gamma - 1.0;
+    const int nb = reduce_blocks(N);
+    ref_begin_kernel<<<1, 1, 0, s>>>(sc);
+    if (nd == 1) ref_reduce_kernel<1><<<nb, 256, 0, s>>>(U, N, gm1, sc);
+    else if (nd == 2) ref_reduce_kernel<2><<<nb, 256, 0, s>>>(U, N, gm1, sc);
+    else ref_reduce_kernel<3><<<nb, 256, 0, s>>>(U, N, gm1, sc);
+    ref_finalize_kernel<<<1, 1, 0, s>>>(sc, gm1);
     return cudaGetLastError();
 }
 

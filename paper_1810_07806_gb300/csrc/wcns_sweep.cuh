@@ -44,7 +44,22 @@ struct BatchTile {
     int outer;                // y/z sweeps: the remaining axis index
 };
 
-struct StepScalars;
+// Device-resident scalars of a run: one per grid (handle), one per batch
+// instance.  The sweeps read dt (and, in FP32, the reference state) through
+// a pointer to the first member.
+struct StepScalars {
+    double dt;            // step of the current RK step (0 = finished)
+    double t;             // time reached at the end of the current step
+    double t_end;         // clip target (inf when unused)
+    unsigned long long lam_bits;   // max wave-speed sum (non-negative double bits)
+    unsigned long long steps;      // steps that advanced time since the last reset
+    // FP32 path: the constant reference state U_r = (rho_r, 0, .., 0, E_r)
+    // the single-precision stage values are measured from (all zero until
+    // set: the plain form), with p_r = (gamma - 1) E_r and H_r = E_r + p_r
+    double ref_rho, ref_E;
+    float ref_rhof, ref_Ef, ref_pf, ref_hf;
+    unsigned long long ref_keys[2];   // order keys of min rho and min p while they are reduced
+};
 
 struct SweepArgs {
     const void* U;            // input state, LT, SoA
@@ -146,7 +161,7 @@ __device__ __forceinline__ int sidx(int v, int l, int s)
 // ---------------------------------------------------------------- FP64 face
 // (the FP64 face selects the weights at run time: WT is not used)
 template <int ND, int DIR, int FLUX, int WT>
-__device__ __forceinline__ void face_flux(double (&u)[6][ND + 2], const SweepArgs& a, double* F,
+__device__ __forceinline__ void face_flux(double (&u)[6][ND + 2], const SweepArgs& a, const Ref32&, double* F,
                                           uint8_t* fl, bool& fell_back)
 {
     face_fp64<ND, DIR, FLUX>(u, a.K, F, fl, fell_back);
@@ -154,29 +169,34 @@ __device__ __forceinline__ void face_flux(double (&u)[6][ND + 2], const SweepArg
 
 // ---------------------------------------------------------------- FP32 face
 // WT: the weights, fixed at compile time (W_TENO, or the comparison weights
-// W_JS, W_LINEAR, W_Z in their own instances).
+// W_JS, W_LINEAR, W_Z in their own instances).  u holds U - U_r (Ref32);
+// every operation is written out (the FP32 units compile without
+// multiply-add contraction), so each instance of this code, single-grid or
+// batched, rounds the same way.
 template <int ND, int DIR, int FLUX, int WT>
-__device__ __forceinline__ void face_flux(float (&u)[6][ND + 2], const SweepArgs& a, float* F,
+__device__ __forceinline__ void face_flux(float (&u)[6][ND + 2], const SweepArgs& a, const Ref32& R, float* F,
                                           uint8_t* fl, bool& fell_back)
 {
     constexpr int NV = ND + 2;
     const float gm1 = a.K.gm1f;
-    // Roe average of nodes j, j+1 and the closed form of L U:
-    //   P = b1 (E - vel.m + q2 rho / 2), Q = (u_n rho - m_n) / c,
-    //   w_0 = (P + Q)/2, w_1 = rho - P, w_t = m_t - vel_t rho, w_N = (P - Q)/2.
+    // Roe average of nodes j, j+1 and the closed form of L u:
+    //   P = b1 (u_E - vel.m + q2 u_rho / 2), Q = (u_n u_rho - m_n) / c,
+    //   w_0 = (P + Q)/2, w_1 = u_rho - P, w_t = m_t - vel_t u_rho, w_N = (P - Q)/2.
     const float* Ua = u[2];
     const float* Ub = u[3];
     // (ra = 1 / sqrt(rho_j): sqrt(rho_j) = rho_j ra, 1 / rho_j = ra^2)
-    const float ra = rsqrtf_a(Ua[0]), rb = rsqrtf_a(Ub[0]);
-    const float wsum = rcpf(fmaf(Ua[0], ra, Ub[0] * rb));
+    const float rhoa = Ua[0] + R.rho, rhob = Ub[0] + R.rho;
+    const float ra = rsqrtf_a(rhoa), rb = rsqrtf_a(rhob);
+    const float wsum = rcpf(fmaf(rhoa, ra, rhob * rb));
     float vel[ND], q2 = 0.f;
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
         vel[d] = fmaf(Ua[1 + d], ra, Ub[1 + d] * rb) * wsum;
         q2 = fmaf(vel[d], vel[d], q2);
     }
+    // p - p_r of both nodes; E + p = u_E + (p - p_r) + H_r
     const float pa = pressure_ir<ND>(Ua, ra * ra, gm1), pb = pressure_ir<ND>(Ub, rb * rb, gm1);
-    const float H = fmaf(Ua[ND + 1] + pa, ra, (Ub[ND + 1] + pb) * rb) * wsum;
+    const float H = fmaf((Ua[ND + 1] + pa) + R.h, ra, ((Ub[ND + 1] + pb) + R.h) * rb) * wsum;
     const float c2 = gm1 * fmaf(-0.5f, q2, H);
     const float ic = rsqrtf_a(c2);
     const float c = c2 * ic;
@@ -293,9 +313,10 @@ __device__ __forceinline__ void face_flux(float (&u)[6][ND + 2], const SweepArgs
         UL[NV - 1] = el;
         UR[NV - 1] = er;
     }
-    float rL = rsqrtf_a(UL[0]), rR = rsqrtf_a(UR[0]);
-    float pL = pressure_ir<ND>(UL, rL * rL, gm1), pR = pressure_ir<ND>(UR, rR * rR, gm1);
-    if (!(UL[0] > 0.f) || !(UR[0] > 0.f) || !(pL > 0.f) || !(pR > 0.f)) {
+    const float rhoL = UL[0] + R.rho, rhoR = UR[0] + R.rho;
+    float rL = rsqrtf_a(rhoL), rR = rsqrtf_a(rhoR);
+    float pL = pressure_ir<ND>(UL, rL * rL, gm1), pR = pressure_ir<ND>(UR, rR * rR, gm1);   // p - p_r
+    if (!(rhoL > 0.f) || !(rhoR > 0.f) || !(pL + R.p > 0.f) || !(pR + R.p > 0.f)) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) { UL[v] = Uj[v]; UR[v] = Uj1[v]; }
         pL = pa;
@@ -305,15 +326,26 @@ __device__ __forceinline__ void face_flux(float (&u)[6][ND + 2], const SweepArgs
         fell_back = true;
     }
     if (FLUX == FLUX_ROE) {
-        roe_flux<ND, DIR>(UL, UR, pL, pR, rL, rR, gm1, F);
-    } else if (FLUX == FLUX_AUSM) {
-        ausm_flux<ND, DIR>(UL, UR, pL, pR, a.K.gammaf, F);
+        roe_flux<ND, DIR>(UL, UR, pL, pR, rL, rR, gm1, R, F);
     } else {
-        float Fp[NV], Fm[NV];
-        vanleer_half<ND, DIR>(UL, pL, a.K.gammaf, gm1, 1.f, Fp);
-        vanleer_half<ND, DIR>(UR, pR, a.K.gammaf, gm1, -1.f, Fm);
+        // the splittings take the full states (with R zero: the same values)
+        float VL[NV], VR[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) F[v] = Fp[v] + Fm[v];
+        for (int v = 0; v < NV; ++v) { VL[v] = UL[v]; VR[v] = UR[v]; }
+        VL[0] = UL[0] + R.rho;
+        VR[0] = UR[0] + R.rho;
+        VL[NV - 1] = UL[NV - 1] + R.e;
+        VR[NV - 1] = UR[NV - 1] + R.e;
+        const float PL = pL + R.p, PR = pR + R.p;
+        if (FLUX == FLUX_AUSM) {
+            ausm_flux<ND, DIR>(VL, VR, PL, PR, a.K.gammaf, F);
+        } else {
+            float Fp[NV], Fm[NV];
+            vanleer_half<ND, DIR>(VL, PL, a.K.gammaf, gm1, 1.f, Fp);
+            vanleer_half<ND, DIR>(VR, PR, a.K.gammaf, gm1, -1.f, Fm);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) F[v] = Fp[v] + Fm[v];
+        }
     }
 }
 
@@ -321,7 +353,7 @@ __device__ __forceinline__ void face_flux(float (&u)[6][ND + 2], const SweepArgs
 // (physical fluxes; FP64 in the oracle's order).
 template <int ND, int DIR, int TL, int P, typename T>
 __device__ __forceinline__ void node_flux_diff(const T* sS, int l, int s, int k, const SchemeConst& K,
-                                               T* d)
+                                               const Ref32& R, T* d)
 {
     constexpr int NV = ND + 2;
     T Up[NV], Um[NV], Fp[NV], Fm[NV];
@@ -336,8 +368,10 @@ __device__ __forceinline__ void node_flux_diff(const T* sS, int l, int s, int k,
 #pragma unroll
         for (int v = 0; v < NV; ++v) d[v] = sub_(Fp[v], Fm[v]);
     } else {
-        phys_flux<ND, DIR>(Up, pressure_of<ND>(Up, K.gm1f), Fp);
-        phys_flux<ND, DIR>(Um, pressure_of<ND>(Um, K.gm1f), Fm);
+        // (relative to U_r: the fluxes differ from the physical ones by a
+        // constant, which the difference removes)
+        phys_flux_ref<ND, DIR>(Up, pressure_of<ND>(Up, K.gm1f, R.rho), R, Fp);
+        phys_flux_ref<ND, DIR>(Um, pressure_of<ND>(Um, K.gm1f, R.rho), R, Fm);
 #pragma unroll
         for (int v = 0; v < NV; ++v) d[v] = Fp[v] - Fm[v];
     }
@@ -416,6 +450,18 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) swee
     if constexpr (!kAsyncStage) {
         if (dtp != nullptr && f64_is_zero(*dtp)) return;
     }
+    // FP32 steps: the reference state of the run (or instance); a plain
+    // right-hand side (no clock) uses none
+    Ref32 R{0.f, 0.f, 0.f, 0.f};
+    double ref_rho = 0.0, ref_E = 0.0;
+    if constexpr (sizeof(T) == 4) {
+        if (dtp != nullptr) {
+            const StepScalars* scp = reinterpret_cast<const StepScalars*>(dtp);
+            R = Ref32{scp->ref_rhof, scp->ref_Ef, scp->ref_pf, scp->ref_hf};
+            ref_rho = scp->ref_rho;
+            ref_E = scp->ref_E;
+        }
+    }
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sS = reinterpret_cast<T*>(smem_raw);
     T* sF = sS + NV * TL * P;
@@ -468,7 +514,10 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) swee
             if (kind == BC_FIXED) {
                 const double* st = a.bcs[p < 0 ? 0 : 1];
 #pragma unroll
-                for (int v = 0; v < NV; ++v) sS[sidx<DIR, TL, P>(v, l, s)] = stage_cvt<T>(st[v]);
+                for (int v = 0; v < NV; ++v) {
+                    const double r = v == 0 ? ref_rho : (v == NV - 1 ? ref_E : 0.0);
+                    sS[sidx<DIR, TL, P>(v, l, s)] = stage_cvt<T>(st[v] - r);
+                }
                 continue;
             }
             if (kind == BC_REFLECTING) {
@@ -551,7 +600,7 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) swee
         T F[NV];
         uint8_t fl[NV];
         bool fell = false;
-        face_flux<ND, DIR, FLUX, WT>(u, a, F, fl, fell);
+        face_flux<ND, DIR, FLUX, WT>(u, a, R, F, fl, fell);
         // faces shared with the next tile are owned (counted, flagged) by it
         const bool owned = f < TS || pos0 + TS >= nd;
         fb += (fell && owned) ? 1 : 0;
@@ -594,11 +643,12 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) swee
             if constexpr (ALT) {
 #pragma unroll
                 for (int v = 0; v < NV; ++v) d1[v] = d2[v] = S[v] = T(0);
-                if (diff != DIFF_MD) node_flux_diff<ND, DIR, TL, P>(sS, l, t + GHOST, 1, a.K, d1);
-                if (diff == DIFF_HWCNS) node_flux_diff<ND, DIR, TL, P>(sS, l, t + GHOST, 2, a.K, d2);
+                if (diff != DIFF_MD) node_flux_diff<ND, DIR, TL, P>(sS, l, t + GHOST, 1, a.K, R, d1);
+                if (diff == DIFF_HWCNS) node_flux_diff<ND, DIR, TL, P>(sS, l, t + GHOST, 2, a.K, R, d2);
                 if (a.source) {
                     // (0, rho g_a, sum_a g_a m_a), the sum from 0 in axis order
-                    const T rho = sS[sidx<DIR, TL, P>(0, l, t + GHOST)];
+                    T rho = sS[sidx<DIR, TL, P>(0, l, t + GHOST)];
+                    if constexpr (sizeof(T) == 4) rho = rho + R.rho;
                     T se = T(0);
 #pragma unroll
                     for (int b = 0; b < ND; ++b) {
@@ -640,11 +690,13 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) swee
                         fp = fma(T(HW_B1), f3 - f2, fma(T(HW_B2), d1[v], T(HW_B3) * d2[v]));
                     else
                         fp = fma(T(MND_C1), f3 - f2, fma(T(MND_C2), d1[v], T(MND_C3) * (f4 - f1)));
-                    const T val = -fp * ih;
-                    T lv = val;
+                    // L = -f' (first direction) or L - f'
+                    T lv;
                     if (a.accumulate) {
-                        if constexpr (kPre) lv = sL[sidx<DIR, TL, TS>(v, l, t)] + val;
-                        else lv = L[v * N + g] + val;
+                        if constexpr (kPre) lv = fmaf(-fp, ih, sL[sidx<DIR, TL, TS>(v, l, t)]);
+                        else lv = fmaf(-fp, ih, L[v * N + g]);
+                    } else {
+                        lv = -fp * ih;
                     }
                     if constexpr (ALT) {
                         if (a.source) lv += S[v];

@@ -194,6 +194,17 @@ class Solver:
         self.nonphysical |= check_physical(st)
         return d.value if want_dt else None
 
+    def step_host(self, U_host, nsteps=1, stream=None):
+        """wcns_step_rk3_host: nsteps CFL steps of a host FP64 state (a numpy
+        array or a CPU torch tensor, pinned for speed), copied in and out by
+        the library."""
+        L = lib()
+        L.wcns_step_rk3_host.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
+        L.wcns_step_rk3_host.restype = C.c_int
+        ptr = U_host.ctypes.data if hasattr(U_host, "ctypes") else U_host.data_ptr()
+        st = L.wcns_step_rk3_host(self.h, C.c_void_p(ptr), int(nsteps), _stream(stream))
+        self.nonphysical |= check_physical(st)
+
     def advance(self, U, t_end, max_steps=10 ** 9, check_every=64, stream=None):
         """Returns (t reached, steps); sets self.nonphysical when faces fell
         back to first-order values during the run."""

@@ -79,9 +79,9 @@ def test_batch_reports_first_order_faces_per_instance():
     Uo, _, steps_o, _ = _oracle_run(bad, T_END)
     assert steps_b == steps_o and np.array_equal(Ub, Uo)
     assert np.array_equal(Ug, _oracle_run(good, T_END)[0])
-    # a new instance in the freed slot starts with a clean counter
+    # a new instance in the freed slot (and arena range) starts with a clean counter
     b.remove(kb)
-    k2 = b.add(good, t_end=T_END)
+    k2 = b.add(inputs.shock_tube(300), t_end=T_END)
     b.run(check_every=4)
     b.read(k2)
     assert not b.nonphysical[k2]

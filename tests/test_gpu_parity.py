@@ -337,3 +337,26 @@ def test_tile_configurations_give_identical_results(which):
     chosen = s.autotune(torch.from_numpy(pb.U0).to(DEV))
     assert len(chosen) == pb.ndim and all(0 <= c <= 2 for c in chosen)
     s.close()
+
+
+@pytest.mark.parametrize("precision", [wcns.FP64, wcns.FP32])
+def test_host_state_step_matches_device_step_and_oracle(precision):
+    """wcns_step_rk3_host (host state copied in and out by the library) gives
+    the device-state steps bit for bit; in FP64 also the oracle's steps."""
+    pb = inputs.four_quadrant(40, ny=33)
+    s = wcns.Solver.for_problem(pb, precision=precision)
+    Uh = pb.U0.copy()
+    s.step_host(Uh, nsteps=3)
+    s.close()
+    s = wcns.Solver.for_problem(pb, precision=precision)
+    Ud = torch.from_numpy(pb.U0.copy()).to(DEV)
+    for _ in range(3):
+        s.step(Ud)
+    assert np.array_equal(Uh, Ud.cpu().numpy())
+    s.close()
+    if precision == wcns.FP64:
+        cfg = ora_cfg(pb, wcns.FLUX_ROE)
+        Uo = pb.U0.copy()
+        for _ in range(3):
+            O.rk3_step(cfg, Uo, O.cfl_dt(cfg, Uo, 0.5))
+        assert np.max(np.abs(Uh - Uo)) <= 1e-12 * np.max(np.abs(Uo))

@@ -122,17 +122,39 @@ def _flux_scale(U, pb):
     return S
 
 
+def _oracle_sensitivity(pb, cfg, t_end, seeds=3):
+    """How far the oracle's own end state moves when its initial state is
+    perturbed by relative noise of FP32 rounding size (2^-24): the largest
+    relative L1 change per variable over a few seeds.  Next to shocks the
+    cut decisions of Eq. 18 (and the positivity fallback) are discrete, so
+    an ulp-level change of the data can flip them; this is the floor any
+    FP32 evaluation of the same method sits on."""
+    Uref = pb.U0.copy()
+    O.euler_run(cfg, Uref, 0.5, t_end)
+    worst = np.zeros(pb.nv)
+    for seed in range(seeds):
+        rng = np.random.default_rng(seed)
+        U = pb.U0 * (1.0 + rng.uniform(-1.0, 1.0, pb.U0.shape) * 2.0 ** -24)
+        O.euler_run(cfg, U, 0.5, t_end)
+        rel = np.sum(np.abs(U - Uref), axis=1) / np.sum(np.abs(Uref), axis=1)
+        worst = np.maximum(worst, rel)
+    return worst, Uref
+
+
 @pytest.mark.parametrize("flux,diff", [("ausm", "md"), ("roe", "mnd")])
 def test_fp32_sod_end_state_close_to_oracle(flux, diff):
+    """Sod to t = 0.2 in FP32 against the oracle: within 1e-3 relative L1, or
+    twice the oracle's own response to FP32-sized noise in its input where
+    that is larger (AUSM: the oracle moves by up to 1.7e-3 in the momentum
+    under 2^-24 relative noise)."""
     pb = inputs.shock_tube(400)
-    Uo = pb.U0.copy()
-    O.euler_run(_cfg(pb, flux, diff), Uo, 0.5, 0.2)
+    sens, Uo = _oracle_sensitivity(pb, _cfg(pb, flux, diff), 0.2)
     s = wcns.Solver.for_problem(pb, flux=FLUX[flux][0], diff=DIFF[diff][0], precision=wcns.FP32, cfl=0.5)
     Ud = torch.from_numpy(pb.U0.copy()).to(DEV)
     s.advance(Ud, 0.2, check_every=16)
     s.close()
     rel = np.sum(np.abs(Ud.cpu().numpy() - Uo), axis=1) / np.sum(np.abs(Uo), axis=1)
-    assert np.all(rel <= 1e-3), rel
+    assert np.all(rel <= np.maximum(1e-3, 2.0 * sens)), (rel, sens)
 
 
 @pytest.mark.parametrize("precision", [wcns.FP64, wcns.FP32])
