@@ -55,8 +55,9 @@ enum { WCNS_DIFF_MD6 = 0, WCNS_DIFF_HWCNS = 1, WCNS_DIFF_MND = 2 };
  * WCNS-JS (Eq. 14), linear (the optimal weights d_k of Eq. 13, i.e. Eq. 7)
  * and WCNS-Z (the weights of Borges et al. that the paper compares with,
  * alpha_k = d_k (1 + tau_5 / (beta_k + eps)) with the tau_5 of Eq. 16).
- * All four run in FP64 everywhere and in FP32 single grids (rescaled like
- * the TENO indicators, tile configuration 0); FP32 batches take TENO only. */
+ * All four run in FP64 and FP32 everywhere (single grids, batches, the
+ * server); in FP32 the comparison weights are rescaled like the TENO
+ * indicators and use tile configuration 0. */
 enum { WCNS_W_TENO = 0, WCNS_W_JS = 1, WCNS_W_LINEAR = 2, WCNS_W_Z = 3 };
 enum { WCNS_FP64 = 0, WCNS_FP32 = 1 };
 
@@ -273,6 +274,22 @@ wcns_status wcns_batch_remove(wcns_batch* b, int slot);
  * work).  If active is non-NULL, synchronises and returns how many
  * instances advanced in the last step (0: all have reached t_end). */
 wcns_status wcns_batch_step(wcns_batch* b, int nsteps, int* active, void* stream);
+
+/* Sweep launch form of the batch (no counterpart in the paper): 0 = one CTA
+ * per tile of the tile table (default), 1 = persistent: as many CTAs as are
+ * resident on the device, each taking tiles from a device counter until the
+ * table is done (no CTA waits on another).  Results do not depend on the
+ * form.  No device work; the next step captures its graph again. */
+wcns_status wcns_batch_launch_mode(wcns_batch* b, int mode);
+
+/* Autotuner of the batch's launch form (no counterpart in the paper): times
+ * `steps` graph-replayed RK3 steps of the current instances in each form,
+ * keeps the faster, and restores the batch's states, clocks and counters, so
+ * the results are unchanged.  mode_out (nullable) receives the form kept,
+ * ms_per_step (nullable, 2 doubles) the time per step of each form (0 when
+ * the batch is empty).  Allocates a temporary copy of the state arena
+ * (WCNS_ERR_NOMEM if it does not fit).  Synchronises the stream. */
+wcns_status wcns_batch_autotune(wcns_batch* b, int steps, int* mode_out, double* ms_per_step, void* stream);
 
 /* Step until every instance has finished or max_steps, checking every
  * `check` steps.  Returns the steps taken.  Synchronises. */

@@ -1,6 +1,7 @@
 // sweep_batch_fp32.cu -- FP32 instances of the batched sweep: one launch covers
 // the tiles of every instance of a batch (tile table), each tile reading its
-// own instance's geometry, boundary rule and time step.
+// own instance's geometry, boundary rule and time step; or, persistent, as
+// many CTAs as fit on the device taking tiles from a counter.
 #include "wcns_internal.h"
 
 namespace wcns {
@@ -12,9 +13,8 @@ static cudaError_t go(const SweepArgs& a, long long ntiles, cudaStream_t s, bool
     auto k = sweep_kernel<float, float, ND, DIR, FLUX, true>;
     const size_t smem = G::smem_bytes();
     if (prepare) return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (ntiles <= 0) return cudaSuccess;
-    k<<<(unsigned)ntiles, G::THREADS, smem, s>>>(a);
-    return cudaGetLastError();
+    static int resident = 0;
+    return launch_tiles(k, G::THREADS, smem, a, ntiles, s, resident);
 }
 
 template <int FLUX>
@@ -30,6 +30,7 @@ static cudaError_t dispatch(int nd, int dir, const SweepArgs& a, long long ntile
 cudaError_t launch_sweep_batch_fp32(int nd, int dir, int flux, const SweepArgs& a, long long ntiles,
                                      cudaStream_t s)
 {
+    if (a.K.weights != W_TENO) return launch_sweep_batch_fp32_weights(a.K.weights, nd, dir, flux, a, ntiles, s);
     return flux == FLUX_ROE ? dispatch<FLUX_ROE>(nd, dir, a, ntiles, s, false)
                             : flux == FLUX_AUSM ? dispatch<FLUX_AUSM>(nd, dir, a, ntiles, s, false)
                             : dispatch<FLUX_VANLEER>(nd, dir, a, ntiles, s, false);

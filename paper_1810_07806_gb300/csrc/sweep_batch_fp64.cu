@@ -1,6 +1,7 @@
 // sweep_batch_fp64.cu -- FP64 instances of the batched sweep: one launch covers
 // the tiles of every instance of a batch (tile table), each tile reading its
-// own instance's geometry, boundary rule and time step.
+// own instance's geometry, boundary rule and time step; or, persistent, as
+// many CTAs as fit on the device taking tiles from a counter.
 #include "wcns_internal.h"
 
 namespace wcns {
@@ -12,9 +13,8 @@ static cudaError_t go(const SweepArgs& a, long long ntiles, cudaStream_t s, bool
     auto k = sweep_kernel<double, double, ND, DIR, FLUX, true>;
     const size_t smem = G::smem_bytes();
     if (prepare) return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (ntiles <= 0) return cudaSuccess;
-    k<<<(unsigned)ntiles, G::THREADS, smem, s>>>(a);
-    return cudaGetLastError();
+    static int resident = 0;
+    return launch_tiles(k, G::THREADS, smem, a, ntiles, s, resident);
 }
 
 template <int FLUX>

@@ -214,6 +214,10 @@ struct wcns_batch {
     cudaGraphExec_t exec = nullptr;
     cudaStream_t capture = nullptr;   // stream used only to record the step graph
     size_t bytes = 0;
+    // sweep launch form: 0 = one CTA per tile (tile table), 1 = persistent
+    // CTAs taking tiles from device counters (one counter per sweep of a step)
+    int launch_mode = 0;
+    unsigned int* work = nullptr;
 };
 
 namespace {
@@ -340,8 +344,10 @@ wcns_status rebuild(wcns_batch* b)
     return WCNS_OK;
 }
 
+constexpr int kWorkCounters = 16;   // >= 3 stages x 3 directions
+
 cudaError_t sweeps(wcns_batch* b, const void* Uin, void* L, cudaStream_t s, int fuse_stage = 0,
-                   float* S_out = nullptr)
+                   float* S_out = nullptr, int counter0 = 0)
 {
     const bool fp32 = b->precision == WCNS_FP32;
     for (int k = 0; k < b->ndim; ++k) {
@@ -359,6 +365,10 @@ cudaError_t sweeps(wcns_batch* b, const void* Uin, void* L, cudaStream_t s, int 
         a.tiles = b->d_tiles[d];
         a.inst_dt = &b->sc[0].dt;
         a.dt_stride = kDtStride;
+        if (b->launch_mode == 1) {
+            a.work = b->work + counter0 + k;
+            a.ntiles = b->ntiles[d];
+        }
         if (fuse_stage && d == 0) {
             a.fuse_stage = fuse_stage;
             a.U0 = b->U;
@@ -378,6 +388,8 @@ cudaError_t step_sequence(wcns_batch* b, cudaStream_t s)
     const bool fp32 = b->precision == WCNS_FP32;
     cudaError_t e = cudaMemsetAsync(b->active, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
+    if (b->launch_mode == 1 && (e = cudaMemsetAsync(b->work, 0, sizeof(unsigned int) * kWorkCounters, s)) != cudaSuccess)
+        return e;
     if (b->nnch > 0) {
         const double gm1 = b->gamma - 1.0;
         float* S0 = fp32 ? (float*)b->S : nullptr;   // FP32: the first stage's input
@@ -399,11 +411,11 @@ cudaError_t step_sequence(wcns_batch* b, cudaStream_t s)
     if (!fp32) {
         double* U1 = (double*)b->S;
         double* L = (double*)b->L;
-        if ((e = sweeps(b, b->U, L, s)) != cudaSuccess) return e;
+        if ((e = sweeps(b, b->U, L, s, 0, nullptr, 0)) != cudaSuccess) return e;
         batch_rk_fp64_kernel<1><<<b->nech, 256, 0, s>>>(b->U, U1, L, b->d_ech, b->sc);
-        if ((e = sweeps(b, U1, L, s)) != cudaSuccess) return e;
+        if ((e = sweeps(b, U1, L, s, 0, nullptr, 3)) != cudaSuccess) return e;
         batch_rk_fp64_kernel<2><<<b->nech, 256, 0, s>>>(b->U, U1, L, b->d_ech, b->sc);
-        if ((e = sweeps(b, U1, L, s)) != cudaSuccess) return e;
+        if ((e = sweeps(b, U1, L, s, 0, nullptr, 6)) != cudaSuccess) return e;
         batch_rk_fp64_kernel<3><<<b->nech, 256, 0, s>>>(b->U, U1, L, b->d_ech, b->sc);
     } else {
         // stage inputs A -> B -> A (A = float(U) from the time-step pass);
@@ -412,9 +424,9 @@ cudaError_t step_sequence(wcns_batch* b, cudaStream_t s)
         float* A = (float*)b->S;
         float* B = b->S2;
         float* L = (float*)b->L;
-        if ((e = sweeps(b, A, L, s, 1, B)) != cudaSuccess) return e;
-        if ((e = sweeps(b, B, L, s, 2, A)) != cudaSuccess) return e;
-        if ((e = sweeps(b, A, L, s, 3, nullptr)) != cudaSuccess) return e;
+        if ((e = sweeps(b, A, L, s, 1, B, 0)) != cudaSuccess) return e;
+        if ((e = sweeps(b, B, L, s, 2, A, 3)) != cudaSuccess) return e;
+        if ((e = sweeps(b, A, L, s, 3, nullptr, 6)) != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }
@@ -434,8 +446,6 @@ wcns_status wcns_batch_create(int ndim, double gamma, const wcns_scheme_params* 
     if (ndim < 1 || ndim > 3) return bfail(WCNS_ERR_INVALID, "ndim must be 1, 2 or 3");
     if (!(gamma > 1.0)) return bfail(WCNS_ERR_INVALID, "gamma must exceed 1");
     if (const char* why = scheme_params_error(prm)) return bfail(WCNS_ERR_INVALID, "%s", why);
-    if (prm->precision == WCNS_FP32 && prm->weights != WCNS_W_TENO)
-        return bfail(WCNS_ERR_INVALID, "FP32 batches take TENO weights only (JS, linear, Z: use WCNS_FP64)");
     if (max_nodes < 1 || max_instances < 1) return bfail(WCNS_ERR_INVALID, "capacities must be positive");
 
     wcns_batch* b = new wcns_batch();
@@ -459,6 +469,7 @@ wcns_status wcns_batch_create(int ndim, double gamma, const wcns_scheme_params* 
     const bool fp32 = b->precision == WCNS_FP32;
     if (!prepared_batch[dev & 63][fp32]) {
         e = fp32 ? prepare_sweeps_batch_fp32() : prepare_sweeps_batch_fp64();
+        if (e == cudaSuccess && fp32) e = prepare_sweeps_fp32_weights();
         if (e != cudaSuccess) { delete b; return bcuda(e, "prepare batched sweeps"); }
         prepared_batch[dev & 63][fp32] = true;
     }
@@ -473,6 +484,7 @@ wcns_status wcns_batch_create(int ndim, double gamma, const wcns_scheme_params* 
     if (e == cudaSuccess && fp32) e = cudaMalloc((void**)&b->S2, M * 4);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->sc, sizeof(StepScalars) * max_instances);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->active, 64);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->work, sizeof(unsigned int) * kWorkCounters);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->fallback, sizeof(long long) * max_instances);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_insts, sizeof(BatchInst) * max_instances);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_slots, sizeof(int) * max_instances);
@@ -502,6 +514,7 @@ wcns_status wcns_batch_destroy(wcns_batch* b)
     cudaFree(b->S2);
     cudaFree(b->sc);
     cudaFree(b->active);
+    cudaFree(b->work);
     cudaFree(b->fallback);
     cudaFree(b->d_insts);
     cudaFree(b->d_slots);
@@ -623,6 +636,75 @@ wcns_status wcns_batch_step(wcns_batch* b, int nsteps, int* active_out, void* st
         BCK(cudaStreamSynchronize(s), "sync");
         *active_out = b->exec ? act : 0;
     }
+    return WCNS_OK;
+}
+
+wcns_status wcns_batch_launch_mode(wcns_batch* b, int mode)
+{
+    set_last_error(nullptr);
+    if (!b || mode < 0 || mode > 1) return bfail(WCNS_ERR_INVALID, "wcns_batch_launch_mode: bad argument");
+    if (mode != b->launch_mode) {
+        b->launch_mode = mode;
+        if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+        if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    }
+    return WCNS_OK;
+}
+
+wcns_status wcns_batch_autotune(wcns_batch* b, int steps, int* mode_out, double* ms_per_step, void* stream)
+{
+    set_last_error(nullptr);
+    if (!b || steps < 1) return bfail(WCNS_ERR_INVALID, "wcns_batch_autotune: bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    BCK(cudaGetLastError(), "pending CUDA error");
+    if (b->dirty) {
+        BCK(cudaStreamSynchronize(s), "sync before table rebuild");
+        wcns_status st = rebuild(b);
+        if (st != WCNS_OK) return st;
+    }
+    double ms[2] = {0.0, 0.0};
+    if (b->nslots_active > 0) {
+        // trial steps on the live batch; state, clocks and counters are saved
+        // first and put back afterwards, so the results do not change
+        const size_t ub = sizeof(double) * (size_t)b->cap_elems;
+        const size_t cb = sizeof(StepScalars) * (size_t)b->cap_slots;
+        const size_t fbb = sizeof(long long) * (size_t)b->cap_slots;
+        char* save = nullptr;
+        if (cudaMalloc((void**)&save, ub + cb + fbb) != cudaSuccess) {
+            cudaGetLastError();
+            return bfail(WCNS_ERR_NOMEM, "wcns_batch_autotune: no room to save the batch state");
+        }
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaError_t e = cudaMemcpyAsync(save, b->U, ub, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(save + ub, b->sc, cb, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(save + ub + cb, b->fallback, fbb, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaEventCreate(&e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&e1);
+        for (int mode = 0; mode < 2 && e == cudaSuccess; ++mode) {
+            wcns_batch_launch_mode(b, mode);
+            wcns_status st = wcns_batch_step(b, 1, nullptr, stream);   // capture + warm-up
+            if (st != WCNS_OK) { e = cudaErrorUnknown; break; }
+            e = cudaEventRecord(e0, s);
+            for (int k = 0; k < steps && e == cudaSuccess; ++k) e = cudaGraphLaunch(b->exec, s);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float t = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+            ms[mode] = t / steps;
+            // restore
+            if (e == cudaSuccess) e = cudaMemcpyAsync(b->U, save, ub, cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(b->sc, save + ub, cb, cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(b->fallback, save + ub + cb, fbb, cudaMemcpyDeviceToDevice, s);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        cudaFree(save);
+        if (e != cudaSuccess) return bcuda(e, "wcns_batch_autotune");
+        wcns_batch_launch_mode(b, ms[1] < ms[0] ? 1 : 0);
+    }
+    if (mode_out) *mode_out = b->launch_mode;
+    if (ms_per_step) { ms_per_step[0] = ms[0]; ms_per_step[1] = ms[1]; }
     return WCNS_OK;
 }
 

@@ -272,8 +272,13 @@ __device__ __forceinline__ void cut_x2(float2 B0, float2 B1, float2 B2, float ep
 // 1/sc, sc = max |s| (floored at FLT_MIN so an all-zero field keeps every
 // stencil without a branch), and the second differences the mirrored
 // stencils share are formed once.  Returns (u_L, u_R) and the two flag words.
+// FAST: only the exact no-cut test runs; a side it cannot settle sets
+// `slow` (the caller then evaluates the face again with FAST off, where the
+// same test sends that side to the full cutoff), and the returned value is
+// Eq. 7, which is then also the full path's value whenever slow stays clear.
+template <bool FAST>
 __device__ __forceinline__ float2 select_interp_x2(float2 S0, float2 S1, float2 S2, float sqrt_eps,
-                                                   const SchemeConst& K, int& fL, int& fR)
+                                                   const SchemeConst& K, int& fL, int& fR, bool& slow)
 {
     float sc = fmaxf(fmaxf(fmaxf(fabsf(S0.x), fabsf(S0.y)), fmaxf(fabsf(S1.x), fabsf(S1.y))),
                      fmaxf(fabsf(S2.x), fabsf(S2.y)));
@@ -294,8 +299,17 @@ __device__ __forceinline__ float2 select_interp_x2(float2 S0, float2 S1, float2 
     const float2 B0 = fma2(D10, D10, mul2(D20, D20));   // Eq. 15
     const float2 B1 = fma2(D11, D11, mul2(D21, D21));
     const float2 B2 = fma2(D12, D12, mul2(D22, D22));
-    cut_x2(B0, B1, B2, eps_s, K, fL, fR);
-    if ((fL & fR) == 7) {                                 // Eq. 7 on both sides
+    if constexpr (FAST) {
+        // the no-cut test of cut_x2, the same expressions
+        const float2 d02 = sub2(B0, B2);
+        const float bmL = fminf(fminf(B0.x, B1.x), B2.x) + eps_s;
+        const float bmR = fminf(fminf(B0.y, B1.y), B2.y) + eps_s;
+        if (fabsf(d02.x) >= K.Kf * bmL || fabsf(d02.y) >= K.Kf * bmR) slow = true;
+        fL = fR = 7;
+    } else {
+        cut_x2(B0, B1, B2, eps_s, K, fL, fR);
+    }
+    if (FAST || (fL & fR) == 7) {                         // Eq. 7 on both sides
         float2 u = mul2(bc2(3.0f / 128), S0);
         u = fma2(bc2(-5.0f / 32), S1, u);
         u = fma2(bc2(45.0f / 64), S2, u);

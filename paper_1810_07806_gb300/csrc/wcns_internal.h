@@ -145,6 +145,30 @@ inline SchemeConst make_scheme_const(const wcns_scheme_params* p, double gamma)
     return K;
 }
 
+// Launch a batched sweep kernel k over ntiles tiles: one CTA per tile, or
+// (a.work set) the persistent form with as many CTAs as are resident on the
+// device (`resident`: a per-kernel cache, 0 until first computed).
+template <typename Kernel>
+inline cudaError_t launch_tiles(Kernel k, int threads, size_t smem, const SweepArgs& a, long long ntiles,
+                                cudaStream_t s, int& resident)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    long long grid = ntiles;
+    if (a.work != nullptr) {
+        if (resident == 0) {
+            int dev = 0, sms = 0, per = 0;
+            cudaError_t e = cudaGetDevice(&dev);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, threads, smem);
+            if (e != cudaSuccess) return e;
+            resident = sms * (per > 0 ? per : 1);
+        }
+        if (grid > resident) grid = resident;
+    }
+    k<<<(unsigned)grid, threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 // Launch one sweep of direction dir, FP64 or FP32 (input and output in the
 // sweep's precision).
 cudaError_t launch_sweep_fp64(int nd, int dir, int flux, const SweepArgs& a, cudaStream_t s);
@@ -171,6 +195,15 @@ cudaError_t launch_sweep_batch_fp32(int nd, int dir, int flux, const SweepArgs& 
                                     cudaStream_t s);
 cudaError_t prepare_sweeps_batch_fp64();
 cudaError_t prepare_sweeps_batch_fp32();
+// FP32 batched sweeps with the comparison weights (sweep_fp32_weights*.cu)
+cudaError_t launch_sweep_batch_fp32_weights(int wt, int nd, int dir, int flux, const SweepArgs& a,
+                                            long long ntiles, cudaStream_t s);
+cudaError_t launch_sweep_batch_fp32_w1(int nd, int dir, int flux, const SweepArgs& a, long long ntiles,
+                                       cudaStream_t s);
+cudaError_t launch_sweep_batch_fp32_w2(int nd, int dir, int flux, const SweepArgs& a, long long ntiles,
+                                       cudaStream_t s);
+cudaError_t launch_sweep_batch_fp32_w3(int nd, int dir, int flux, const SweepArgs& a, long long ntiles,
+                                       cudaStream_t s);
 // Raise the dynamic shared-memory limit of every sweep instance (once per device).
 cudaError_t prepare_sweeps_fp64();
 cudaError_t prepare_sweeps_fp32();

@@ -376,8 +376,6 @@ wcns_status wcns_batch_submit(wcns_server* sv, const wcns_request* req, uint64_t
     if (!(req->t_end >= 0.0)) return sfail(WCNS_ERR_INVALID, "t_end must be >= 0");
     if (!(req->gamma > 1.0)) return sfail(WCNS_ERR_INVALID, "gamma must exceed 1");
     if (const char* why = scheme_params_error(&req->params)) return sfail(WCNS_ERR_INVALID, "%s", why);
-    if (req->params.precision == WCNS_FP32 && req->params.weights != WCNS_W_TENO)
-        return sfail(WCNS_ERR_INVALID, "served FP32 requests take TENO weights only");
     if (grid_has_single_grid_features(&g))
         return sfail(WCNS_ERR_INVALID,
                      "served requests take periodic and transmissive boundaries without a body force");

@@ -97,6 +97,10 @@ struct SweepArgs {
     const BatchTile* tiles;
     const double* inst_dt;    // dt of instance i at inst_dt[i * dt_stride]
     int dt_stride;            // in doubles
+    // persistent batched launch (nullable): the tile counter this launch
+    // takes work from (zero at launch) and the number of tiles
+    unsigned int* work;
+    long long ntiles;
 };
 
 // 4-byte asynchronous global->shared copies (cp.async): the staging loads
@@ -159,12 +163,14 @@ __device__ __forceinline__ int sidx(int v, int l, int s)
 }
 
 // ---------------------------------------------------------------- FP64 face
-// (the FP64 face selects the weights at run time: WT is not used)
-template <int ND, int DIR, int FLUX, int WT>
-__device__ __forceinline__ void face_flux(double (&u)[6][ND + 2], const SweepArgs& a, const Ref32&, double* F,
+// (the FP64 face selects the weights at run time: WT is not used, and it
+// has its own division-free screen: FAST is not used)
+template <int ND, int DIR, int FLUX, int WT, bool FAST = false>
+__device__ __forceinline__ bool face_flux(double (&u)[6][ND + 2], const SweepArgs& a, const Ref32&, double* F,
                                           uint8_t* fl, bool& fell_back)
 {
     face_fp64<ND, DIR, FLUX>(u, a.K, F, fl, fell_back);
+    return true;
 }
 
 // ---------------------------------------------------------------- FP32 face
@@ -172,9 +178,12 @@ __device__ __forceinline__ void face_flux(double (&u)[6][ND + 2], const SweepArg
 // W_JS, W_LINEAR, W_Z in their own instances).  u holds U - U_r (Ref32);
 // every operation is written out (the FP32 units compile without
 // multiply-add contraction), so each instance of this code, single-grid or
-// batched, rounds the same way.
-template <int ND, int DIR, int FLUX, int WT>
-__device__ __forceinline__ void face_flux(float (&u)[6][ND + 2], const SweepArgs& a, const Ref32& R, float* F,
+// batched, rounds the same way.  FAST (TENO): the face is evaluated only if
+// every side of every field passes the exact no-cut test; otherwise the
+// function returns false early (F, fl not written) and the caller runs the
+// face again with FAST off.  A face evaluated either way gives the same bits.
+template <int ND, int DIR, int FLUX, int WT, bool FAST = false>
+__device__ __forceinline__ bool face_flux(float (&u)[6][ND + 2], const SweepArgs& a, const Ref32& R, float* F,
                                           uint8_t* fl, bool& fell_back)
 {
     constexpr int NV = ND + 2;
@@ -233,11 +242,15 @@ __device__ __forceinline__ void face_flux(float (&u)[6][ND + 2], const SweepArgs
             W2[m][NV - 1] = sub2(Ph, Qh);
         }
         float2 w2[NV];   // (u_L, u_R) of each characteristic field
+        bool slow = false;
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
             int fL, fR;
-            w2[k] = select_interp_x2(W2[0][k], W2[1][k], W2[2][k], a.sqrt_eps_f, a.K, fL, fR);
+            w2[k] = select_interp_x2<FAST>(W2[0][k], W2[1][k], W2[2][k], a.sqrt_eps_f, a.K, fL, fR, slow);
             fl[k] = (uint8_t)(fL | (fR << 3));
+        }
+        if constexpr (FAST) {
+            if (slow) return false;
         }
         // U = R w for both sides at once
         const float2 r = add2(add2(w2[0], w2[1]), w2[NV - 1]);
@@ -347,6 +360,7 @@ __device__ __forceinline__ void face_flux(float (&u)[6][ND + 2], const SweepArgs
             for (int v = 0; v < NV; ++v) F[v] = Fp[v] + Fm[v];
         }
     }
+    return true;
 }
 
 // f(U_{s+k}) - f(U_{s-k}) in direction DIR for the staged nodes of line l
@@ -386,8 +400,10 @@ __device__ __forceinline__ T stage_cvt(LT x)
     else return (T)x;
 }
 
-template <typename T, typename LT, int ND, int DIR, int FLUX, bool BATCH = false, int CFG = 0, int WT = 0>
-__global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) sweep_kernel(const SweepArgs a)
+// One tile of a sweep (tile: the index into the batch's tile table; single
+// grids take the tile from the launch coordinates).
+template <typename T, typename LT, int ND, int DIR, int FLUX, bool BATCH, int CFG, int WT>
+__device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
 {
     constexpr int NV = ND + 2;
     using G = TileGeom<T, ND, DIR, CFG>;
@@ -409,7 +425,7 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) swee
     float* Db = a.D;
     float* Sob = a.S_out;
     if constexpr (BATCH) {
-        const BatchTile bt = a.tiles[blockIdx.x];
+        const BatchTile bt = a.tiles[tile];
         const BatchInst& I = a.insts[bt.inst];
         Ub = reinterpret_cast<const LT*>(a.U) + I.off;
         Lb = reinterpret_cast<T*>(a.L) + I.off;
@@ -586,21 +602,25 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) swee
     }
     __syncthreads();
 
-    // (2) midpoint fluxes of faces j + 1/2, j = pos0 - 3 + f
+    // (2) midpoint fluxes of faces j + 1/2, j = pos0 - 3 + f.  3D FP32 TENO
+    // sweeps defer a face whose selection needs the full cutoff (Eq. 16-18)
+    // to a second pass over a shared list: the first pass carries only the
+    // exact no-cut test, and the few deferred faces then run the full code
+    // side by side in whole warps instead of as divergent branches (5% off
+    // the Taylor-Green step).  A deferred face is evaluated twice, so where
+    // cuts are frequent (shocked 1D batches: 5% slower) the single pass stays.
+    constexpr bool kDefer = sizeof(T) == 4 && WT == W_TENO && ND == 3;
+    __shared__ int s_slow[kDefer ? TL * NF : 1];
+    __shared__ int s_nslow;
+    if (kDefer && threadIdx.x == 0) s_nslow = 0;
     int fb = 0;
-    for (int e = threadIdx.x; e < TL * NF; e += blockDim.x) {
-        int l, f;
-        if (DIR == 0) { f = e % NF; l = e / NF; } else { l = e % TL; f = e / TL; }
-        if (l >= lcount || f >= nfaces) continue;
-        T u[6][NV];
+    auto load_face = [&](int l, int f, T (&u)[6][NV]) {
 #pragma unroll
         for (int m = 0; m < 6; ++m)
 #pragma unroll
             for (int v = 0; v < NV; ++v) u[m][v] = sS[sidx<DIR, TL, P>(v, l, f + m)];
-        T F[NV];
-        uint8_t fl[NV];
-        bool fell = false;
-        face_flux<ND, DIR, FLUX, WT>(u, a, R, F, fl, fell);
+    };
+    auto store_face = [&](int l, int f, const T (&F)[NV], const uint8_t (&fl)[NV], bool fell) {
         // faces shared with the next tile are owned (counted, flagged) by it
         const bool owned = f < TS || pos0 + TS >= nd;
         fb += (fell && owned) ? 1 : 0;
@@ -612,6 +632,38 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) swee
 #pragma unroll
             for (int k = 0; k < NV; ++k)
                 a.flags[((long long)k * lines + line0 + l) * (nd + 5) + j3] = fl[k];
+        }
+    };
+    if constexpr (kDefer) __syncthreads();   // s_nslow is set
+    for (int e = threadIdx.x; e < TL * NF; e += blockDim.x) {
+        int l, f;
+        if (DIR == 0) { f = e % NF; l = e / NF; } else { l = e % TL; f = e / TL; }
+        if (l >= lcount || f >= nfaces) continue;
+        T u[6][NV];
+        load_face(l, f, u);
+        T F[NV];
+        uint8_t fl[NV];
+        bool fell = false;
+        if (!face_flux<ND, DIR, FLUX, WT, kDefer>(u, a, R, F, fl, fell)) {
+            s_slow[atomicAdd(&s_nslow, 1)] = e;
+            continue;
+        }
+        store_face(l, f, F, fl, fell);
+    }
+    if constexpr (kDefer) {
+        __syncthreads();
+        const int nslow = s_nslow;
+        for (int k = threadIdx.x; k < nslow; k += blockDim.x) {
+            const int e = s_slow[k];
+            int l, f;
+            if (DIR == 0) { f = e % NF; l = e / NF; } else { l = e % TL; f = e / TL; }
+            T u[6][NV];
+            load_face(l, f, u);
+            T F[NV];
+            uint8_t fl[NV];
+            bool fell = false;
+            face_flux<ND, DIR, FLUX, WT, false>(u, a, R, F, fl, fell);
+            store_face(l, f, F, fl, fell);
         }
     }
     if (fb) atomicAdd((unsigned long long*)fbp, (unsigned long long)fb);
@@ -735,6 +787,31 @@ __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) swee
     };
     if (diff == DIFF_MD && !a.source) node_phase(std::false_type{});
     else node_phase(std::true_type{});
+}
+
+// The sweep kernel.  Single grids and tile-table batches run one tile per
+// CTA.  Persistent batched launches (a.work non-null) start a fixed number of
+// CTAs, each of which takes tiles from a device counter (atomicAdd) until the
+// table is exhausted; no CTA waits for another, so nothing can hang.
+template <typename T, typename LT, int ND, int DIR, int FLUX, bool BATCH = false, int CFG = 0, int WT = 0>
+__global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) sweep_kernel(const SweepArgs a)
+{
+    if constexpr (BATCH) {
+        if (a.work != nullptr) {
+            __shared__ long long s_tile;
+            for (;;) {
+                __syncthreads();   // the previous tile is done with shared memory
+                if (threadIdx.x == 0) s_tile = (long long)atomicAdd(a.work, 1u);
+                __syncthreads();
+                const long long t = s_tile;
+                if (t >= a.ntiles) return;
+                sweep_tile<T, LT, ND, DIR, FLUX, BATCH, CFG, WT>(a, t);
+            }
+        }
+        sweep_tile<T, LT, ND, DIR, FLUX, BATCH, CFG, WT>(a, blockIdx.x);
+    } else {
+        sweep_tile<T, LT, ND, DIR, FLUX, BATCH, CFG, WT>(a, 0);
+    }
 }
 
 }  // namespace wcns

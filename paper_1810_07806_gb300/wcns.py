@@ -398,6 +398,26 @@ class Batch:
         check(lib().wcns_batch_step(self.h, int(nsteps), C.byref(a), _stream(stream)))
         return a.value
 
+    def launch_mode(self, mode):
+        """0: one CTA per tile (tile table); 1: persistent CTAs taking tiles
+        from a device counter."""
+        L = lib()
+        L.wcns_batch_launch_mode.argtypes = [C.c_void_p, C.c_int]
+        L.wcns_batch_launch_mode.restype = C.c_int
+        check(L.wcns_batch_launch_mode(self.h, int(mode)))
+
+    def autotune(self, steps=5, stream=None):
+        """Time both launch forms on the current instances, keep the faster
+        (state unchanged).  Returns (mode kept, [ms per step of each form])."""
+        L = lib()
+        L.wcns_batch_autotune.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double),
+                                          C.c_void_p]
+        L.wcns_batch_autotune.restype = C.c_int
+        m = C.c_int()
+        ms = (C.c_double * 2)()
+        check(L.wcns_batch_autotune(self.h, int(steps), C.byref(m), ms, _stream(stream)))
+        return m.value, [ms[0], ms[1]]
+
     def run(self, max_steps=10 ** 9, check_every=32, stream=None):
         s = C.c_int()
         check(lib().wcns_batch_run(self.h, int(min(max_steps, 2 ** 31 - 1)), int(check_every), C.byref(s),

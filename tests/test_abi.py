@@ -95,14 +95,15 @@ def test_scalar_run_rejects_bad_time_arguments():
     assert L.wcns_scalar_run(0, C.byref(p), 16, 0.1, 1.0, 0, 1, ptr, 16, None) == wcns.OK
 
 
-def test_fp32_batch_rejects_comparison_weights_without_a_gpu():
+def test_batch_create_rejects_bad_arguments_without_a_gpu():
     L = wcns.lib()
     L.wcns_batch_create.argtypes = [C.c_int, C.c_double, C.POINTER(wcns.SchemeParams), C.c_longlong, C.c_int,
                                     C.POINTER(C.c_void_p)]
-    for w in (wcns.W_JS, wcns.W_LINEAR, wcns.W_Z):
-        p = wcns.default_params(weights=w, precision=wcns.FP32)
+    for nd, mx, ni, kw in ((4, 1000, 4, {}), (1, 0, 4, {}), (1, 1000, 0, {}), (1, 1000, 4, dict(weights=7)),
+                           (1, 1000, 4, dict(precision=2))):
+        p = wcns.default_params(**kw)
         h = C.c_void_p()
-        assert L.wcns_batch_create(1, 1.4, C.byref(p), 1000, 4, C.byref(h)) == wcns.ERR_INVALID
+        assert L.wcns_batch_create(nd, 1.4, C.byref(p), mx, ni, C.byref(h)) == wcns.ERR_INVALID
         assert h.value is None
 
 

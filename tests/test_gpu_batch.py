@@ -135,3 +135,47 @@ def test_batch_slots_and_arena_are_reused():
         Ua, ta, sa = _alone(pbs[k], wcns.FP64, pbs[k].t_end)
         assert np.array_equal(Ub, Ua)
     b.close()
+
+
+@pytest.mark.parametrize("precision", [wcns.FP64, wcns.FP32])
+def test_persistent_launch_and_autotune_give_identical_results(precision):
+    """The persistent launch form (CTAs taking tiles from a device counter)
+    and the tile-table form compute the same faces: end states bit-identical;
+    the autotuner's trial steps leave the batch's results unchanged."""
+    pbs = _uneven_1d(10, 3)
+    out = []
+    for mode in (0, 1, "tuned"):
+        b = wcns.Batch(1, max_nodes=sum(p.cells for p in pbs), max_instances=len(pbs), precision=precision)
+        slots = [b.add(pb) for pb in pbs]
+        if mode == "tuned":
+            b.step(3)
+            chosen, ms = b.autotune(steps=2)
+            assert chosen in (0, 1) and ms[0] > 0 and ms[1] > 0
+        else:
+            b.launch_mode(mode)
+        b.run(check_every=8)
+        out.append([b.read(k) for k in slots])
+        b.close()
+    for k in range(len(pbs)):
+        for other in (1, 2):
+            assert np.array_equal(out[0][k][0], out[other][k][0])
+            assert out[0][k][1:] == out[other][k][1:]
+
+
+@pytest.mark.parametrize("weights", [wcns.W_JS, wcns.W_LINEAR, wcns.W_Z])
+def test_fp32_batch_with_comparison_weights_equals_instances_alone(weights):
+    """FP32 batches take the comparison weights (Eq. 14, Eq. 13, WCNS-Z):
+    each instance bit-identical to the single-grid FP32 solver."""
+    pbs = _uneven_1d(4, 8)
+    b = wcns.Batch(1, max_nodes=sum(p.cells for p in pbs), max_instances=len(pbs), precision=wcns.FP32,
+                   weights=weights)
+    slots = [b.add(pb) for pb in pbs]
+    b.run(check_every=8)
+    for pb, k in zip(pbs, slots):
+        Ub, tb, sb = b.read(k)
+        s = wcns.Solver.for_problem(pb, precision=wcns.FP32, weights=weights)
+        U = torch.from_numpy(pb.U0.copy()).cuda()
+        ta, sa = s.advance(U, pb.t_end, check_every=16)
+        s.close()
+        assert (tb, sb) == (ta, sa) and np.array_equal(Ub, U.cpu().numpy())
+    b.close()

@@ -130,16 +130,22 @@ def test_request_larger_than_the_budget_is_rejected():
 def test_unservable_requests_are_rejected_at_submit():
     """Requests the batched engine cannot run fail at submit, with a reason:
     single-grid features (reflecting or fixed boundaries, a body force) and
-    FP32 with the comparison weights."""
+    bad scheme parameters.  The comparison weights are served in both
+    precisions, each result equal to the same problem alone."""
     sv = wcns.Server(hbm_budget_bytes=1 << 28, max_instances_per_class=4, steps_per_tick=2)
     with pytest.raises(wcns.WcnsError):
         sv.submit(inputs.rayleigh_taylor(8), tag=1, t_end=0.01)
     with pytest.raises(wcns.WcnsError):
-        sv.submit(inputs.four_quadrant(32, t_end=0.01), tag=2, precision=wcns.FP32, weights=wcns.W_JS)
-    with pytest.raises(wcns.WcnsError):
         sv.submit(inputs.four_quadrant(32, t_end=0.01), tag=3, flux=9)
-    # the same problem with FP64 JS weights is served
-    sv.submit(inputs.four_quadrant(32, t_end=0.01), tag=4, weights=wcns.W_JS)
-    got = _drain(sv, 1, timeout_s=60)
-    assert got[4]["status"] == wcns.OK
+    pb = inputs.four_quadrant(32, t_end=0.01)
+    sv.submit(pb, tag=4, weights=wcns.W_JS)
+    sv.submit(pb, tag=5, weights=wcns.W_Z, precision=wcns.FP32)
+    got = _drain(sv, 2, timeout_s=60)
+    assert got[4]["status"] == wcns.OK and got[5]["status"] == wcns.OK
+    for tag, prec, w in ((4, wcns.FP64, wcns.W_JS), (5, wcns.FP32, wcns.W_Z)):
+        s = wcns.Solver.for_problem(pb, precision=prec, weights=w)
+        U = torch.from_numpy(pb.U0.copy()).cuda()
+        s.advance(U, pb.t_end)
+        assert np.array_equal(got[tag]["U"], U.cpu().numpy())
+        s.close()
     sv.close()
