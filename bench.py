@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--side-lo", type=int, default=128, help="serve: smallest grid side")
     ap.add_argument("--side-hi", type=int, default=1024, help="serve: largest grid side")
     ap.add_argument("--no-serve", action="store_true", help="skip the short serving replay of the default line")
+    ap.add_argument("--l1-max-side", type=int, default=1 << 30,
+                    help="serve: FP32 error against FP64 only for requests up to this side (FP64 solves are slow)")
     ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "fp64"],
                     help="single-grid workloads: the path timed (auto: the workload's default)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain-path line")
@@ -607,7 +609,7 @@ def serve_replay(trace, steps_per_tick=16):
             "max_queue": int(max(qdepth) if qdepth else 0), "stats": st}
 
 
-def plain_replay(trace, fp64_reference=True):
+def plain_replay(trace, fp64_reference=True, ref_max_side=1 << 30):
     """The plain baseline on the same trace: one request at a time, in arrival
     order, each solved alone by the single-grid path in its own precision
     (host state in, wcns_advance, host state out).  Latencies are those of a
@@ -634,7 +636,7 @@ def plain_replay(trace, fp64_reference=True):
         busy += solve
         cells += pb.cells * 3 * steps
         out.append({"U": Uh, "steps": steps, "latency": finish - r.arrival_s, "solve_s": solve})
-        if fp64_reference and r.fp32:
+        if fp64_reference and r.fp32 and r.side <= ref_max_side:
             s = wcns.Solver.for_problem(pb, precision=wcns.FP64, cfl=0.5)
             U = torch.from_numpy(pb.U0.copy()).cuda()
             s.advance(U, r.t_end, check_every=64)
@@ -707,7 +709,7 @@ def serve_arm(args):
     from paper_1810_07806_gb300 import inputs
     trace = inputs.serving_trace(args.requests, rate=args.rate, side_lo=args.side_lo, side_hi=args.side_hi)
     served = serve_replay(trace)
-    plain = plain_replay(trace)
+    plain = plain_replay(trace, ref_max_side=args.l1_max_side)
     summ = serving_summary(trace, served, plain)
     print(json.dumps({
         "metric": METRIC, "value": summ["served"]["value"], "unit": UNIT, "n_gpus": 1,
@@ -715,7 +717,8 @@ def serve_arm(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": "serving_four_quadrant_2d_trace", "requests": len(trace), "rate_per_s": args.rate,
                    "seed": 7806, "side": "log-uniform %d..%d" % (args.side_lo, args.side_hi),
-                   "t_end": "U[0.1,0.3]", "fp32_share": 0.5},
+                   "t_end": "U[0.1,0.3]", "fp32_share": 0.5,
+                   "fp32_error_for_sides_up_to": min(args.l1_max_side, args.side_hi)},
         **summ}))
 
 
