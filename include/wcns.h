@@ -73,8 +73,9 @@ enum { WCNS_FP64 = 0, WCNS_FP32 = 1 };
  * rho u_1 .. rho u_ndim, E; rho > 0, p > 0).  gravity is a body force per
  * unit mass: the RHS gains (0, rho g, rho u.g) (Sec. 3.9: g = (0, 1)).
  * Axes >= ndim are ignored.  n[a] >= 2 (transmissive) or >= 1 (periodic).
- * Reflecting and fixed sides and gravity are single-grid features (batches
- * and the server reject them). */
+ * Single grids, batches and the server take every boundary kind and the
+ * body force; the allocation-free step takes transmissive and periodic
+ * sides without a body force. */
 typedef struct {
     int ndim;
     int n[3];

@@ -176,6 +176,7 @@ struct BatchSlot {
     int n[3] = {1, 1, 1};
     int periodic[3] = {0, 0, 0};
     double h[3] = {1, 1, 1};
+    GridInfo G;            // boundary kinds, fixed states, body force
     long long N = 0;
     long long off = 0;     // element offset in the arenas
     long long elems = 0;   // reserved elements (nv * N rounded up)
@@ -218,6 +219,7 @@ struct wcns_batch {
     // CTAs taking tiles from device counters (one counter per sweep of a step)
     int launch_mode = 0;
     unsigned int* work = nullptr;
+    bool any_gravity = false;   // some instance has a body force (the last sweep adds it)
 };
 
 namespace {
@@ -294,6 +296,7 @@ wcns_status rebuild(wcns_batch* b)
     std::vector<BatchTile> tiles[3];
     std::vector<NodeChunk> nch;
     std::vector<ElemChunk> ech;
+    bool any_gravity = false;
     for (int i = 0; i < b->cap_slots; ++i) {
         const BatchSlot& s = b->slots[i];
         BatchInst& I = insts[i];
@@ -308,7 +311,14 @@ wcns_status rebuild(wcns_batch* b)
             I.h[a] = s.h[a];
             I.inv_h[a] = a < b->ndim ? 1.0 / s.h[a] : 0.0;
             I.inv_hf[a] = (float)I.inv_h[a];
+            for (int sd = 0; sd < 2; ++sd) {
+                I.bc[a][sd] = s.G.bc[a][sd];
+                for (int v = 0; v < 5; ++v) I.bcs[a][sd][v] = s.G.bc_state[a][sd][v];
+            }
+            I.grav[a] = s.G.gravity[a];
         }
+        I.has_grav = s.G.has_gravity ? 1 : 0;
+        if (s.G.has_gravity) any_gravity = true;
         for (int d = 0; d < b->ndim; ++d) {
             if (fp32) build_tiles<float>(b->ndim, d, tiles[d], i, s);
             else build_tiles<double>(b->ndim, d, tiles[d], i, s);
@@ -338,6 +348,7 @@ wcns_status rebuild(wcns_batch* b)
     b->nnch = (int)nch.size();
     b->nech = (int)ech.size();
     b->nslots_active = (int)active.size();
+    b->any_gravity = any_gravity;
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
     if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
     b->dirty = false;
@@ -369,6 +380,9 @@ cudaError_t sweeps(wcns_batch* b, const void* Uin, void* L, cudaStream_t s, int 
             a.work = b->work + counter0 + k;
             a.ntiles = b->ntiles[d];
         }
+        // the last sweep of an RHS adds the body force of the instances that
+        // have one (as a single grid's last sweep)
+        a.source = b->any_gravity && k == b->ndim - 1;
         if (fuse_stage && d == 0) {
             a.fuse_stage = fuse_stage;
             a.U0 = b->U;
@@ -534,23 +548,16 @@ wcns_status wcns_batch_add(wcns_batch* b, const wcns_grid* g, const double* U0, 
     if (!b || !g || !U0 || !slot_out) return bfail(WCNS_ERR_INVALID, "wcns_batch_add: null argument");
     if (g->ndim != b->ndim) return bfail(WCNS_ERR_INVALID, "grid dimension differs from the batch's");
     if (!(t_end >= 0.0)) return bfail(WCNS_ERR_INVALID, "t_end must be >= 0");
-    if (grid_has_single_grid_features(g))
-        return bfail(WCNS_ERR_INVALID, "batches take periodic and transmissive boundaries without a body force");
-    for (int a = 0; a < b->ndim; ++a)
-        for (int sd = 0; sd < 2; ++sd)
-            if (g->bc[a][sd] != WCNS_BC_PERIODIC && g->bc[a][sd] != WCNS_BC_TRANSMISSIVE)
-                return bfail(WCNS_ERR_INVALID, "unknown boundary kind");
+    // the single-grid rules: boundary kinds (transmissive, periodic,
+    // reflecting, fixed state), node spacing, fixed states, body force
     BatchSlot s;
-    s.N = 1;
+    char why[256];
+    if (const char* msg = grid_error(g, b->gamma, s.G, why, sizeof why)) return bfail(WCNS_ERR_INVALID, "%s", msg);
+    s.N = s.G.N;
     for (int a = 0; a < b->ndim; ++a) {
-        const int per = g->bc[a][0] == WCNS_BC_PERIODIC;
-        if ((g->bc[a][1] == WCNS_BC_PERIODIC) != per)
-            return bfail(WCNS_ERR_INVALID, "periodic must be set on both sides of an axis");
-        if (g->n[a] < (per ? 1 : 2) || !(g->hi[a] > g->lo[a])) return bfail(WCNS_ERR_INVALID, "bad axis");
-        s.n[a] = g->n[a];
-        s.periodic[a] = per;
-        s.h[a] = (g->hi[a] - g->lo[a]) / (per ? g->n[a] : g->n[a] - 1);
-        s.N *= g->n[a];
+        s.n[a] = s.G.n[a];
+        s.periodic[a] = s.G.periodic[a];
+        s.h[a] = s.G.h[a];
     }
     if (b->ndim == 3 && (s.n[1] > 65535 || s.n[2] > 65535)) return bfail(WCNS_ERR_INVALID, "grid too large");
     int slot = -1;

@@ -376,13 +376,12 @@ wcns_status wcns_batch_submit(wcns_server* sv, const wcns_request* req, uint64_t
     if (!(req->t_end >= 0.0)) return sfail(WCNS_ERR_INVALID, "t_end must be >= 0");
     if (!(req->gamma > 1.0)) return sfail(WCNS_ERR_INVALID, "gamma must exceed 1");
     if (const char* why = scheme_params_error(&req->params)) return sfail(WCNS_ERR_INVALID, "%s", why);
-    if (grid_has_single_grid_features(&g))
-        return sfail(WCNS_ERR_INVALID,
-                     "served requests take periodic and transmissive boundaries without a body force");
-    for (int a = 0; a < g.ndim; ++a)
-        for (int sd = 0; sd < 2; ++sd)
-            if (g.bc[a][sd] != WCNS_BC_PERIODIC && g.bc[a][sd] != WCNS_BC_TRANSMISSIVE)
-                return sfail(WCNS_ERR_INVALID, "unknown boundary kind");
+    {
+        GridInfo G;
+        char why[256];
+        if (const char* msg = grid_error(&g, req->gamma, G, why, sizeof why))
+            return sfail(WCNS_ERR_INVALID, "%s", msg);
+    }
     Pending p;
     p.req = *req;
     const long long N = nodes_of(g);

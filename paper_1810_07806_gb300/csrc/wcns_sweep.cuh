@@ -35,6 +35,10 @@ struct BatchInst {
     double h[3];              // node spacing per axis
     double inv_h[3];          // 1 / h per axis
     float inv_hf[3];
+    int bc[3][2];             // boundary kind of each side (BC_*)
+    double bcs[3][2][5];      // fixed states (conserved variables)
+    double grav[3];           // body force per unit mass
+    int has_grav;             // some component of grav is non-zero
 };
 
 struct BatchTile {
@@ -84,10 +88,11 @@ struct SweepArgs {
     double* U0;
     float* D;
     float* S_out;
-    // boundary rule of a non-periodic direction (single grids; batches leave
-    // both sides transmissive): WCNS_BC_* kinds of the low and high side and
-    // the fixed states; the last sweep of an RHS adds the body-force source
-    // (0, rho g, rho u.g) when source is set
+    // boundary rule of a non-periodic direction (single grids; batched
+    // sweeps read their instance's): WCNS_BC_* kinds of the low and high side
+    // and the fixed states; the last sweep of an RHS adds the body-force
+    // source (0, rho g, rho u.g) when source is set (batched: for the
+    // instances with a body force)
     int bc_lo, bc_hi;
     double bcs[2][5];
     int source;
@@ -424,9 +429,19 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
     double* U0b = a.U0;
     float* Db = a.D;
     float* Sob = a.S_out;
+    // boundary rule of this direction's sides, fixed states, body force
+    int bcl = a.bc_lo, bch = a.bc_hi;
+    const double(*bcs)[5] = a.bcs;
+    const double* gravp = a.grav;
+    int source = a.source;
     if constexpr (BATCH) {
         const BatchTile bt = a.tiles[tile];
         const BatchInst& I = a.insts[bt.inst];
+        bcl = I.bc[DIR][0];
+        bch = I.bc[DIR][1];
+        bcs = I.bcs[DIR];
+        gravp = I.grav;
+        source = a.source && I.has_grav;
         Ub = reinterpret_cast<const LT*>(a.U) + I.off;
         Lb = reinterpret_cast<T*>(a.L) + I.off;
         if (a.fuse_stage) {
@@ -516,7 +531,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
     const bool wrap_mod = periodic && nd < P;
     // reflecting walls (ghost -1-k mirrors node k, normal momentum negated;
     // the axis has at least 5 nodes) and fixed states: synchronous copies
-    const bool bc_special = !BATCH && (a.bc_lo >= BC_REFLECTING || a.bc_hi >= BC_REFLECTING);
+    const bool bc_special = bcl >= BC_REFLECTING || bch >= BC_REFLECTING;
     for (int e = threadIdx.x; e < TL * P; e += blockDim.x) {
         int l, s;
         if (DIR == 0) { s = e % P; l = e / P; } else { l = e % TL; s = e / TL; }
@@ -526,9 +541,9 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
             if (wrap_mod) { p %= nd; if (p < 0) p += nd; }
             else p = p < 0 ? p + nd : (p >= nd ? p - nd : p);
         } else if (bc_special && (p < 0 || p >= nd)) {
-            const int kind = p < 0 ? a.bc_lo : a.bc_hi;
+            const int kind = p < 0 ? bcl : bch;
             if (kind == BC_FIXED) {
-                const double* st = a.bcs[p < 0 ? 0 : 1];
+                const double* st = bcs[p < 0 ? 0 : 1];
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
                     const double r = v == 0 ? ref_rho : (v == NV - 1 ? ref_E : 0.0);
@@ -697,14 +712,14 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
                 for (int v = 0; v < NV; ++v) d1[v] = d2[v] = S[v] = T(0);
                 if (diff != DIFF_MD) node_flux_diff<ND, DIR, TL, P>(sS, l, t + GHOST, 1, a.K, R, d1);
                 if (diff == DIFF_HWCNS) node_flux_diff<ND, DIR, TL, P>(sS, l, t + GHOST, 2, a.K, R, d2);
-                if (a.source) {
+                if (source) {
                     // (0, rho g_a, sum_a g_a m_a), the sum from 0 in axis order
                     T rho = sS[sidx<DIR, TL, P>(0, l, t + GHOST)];
                     if constexpr (sizeof(T) == 4) rho = rho + R.rho;
                     T se = T(0);
 #pragma unroll
                     for (int b = 0; b < ND; ++b) {
-                        const T gb = T(a.grav[b]), mb = sS[sidx<DIR, TL, P>(1 + b, l, t + GHOST)];
+                        const T gb = T(gravp[b]), mb = sS[sidx<DIR, TL, P>(1 + b, l, t + GHOST)];
                         if constexpr (sizeof(T) == 8) {
                             S[1 + b] = mul_(gb, rho);
                             se = add_(se, mul_(gb, mb));
@@ -729,7 +744,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
                     else q = md_fp64(f0, f1, f2, f3, f4, f5, ih);
                     double lval = a.accumulate ? sub_(L[v * N + g], q) : -q;
                     if constexpr (ALT) {
-                        if (a.source && v > 0) lval = add_(lval, S[v]);   // after every direction
+                        if (source && v > 0) lval = add_(lval, S[v]);   // after every direction
                     }
                     L[v * N + g] = lval;
                 } else {
@@ -751,7 +766,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
                         lv = -fp * ih;
                     }
                     if constexpr (ALT) {
-                        if (a.source) lv += S[v];
+                        if (source) lv += S[v];
                     }
                     if constexpr (G::FUSE) {
                         if (a.fuse_stage) {
@@ -785,7 +800,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
             }
         }
     };
-    if (diff == DIFF_MD && !a.source) node_phase(std::false_type{});
+    if (diff == DIFF_MD && !source) node_phase(std::false_type{});
     else node_phase(std::true_type{});
 }
 

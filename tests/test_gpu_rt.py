@@ -133,11 +133,31 @@ def test_rayleigh_taylor_fp32_close_to_oracle_and_symmetric():
     assert asym <= max(10 * np.max(np.abs(b[0] - a[0])), 1e-5), asym
 
 
-def test_batches_and_server_reject_single_grid_features():
-    pb = inputs.rayleigh_taylor(8)
-    b = wcns.Batch(2, max_nodes=pb.cells, max_instances=1)
-    with pytest.raises(wcns.WcnsError):
-        b.add(pb, t_end=0.1)
+@pytest.mark.parametrize("precision", [wcns.FP64, wcns.FP32])
+def test_rayleigh_taylor_in_a_batch_equals_the_single_grid(precision):
+    """Reflecting walls, fixed states and the body force in a batch (and
+    beside a quadrant instance without them): each instance gives the
+    single-grid solver's result bit for bit; in FP64 that is the oracle's."""
+    rt = inputs.rayleigh_taylor(16)
+    others = [inputs.rayleigh_taylor(8), _mixed(2, (23, 17), 5, (R, F), (F, R), (0.0, 1.0, 0.0))]
+    for pb in others:
+        pb.gamma = rt.gamma
+    pbs = [rt] + others
+    b = wcns.Batch(2, max_nodes=sum(p.cells for p in pbs), max_instances=len(pbs), gamma=rt.gamma,
+                   precision=precision)
+    slots = [b.add(pb, t_end=0.05) for pb in pbs]
+    b.run(check_every=8)
+    for pb, k in zip(pbs, slots):
+        Ub, tb, sb = b.read(k)
+        s = wcns.Solver.for_problem(pb, precision=precision, cfl=0.5)
+        U = torch.from_numpy(pb.U0.copy()).to(DEV)
+        ta, sa = s.advance(U, 0.05, check_every=16)
+        s.close()
+        assert (tb, sb) == (ta, sa) and np.array_equal(Ub, U.cpu().numpy()), pb.name
+        if precision == wcns.FP64:
+            Uo = pb.U0.copy()
+            O.euler_run(ora_cfg(pb, "roe"), Uo, 0.5, 0.05)
+            assert np.array_equal(Ub, Uo), pb.name
     b.close()
 
 

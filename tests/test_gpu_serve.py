@@ -127,25 +127,29 @@ def test_request_larger_than_the_budget_is_rejected():
     sv.close()
 
 
-def test_unservable_requests_are_rejected_at_submit():
-    """Requests the batched engine cannot run fail at submit, with a reason:
-    single-grid features (reflecting or fixed boundaries, a body force) and
-    bad scheme parameters.  The comparison weights are served in both
-    precisions, each result equal to the same problem alone."""
+def test_bad_requests_are_rejected_and_every_scheme_is_served():
+    """Requests with bad parameters fail at submit, with a reason.  The
+    comparison weights (both precisions) and the Rayleigh-Taylor boundaries
+    and body force are served, each result equal to the same problem solved
+    alone by the single-grid path."""
     sv = wcns.Server(hbm_budget_bytes=1 << 28, max_instances_per_class=4, steps_per_tick=2)
     with pytest.raises(wcns.WcnsError):
-        sv.submit(inputs.rayleigh_taylor(8), tag=1, t_end=0.01)
-    with pytest.raises(wcns.WcnsError):
         sv.submit(inputs.four_quadrant(32, t_end=0.01), tag=3, flux=9)
+    with pytest.raises(wcns.WcnsError):
+        sv.submit(inputs.rayleigh_taylor(1), tag=6, t_end=0.01)   # reflecting axis of 1 node
     pb = inputs.four_quadrant(32, t_end=0.01)
+    rt = inputs.rayleigh_taylor(8)
     sv.submit(pb, tag=4, weights=wcns.W_JS)
     sv.submit(pb, tag=5, weights=wcns.W_Z, precision=wcns.FP32)
-    got = _drain(sv, 2, timeout_s=60)
-    assert got[4]["status"] == wcns.OK and got[5]["status"] == wcns.OK
-    for tag, prec, w in ((4, wcns.FP64, wcns.W_JS), (5, wcns.FP32, wcns.W_Z)):
-        s = wcns.Solver.for_problem(pb, precision=prec, weights=w)
-        U = torch.from_numpy(pb.U0.copy()).cuda()
-        s.advance(U, pb.t_end)
-        assert np.array_equal(got[tag]["U"], U.cpu().numpy())
+    sv.submit(rt, tag=7, t_end=0.02)
+    sv.submit(rt, tag=8, t_end=0.02, precision=wcns.FP32)
+    got = _drain(sv, 4, timeout_s=60)
+    for tag, prob, prec, w, t_end in ((4, pb, wcns.FP64, wcns.W_JS, pb.t_end), (5, pb, wcns.FP32, wcns.W_Z, pb.t_end),
+                                      (7, rt, wcns.FP64, wcns.W_TENO, 0.02), (8, rt, wcns.FP32, wcns.W_TENO, 0.02)):
+        assert got[tag]["status"] == wcns.OK
+        s = wcns.Solver.for_problem(prob, precision=prec, weights=w)
+        U = torch.from_numpy(prob.U0.copy()).cuda()
+        s.advance(U, t_end)
+        assert np.array_equal(got[tag]["U"], U.cpu().numpy()), tag
         s.close()
     sv.close()
