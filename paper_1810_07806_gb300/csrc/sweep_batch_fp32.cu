@@ -11,10 +11,12 @@ static cudaError_t go(const SweepArgs& a, long long ntiles, cudaStream_t s, bool
 {
     using G = TileGeom<float, ND, DIR>;
     auto k = sweep_kernel<float, float, ND, DIR, FLUX, true>;
-    const size_t smem = G::smem_bytes();
-    if (prepare) return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    static int resident = 0;
-    return launch_tiles(k, G::THREADS, smem, a, ntiles, s, resident);
+    if (prepare)
+        return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_bytes());
+    SweepArgs b = a;
+    b.alias_L = sweep_alias_L(a) ? 1 : 0;
+    static int resident[2] = {0, 0};
+    return launch_tiles(k, G::THREADS, G::smem_bytes(b.alias_L != 0), b, ntiles, s, resident[b.alias_L]);
 }
 
 template <int FLUX>

@@ -16,8 +16,11 @@ static cudaError_t go(const SweepArgs& a, cudaStream_t s, bool prepare)
     constexpr int CFG = ND == 1 ? 0 : SWEEP_CFG;
     using G = TileGeom<float, ND, DIR, CFG>;
     auto k = sweep_kernel<float, float, ND, DIR, FLUX, false, CFG>;
-    const size_t smem = G::smem_bytes();
-    if (prepare) return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (prepare)
+        return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_bytes());
+    SweepArgs b = a;
+    b.alias_L = sweep_alias_L(a) ? 1 : 0;
+    const size_t smem = G::smem_bytes(b.alias_L != 0);
     dim3 grid;
     const int nd = a.n[DIR];
     if (DIR == 0) {
@@ -27,7 +30,7 @@ static cudaError_t go(const SweepArgs& a, cudaStream_t s, bool prepare)
         grid = dim3((a.n[0] + G::TL - 1) / G::TL, (nd + G::TS - 1) / G::TS,
                     DIR == 1 ? (ND == 3 ? a.n[2] : 1) : a.n[1]);
     }
-    k<<<grid, G::THREADS, smem, s>>>(a);
+    k<<<grid, G::THREADS, smem, s>>>(b);
     return cudaGetLastError();
 }
 

@@ -106,7 +106,18 @@ struct SweepArgs {
     // takes work from (zero at launch) and the number of tiles
     unsigned int* work;
     long long ntiles;
+    // FP32: load L after the faces into the staged nodes' space (only for a
+    // plain Eq. 3 node phase without a source or a fused stage; the launch
+    // then passes TileGeom::smem_bytes(true))
+    int alias_L;
 };
+
+// Whether a sweep with these arguments may share the staged nodes' space
+// with the prefetched L (see SweepArgs::alias_L).
+inline bool sweep_alias_L(const SweepArgs& a)
+{
+    return a.K.diff == DIFF_MD && !a.source && !a.fuse_stage;
+}
 
 // 4-byte asynchronous global->shared copies (cp.async): the staging loads
 // and the prefetch of the RHS being accumulated proceed while the CTA
@@ -153,10 +164,17 @@ struct TileGeom {
     // The FP32 x sweep (the last of a step's stage) can fuse the stage
     // combination: it prefetches the FP64 base state and the FP32 increment.
     static constexpr bool FUSE = sizeof(T) == 4 && DIR == 0;
-    static constexpr size_t smem_bytes()
+    // Bytes of the staged nodes, faces and (unless it shares the staged
+    // nodes' space, alias_L) the prefetched L, rounded up to 16 bytes, then
+    // the fused stage arrays.  A launch passes the size of its own layout.
+    static constexpr size_t front_bytes(bool alias_L)
     {
-        return sizeof(T) * (size_t)(ND + 2) * TL * (P + NF + (PREFETCH_L ? TS : 0)) +
-               (FUSE ? (size_t)(ND + 2) * TL * TS * (sizeof(double) + sizeof(float)) : 0);
+        return (sizeof(T) * (size_t)(ND + 2) * TL * (P + NF + (PREFETCH_L && !alias_L ? TS : 0)) + 15) &
+               ~(size_t)15;
+    }
+    static constexpr size_t smem_bytes(bool alias_L = false)
+    {
+        return front_bytes(alias_L) + (FUSE ? (size_t)(ND + 2) * TL * TS * (sizeof(double) + sizeof(float)) : 0);
     }
 };
 
@@ -496,9 +514,14 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sS = reinterpret_cast<T*>(smem_raw);
     T* sF = sS + NV * TL * P;
-    T* sL = sF + NV * TL * NF;   // prefetched L (FP32 accumulating sweeps)
+    // prefetched L (FP32 accumulating sweeps).  A sweep whose node phase
+    // needs neither the staged nodes (plain Eq. 3, no source) nor a fused
+    // stage loads L after the faces into the staged nodes' space: the tile
+    // then needs less shared memory and more CTAs fit on an SM.
+    const bool aliasL = kPre && a.alias_L != 0;
+    T* sL = aliasL ? sS : sF + NV * TL * NF;
     // fused stage combination (FP32 x sweep): prefetched base state and increment
-    double* sU0 = reinterpret_cast<double*>(sL + (G::PREFETCH_L ? NV * TL * TS : 0));
+    double* sU0 = reinterpret_cast<double*>(smem_raw + G::front_bytes(aliasL));
     float* sD = reinterpret_cast<float*>(sU0 + (G::FUSE ? NV * TL * TS : 0));
     float* sUf = reinterpret_cast<float*>(sU0);   // stage 2: float(U0) in the same space
 
@@ -579,18 +602,20 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
             return;
         }
     }
-    if constexpr (kPre) {
-        if (a.accumulate) {                    // group: the L values this tile adds to
-            const T* Lg = Lb;
-            for (int e = threadIdx.x; e < TL * TS; e += blockDim.x) {
-                int l, t;
-                if (DIR == 0) { t = e % TS; l = e / TS; } else { l = e % TL; t = e / TL; }
-                if (l >= lcount || t >= tcount) continue;
-                const T* src = Lg + base0 + l * lstride + (long long)(pos0 + t) * sd;
+    // the L values this tile adds to (cp.async into sL)
+    auto prefetch_L = [&]() {
+        const T* Lg = Lb;
+        for (int e = threadIdx.x; e < TL * TS; e += blockDim.x) {
+            int l, t;
+            if (DIR == 0) { t = e % TS; l = e / TS; } else { l = e % TL; t = e / TL; }
+            if (l >= lcount || t >= tcount) continue;
+            const T* src = Lg + base0 + l * lstride + (long long)(pos0 + t) * sd;
 #pragma unroll
-                for (int v = 0; v < NV; ++v) cp_async4(&sL[sidx<DIR, TL, TS>(v, l, t)], src + v * N);
-            }
+            for (int v = 0; v < NV; ++v) cp_async4(&sL[sidx<DIR, TL, TS>(v, l, t)], src + v * N);
         }
+    };
+    if constexpr (kPre) {
+        if (a.accumulate && !aliasL) prefetch_L();   // group: lands while the faces are computed
         if constexpr (G::FUSE) {
             if (a.fuse_stage) {
                 for (int e = threadIdx.x; e < TL * TS; e += blockDim.x) {
@@ -682,7 +707,14 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
         }
     }
     if (fb) atomicAdd((unsigned long long*)fbp, (unsigned long long)fb);
-    if constexpr (kPre) cp_async_wait<0>();    // prefetched L has landed
+    if constexpr (kPre) {
+        if (aliasL && a.accumulate) {
+            __syncthreads();                   // every face has read the staged nodes
+            prefetch_L();
+            cp_async_commit();
+        }
+        cp_async_wait<0>();                    // prefetched L has landed
+    }
     __syncthreads();
 
     // (3) Eq. 3 (or Eq. 4, 5) at nodes pos0 .. pos0 + tcount - 1.  The node
