@@ -233,6 +233,31 @@ def test_full_size_rhs_sampled_against_oracle(which):
     assert np.all(err <= RTOL * (np.abs(Lo) + S)), (err / (np.abs(Lo) + S)).max()
 
 
+def test_full_size_fp32_rhs_sampled_against_oracle():
+    """The FP32 sweeps at the benchmark's size (Taylor-Green 256^3) in the
+    tile shapes the autotuner picks for the benchmark: the RHS of a
+    developed state (two FP32 steps), at sampled nodes, within the FP32
+    bound of the small cases against the oracle's pointwise RHS of the same
+    state (rounded to FP32, as the FP32 RHS sees it)."""
+    pb = inputs.taylor_green(256)
+    s = wcns.Solver.for_problem(pb, precision=wcns.FP32)
+    Ud = torch.from_numpy(pb.U0).to(DEV)
+    s.autotune(Ud)
+    for _ in range(2):
+        s.step(Ud)
+    U32 = Ud.float()
+    U = U32.double().cpu().numpy()
+    L32 = torch.empty_like(U32)
+    s.rhs(U32, L32)
+    Lg = L32.double().cpu().numpy().reshape(pb.nv, -1)
+    s.close()
+    idx = np.unique(np.concatenate([_sample(pb.cells, 3000, 17), [0, pb.cells - 1, pb.n[0] - 1]]))
+    Lo = O.euler_rhs_at(ora_cfg(pb, wcns.FLUX_ROE), U, idx)
+    S = flux_scale(U, pb)[:, None]
+    rel = np.max(np.abs(Lg[:, idx] - Lo) / (np.abs(Lo) + S))
+    assert rel < 2e-6, rel
+
+
 # ---------------------------------------------------------------- FP32 path
 def test_fp32_rhs_close_to_oracle():
     """FP32 RHS on a smooth state: normwise relative error of a few 1e-6."""
