@@ -347,6 +347,23 @@ def ours_arm(args, world, rank, local):
         solver.step(U)
     torch.cuda.synchronize()
 
+    # e2e: the C-ABI call on a HOST state (wcns_step_rk3_host copies it in,
+    # steps, copies it out and synchronises), one call per step
+    nbytes = U.numel() * U.element_size()
+    Uh = torch.from_numpy(pb.U0.copy()).pin_memory()
+    e2e_steps = max(1, min(args.steps, 10))
+    solver.step_host(Uh)            # first call: the device copy and the step graph
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        solver.step_host(Uh)
+    e2e_el = time.perf_counter() - t0
+    e2e_el = max_over_ranks(e2e_el, world, dev)
+    e2e = {"value": whole_job_rate(nodes, 3 * e2e_steps, world, e2e_el), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes, "steps": e2e_steps, "call": "wcns_step_rk3_host (pinned host state)"}
+    solver.step(U)                  # the device state's step graph again, before the timed steps
+    torch.cuda.synchronize()
+
     uuid = None
     try:
         uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
@@ -382,31 +399,19 @@ def ours_arm(args, world, rank, local):
     traffic = profile_traffic("sweep") if fp32 else None
     w = 4 if fp32 else 8
     bytes_launch = nodes * pb.nv * w * 2 / nd
+    # measured FMA-chain throughput of this GPU, beside the derived peak
+    probe = {"fp32": wcns.alu_probe(0), "fp32_packed": wcns.alu_probe(1), "fp64": wcns.alu_probe(2)}
     roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved_tflops / peak, "traffic": traffic,
                 "kernel": "sweep_kernel (fused interpolation+flux+MD, one direction)",
                 "peak_source": "derived: %d SMs x %s x 2 flops x %.0f MHz" % (
                     pk["sms"], "128 FP32 lanes" if fp32 else "2 FP64 FMA/clk", pk["sm_max_mhz"]),
                 "flops_per_launch": flops_launch, "avg_launch_ms": avg_ms, "launches": sweep_n,
+                "alu_probe_tflops": probe,
                 "hbm": {"algorithmic_bytes_per_launch": bytes_launch,
                         "achieved_gbs": bytes_launch / (avg_ms / 1e3) / 1e9,
                         "peak_gbs": pk["hbm_gbs"], "peak_source": pk["hbm_source"],
                         "frac": bytes_launch / (avg_ms / 1e3) / 1e9 / pk["hbm_gbs"]}}
-
-    # e2e: the C-ABI call on a HOST state (wcns_step_rk3_host copies it in,
-    # steps, copies it out and synchronises), one call per step
-    Uh = torch.from_numpy(pb.U0.copy()).pin_memory()
-    e2e_steps = max(1, min(args.steps, 10))
-    solver.step_host(Uh)            # first call: the device copy and the step graph
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        solver.step_host(Uh)
-    e2e_el = time.perf_counter() - t0
-    e2e_el = max_over_ranks(e2e_el, world, dev)
-    nbytes = U.numel() * U.element_size()
-    e2e = {"value": whole_job_rate(nodes, 3 * e2e_steps, world, e2e_el), "unit": UNIT, "h2d_bytes_per_step": nbytes,
-           "d2h_bytes_per_step": nbytes, "steps": e2e_steps, "call": "wcns_step_rk3_host (pinned host state)"}
 
     # the FP64 plain path on the same workload
     fp64_line = None

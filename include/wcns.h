@@ -404,6 +404,14 @@ wcns_status wcns_scalar_run(int kind, const wcns_scheme_params* params, int n, d
                             double t_end, int nsteps, int count, double* u, long long ld,
                             void* stream);
 
+/* Arithmetic-throughput probe (a measurement utility, no counterpart in the
+ * paper): runs independent fused multiply-add chains on every SM of the
+ * current device and writes the rate reached in TFLOP/s (an FMA counts 2
+ * flops).  kind 0: FP32 fmaf; 1: packed FP32 (__ffma2_rn, two FMAs per
+ * instruction); 2: FP64 fma.  Allocates a small device buffer; synchronises
+ * the stream. */
+wcns_status wcns_alu_probe(int kind, double* tflops, void* stream);
+
 /* Number of kernel launches one wcns_step_rk3 call issues (for accounting). */
 int wcns_launches_per_step(const wcns_handle* h, int cfl_step);
 

@@ -30,7 +30,8 @@ EXTRA = {"sweep_fp32.cu": FP32_FLAGS, "sweep_fp32_cfg1.cu": FP32_FLAGS, "sweep_f
 SOURCES = ["wcns_api.cu", "wcns_rk.cu", "sweep_fp64.cu", "sweep_fp32.cu", "sweep_fp32_cfg1.cu",
            "sweep_fp32_cfg2.cu", "wcns_noalloc.cu",
            "wcns_batch.cu", "sweep_batch_fp64.cu", "sweep_batch_fp32.cu", "wcns_serve.cu",
-           "wcns_scalar.cu", "sweep_fp32_weights.cu", "sweep_fp32_weights_lin.cu", "sweep_fp32_weights_z.cu"]
+           "wcns_scalar.cu", "sweep_fp32_weights.cu", "sweep_fp32_weights_lin.cu", "sweep_fp32_weights_z.cu",
+           "wcns_probe.cu"]
 
 
 def nvcc():

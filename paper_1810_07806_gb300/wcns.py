@@ -276,6 +276,17 @@ def step_rk3_noalloc(grid, gamma, params, U, dt=0.0, want_dt=False, stream=None)
     return d.value if want_dt else None
 
 
+def alu_probe(kind, stream=None):
+    """wcns_alu_probe: TFLOP/s of FMA chains on every SM (0: FP32, 1: packed
+    FP32, 2: FP64)."""
+    L = lib()
+    L.wcns_alu_probe.argtypes = [C.c_int, C.POINTER(C.c_double), C.c_void_p]
+    L.wcns_alu_probe.restype = C.c_int
+    t = C.c_double()
+    check(L.wcns_alu_probe(int(kind), C.byref(t), _stream(stream)))
+    return t.value
+
+
 def _scalar_lines(u):
     if u.dim() == 1:
         return 1, u.shape[0], u.shape[0]
