@@ -698,12 +698,14 @@ wcns_status wcns_batch_autotune(wcns_batch* b, int steps, int* mode_out, double*
             float t = 0.f;
             if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
             ms[mode] = t / steps;
-            // restore
-            if (e == cudaSuccess) e = cudaMemcpyAsync(b->U, save, ub, cudaMemcpyDeviceToDevice, s);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(b->sc, save + ub, cb, cudaMemcpyDeviceToDevice, s);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(b->fallback, save + ub + cb, fbb, cudaMemcpyDeviceToDevice, s);
+            // restore (also after a failed trial, so the batch keeps its state)
+            const cudaError_t r1 = cudaMemcpyAsync(b->U, save, ub, cudaMemcpyDeviceToDevice, s);
+            const cudaError_t r2 = cudaMemcpyAsync(b->sc, save + ub, cb, cudaMemcpyDeviceToDevice, s);
+            const cudaError_t r3 = cudaMemcpyAsync(b->fallback, save + ub + cb, fbb, cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess) e = r1 != cudaSuccess ? r1 : (r2 != cudaSuccess ? r2 : r3);
         }
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        const cudaError_t es = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = es;
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
         cudaFree(save);
