@@ -245,10 +245,12 @@ wcns_status wcns_step_rk3_noalloc(const wcns_grid* grid, double gamma,
  * Batches (no counterpart in the paper; the method is applied unchanged to
  * every instance).  A batch advances many independent grids of one
  * dimension, precision and scheme together: each instance has its own node
- * counts, boundary rules, CFL time step and end time.  One launch per sweep
- * direction covers the tiles of all instances; one SSP-RK3 step of the
- * whole batch is captured as a CUDA graph and replayed.  An instance gives
- * the same result in a batch as alone (bit for bit in FP64).
+ * counts, boundary rules (every kind, with the fixed states and the body
+ * force), CFL time step, end time and, in FP32, reference state.  One
+ * launch per sweep direction covers the tiles of all instances; one SSP-RK3
+ * step of the whole batch is captured as a CUDA graph and replayed.  An
+ * instance gives the same result in a batch as alone, bit for bit, in FP64
+ * and in FP32 (the batched and single-grid kernels round identically).
  * --------------------------------------------------------------------- */
 typedef struct wcns_batch wcns_batch;
 
@@ -312,8 +314,8 @@ wcns_status wcns_batch_read(wcns_batch* b, int slot, double* U_out, int out_on_d
  * admitted advances together, a fixed number of RK3 steps per tick;
  * requests join and leave at step boundaries; finished states are copied
  * to the host and returned by wcns_serve_poll.  A result equals the same
- * problem solved alone (bit for bit).  The server uses the CUDA device that
- * is current when it is created.
+ * problem solved alone (bit for bit, either precision).  The server uses the
+ * CUDA device that is current when it is created.
  * --------------------------------------------------------------------- */
 typedef struct wcns_server wcns_server;
 

@@ -107,7 +107,8 @@ inline const char* grid_error(const wcns_grid* g, double gamma, GridInfo& G, cha
     return nullptr;
 }
 
-// Reflecting or fixed sides, or a body force: single-grid features.
+// Reflecting or fixed sides, or a body force (the allocation-free step does
+// not take them).
 inline bool grid_has_single_grid_features(const wcns_grid* g)
 {
     for (int a = 0; a < g->ndim && a < 3; ++a) {
