@@ -568,6 +568,67 @@ def batch_arm(args):
     sens = [rel(a, c) for a, c in zip(pert, res[wcns.FP64])]
     out["fp32"]["fp64_response_to_2^-24_input_noise"] = {"max": max(sens), "median": float(np.median(sens))}
     out["fp32"]["fp32_error_median"] = float(np.median(errs32))
+    # the smooth counterpart: 4096 density waves (N log-uniform 200..4000),
+    # FP32 batch against the FP64 batch (= the oracle) and the plain path
+    smooth = inputs.density_wave_batch(4096)
+    snodes = sum(p.cells for p in smooth)
+    b = wcns.Batch(1, max_nodes=snodes, max_instances=len(smooth), precision=wcns.FP32)
+    for pb in smooth:
+        b.add(pb, t_end=10.0)       # every instance still running in the timed steps
+    b.step(max(1, args.warmup))
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    b.step(args.steps)
+    e1.record()
+    torch.cuda.synchronize()
+    sms = e0.elapsed_time(e1) / args.steps
+    b.close()
+    ssub = smooth[:64]
+    sres = {}
+    for prec in (wcns.FP32, wcns.FP64):
+        b = wcns.Batch(1, max_nodes=sum(p.cells for p in ssub), max_instances=len(ssub), precision=prec)
+        sl = [b.add(pb) for pb in ssub]
+        b.run(check_every=64)
+        sres[prec] = [b.read(k)[0] for k in sl]
+        b.close()
+    serr = [rel(a, c) for a, c in zip(sres[wcns.FP32], sres[wcns.FP64])]
+    sol = [wcns.Solver.for_problem(pb) for pb in ssub]
+    Us = [torch.from_numpy(pb.U0.copy()).cuda() for pb in ssub]
+    for s_, U in zip(sol, Us):
+        s_.step(U)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        for s_, U in zip(sol, Us):
+            s_.step(U)
+    torch.cuda.synchronize()
+    plain_rate = sum(p.cells for p in ssub) * 3 * 3 / (time.perf_counter() - t0)
+    smooth_line = {"workload": "4096 periodic density waves, N log-uniform 200..4000, seed 1811",
+                   "fp32_batch": {"value": snodes * 3 / sms * 1e3, "ms_per_step": sms},
+                   "fp32_l1_rel_error_vs_fp64_t0.2_64_instances": {"max": max(serr),
+                                                                  "median": float(np.median(serr))},
+                   "plain_fp64_one_instance_per_launch": {"value": plain_rate}}
+    # the FP64 oracle on the same instances (all host cores over each
+    # instance's lines: one line each in 1D), a bounded sample of RK3 steps
+    cpu = None
+    if not args.no_cpu:
+        from oracle import oracle as O
+        t0 = time.perf_counter()
+        cells = 0.0
+        k = 0
+        while time.perf_counter() - t0 < 10.0 and k < len(pbs):
+            pb = pbs[k]
+            cfg = O.make_cfg(ndim=1, n=pb.n, h=pb.h)
+            U = pb.U0.copy()
+            for _ in range(5):
+                O.rk3_step(cfg, U, O.cfl_dt(cfg, U, 0.5))
+            cells += pb.cells * 3 * 5
+            k += 1
+        secs = time.perf_counter() - t0
+        cpu = {"value": cells / secs, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)),
+               "kind": "oracle", "sample": "first %d instances, 5 RK3 steps each, %.1f s" % (k, secs)}
     print(json.dumps({
         "metric": METRIC, "value": out["fp32"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": out["fp32"]["ms_per_step"], "higher_is_better": True,
@@ -579,7 +640,8 @@ def batch_arm(args):
         "fp32_l1_rel_error_vs_fp64": out["fp32"]["l1_rel_error_vs_fp64_t0.2_64_instances"],
         "fp32_l1_rel_error_median": out["fp32"]["fp32_error_median"],
         "fp64_response_to_fp32_sized_input_noise": out["fp32"]["fp64_response_to_2^-24_input_noise"],
-        "batched_fp64": out["fp64"], "plain_fp64_one_instance_per_launch": out["plain_fp64"]}))
+        "batched_fp64": out["fp64"], "plain_fp64_one_instance_per_launch": out["plain_fp64"],
+        "smooth_batch": smooth_line, "cpu_baseline": cpu}))
 
 
 def serve_replay(trace, steps_per_tick=16):

@@ -182,6 +182,26 @@ def shu_osher_batch(count=4096, seed=1810, n_lo=200, n_hi=4000, gamma=1.4):
     return [shu_osher_like(int(ns[i]), mach[i], eps[i], kk[i], gamma) for i in range(count)]
 
 
+def density_wave_batch(count=4096, seed=1811, n_lo=200, n_hi=4000, gamma=1.4, t_end=0.2):
+    """Smooth counterparts of the Shu-Osher batch, for the FP32 error where
+    no discontinuity is present: periodic [0, 1), N log-uniform in
+    [n_lo, n_hi], rho = 1 + a sin(2 pi k x + phi), a U[0.05, 0.3], k in
+    1..4, u U[0.5, 1.5], p = 1 (each an exact translation at speed u)."""
+    rng = np.random.default_rng(seed)
+    ns = np.rint(np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), count))).astype(int)
+    amp = rng.uniform(0.05, 0.3, count)
+    kk = rng.integers(1, 5, count)
+    phi = rng.uniform(0.0, 2 * np.pi, count)
+    vel = rng.uniform(0.5, 1.5, count)
+    out = []
+    for i in range(count):
+        x, _ = axis_nodes(int(ns[i]), 0.0, 1.0, True)
+        rho = 1.0 + amp[i] * np.sin(2 * np.pi * kk[i] * x + phi[i])
+        U = prim_to_cons(rho, [np.full_like(x, vel[i])], np.ones_like(x), gamma)
+        out.append(_finish("density_wave", 1, (int(ns[i]),), (0.0,), (1.0,), (1,), gamma, U, t_end))
+    return out
+
+
 # ---------------------------------------------------------------- serving trace
 @dataclass
 class Request:
