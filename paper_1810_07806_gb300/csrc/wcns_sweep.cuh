@@ -138,15 +138,16 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 // Tile shapes: lines per tile (TL) x nodes per line (TS); TL * (TS + 5) faces
 // is a multiple of the 256 threads.  Configuration 0 is the default; the
-// autotuner (FP32, 2D/3D) may pick 1 (longer pencils: fewer recomputed halo
-// faces) or 2 (whole-line x pencils, narrower y/z tiles) per direction.
+// autotuner (FP32, 2D/3D) may pick, per direction, 1 (x: 8 lines of 59, two
+// faces per thread, fewer tiles to set up; y/z: longer pencils, fewer
+// recomputed halo faces) or 2 (whole-line x pencils, narrower y/z tiles).
 constexpr int tile_lines(int nd, int dir, int cfg)
 {
-    return nd == 1 ? 1 : (dir == 0 ? (cfg == 0 ? 4 : (cfg == 1 ? 2 : 1)) : (cfg == 0 ? 16 : 8));
+    return nd == 1 ? 1 : (dir == 0 ? (cfg == 0 ? 4 : (cfg == 1 ? 8 : 1)) : (cfg == 0 ? 16 : 8));
 }
 constexpr int tile_nodes(int nd, int dir, int cfg)
 {
-    return nd == 1 ? 251 : (dir == 0 ? (cfg == 0 ? 59 : (cfg == 1 ? 123 : 251)) : (cfg == 1 ? 123 : 59));
+    return nd == 1 ? 251 : (dir == 0 ? (cfg == 0 ? 59 : (cfg == 1 ? 59 : 251)) : (cfg == 1 ? 123 : 59));
 }
 
 template <typename T, int ND, int DIR, int CFG = 0>
