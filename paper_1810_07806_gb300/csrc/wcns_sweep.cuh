@@ -159,7 +159,10 @@ struct TileGeom {
     static constexpr int THREADS = 256;
     // FP32: at most 64 registers so four CTAs share an SM.  FP64: at most 128,
     // two CTAs (measured a little faster than one CTA with 175 registers).
-    static constexpr int MIN_CTAS = sizeof(T) == 4 ? 4 : 2;
+    // The 3D FP32 x tile of 8 lines (configuration 1) needs 59 KB of shared
+    // memory with its fused stage arrays, so only 3 CTAs fit anyway: it may
+    // use 85 registers.
+    static constexpr int MIN_CTAS = sizeof(T) == 4 ? (ND == 3 && DIR == 0 && CFG == 1 ? 3 : 4) : 2;
     // FP32 sweeps that accumulate prefetch the TS nodes of L they update
     static constexpr bool PREFETCH_L = sizeof(T) == 4;
     // The FP32 x sweep (the last of a step's stage) can fuse the stage
