@@ -197,3 +197,36 @@ def test_fp32_batch_of_smooth_waves_within_1e6_of_the_oracle():
         rel = np.sum(np.abs(U - Uo), axis=1) / np.sum(np.abs(Uo), axis=1)
         assert t == pb.t_end and np.all(rel <= 1e-6), (pb.n, rel)
     b.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_3d_fp32_equals_single_grid(mode):
+    """3D FP32 batches (the deferred full-cutoff pass, the shared-memory
+    layouts of the y/z sweeps) in both launch forms: each instance equals the
+    single-grid FP32 solver bit for bit, and stays within the FP32 bounds of
+    the oracle's run (smooth Taylor-Green 1e-6; the rough state, whose jumps
+    make cut decisions sensitive to rounding, 1e-3)."""
+    pbs = [inputs.taylor_green(12), inputs.taylor_green(16), _rough3d()]
+    for p in pbs:
+        p.t_end = 0.02
+    b = wcns.Batch(3, max_nodes=sum(p.cells for p in pbs), max_instances=len(pbs), precision=wcns.FP32)
+    b.launch_mode(mode)
+    slots = [b.add(pb) for pb in pbs]
+    b.run(check_every=4)
+    for pb, k in zip(pbs, slots):
+        Ub, tb, sb = b.read(k)
+        Ua, ta, sa = _alone(pb, wcns.FP32, pb.t_end)
+        assert (tb, sb) == (ta, sa) and np.array_equal(Ub, Ua), pb.name
+        Uo = pb.U0.copy()
+        O.euler_run(O.make_cfg(ndim=3, n=pb.n, h=pb.h, periodic=pb.periodic), Uo, 0.5, pb.t_end)
+        d = np.sum(np.abs(Ub - Uo).reshape(5, -1), axis=1)
+        tot = np.sum(np.abs(Uo).reshape(5, -1), axis=1)
+        tot[1:-1] = tot[1:-1].max()
+        bound = 1e-6 if pb.name == "taylor_green" else 1e-3
+        assert np.all(d <= bound * tot), (pb.name, d / tot)
+    b.close()
+
+
+def _rough3d():
+    U = inputs.random_rough_state(3, (14, 11, 9), 31)
+    return inputs._finish("rough", 3, (14, 11, 9), (0.0,) * 3, (1.0, 1.3, 1.6), (1, 0, 1), 1.4, U, 0.0)
