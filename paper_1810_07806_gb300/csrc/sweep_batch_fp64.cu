@@ -13,7 +13,7 @@ static cudaError_t go(const SweepArgs& a, long long ntiles, cudaStream_t s, bool
     auto k = sweep_kernel<double, double, ND, DIR, FLUX, true>;
     const size_t smem = G::smem_bytes();
     if (prepare) return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    static int resident = 0;
+    static std::atomic<int> resident{0};
     return launch_tiles(k, G::THREADS, smem, a, ntiles, s, resident);
 }
 

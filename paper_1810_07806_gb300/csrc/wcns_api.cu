@@ -100,7 +100,10 @@ void wcns_default_params(wcns_scheme_params* p)
     p->eps_js = 1e-6;
 }
 
-static bool prepared_fp64[64], prepared_fp32[64];
+// Per device: the sweep kernels' shared-memory attributes are set (atomic:
+// two host threads creating their first handles at once may both set them,
+// which is harmless, without a data race).
+static std::atomic<bool> prepared_fp64[64], prepared_fp32[64];
 
 wcns_status wcns_create(const wcns_grid* g, double gamma, const wcns_scheme_params* prm,
                         wcns_handle** out)

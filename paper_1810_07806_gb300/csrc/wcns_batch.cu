@@ -445,7 +445,8 @@ cudaError_t step_sequence(wcns_batch* b, cudaStream_t s)
     return cudaGetLastError();
 }
 
-bool prepared_batch[64][2];
+// per device and precision: the batched kernels' attributes are set
+std::atomic<bool> prepared_batch[64][2];
 
 }  // namespace
 

@@ -1,6 +1,7 @@
 // wcns_internal.h -- launch interface between the C ABI and the kernels.
 #pragma once
 #include <cuda_runtime.h>
+#include <atomic>
 #include <math.h>
 #include <stdio.h>
 #include "../../include/wcns.h"
@@ -148,23 +149,26 @@ inline SchemeConst make_scheme_const(const wcns_scheme_params* p, double gamma)
 
 // Launch a batched sweep kernel k over ntiles tiles: one CTA per tile, or
 // (a.work set) the persistent form with as many CTAs as are resident on the
-// device (`resident`: a per-kernel cache, 0 until first computed).
+// device (`resident`: a per-kernel cache, 0 until first computed; atomic, so
+// host threads launching at once may both compute it, without a race).
 template <typename Kernel>
 inline cudaError_t launch_tiles(Kernel k, int threads, size_t smem, const SweepArgs& a, long long ntiles,
-                                cudaStream_t s, int& resident)
+                                cudaStream_t s, std::atomic<int>& resident)
 {
     if (ntiles <= 0) return cudaSuccess;
     long long grid = ntiles;
     if (a.work != nullptr) {
-        if (resident == 0) {
+        int res = resident.load(std::memory_order_relaxed);
+        if (res == 0) {
             int dev = 0, sms = 0, per = 0;
             cudaError_t e = cudaGetDevice(&dev);
             if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
             if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, threads, smem);
             if (e != cudaSuccess) return e;
-            resident = sms * (per > 0 ? per : 1);
+            res = sms * (per > 0 ? per : 1);
+            resident.store(res, std::memory_order_relaxed);
         }
-        if (grid > resident) grid = resident;
+        if (grid > res) grid = res;
     }
     k<<<(unsigned)grid, threads, smem, s>>>(a);
     return cudaGetLastError();
