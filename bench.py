@@ -686,7 +686,7 @@ def plain_replay(trace, fp64_reference=True, ref_max_side=1 << 30):
     equals the oracle bit for bit) is computed too, for the FP32 error."""
     import torch
     from paper_1810_07806_gb300 import wcns
-    out, ref = [], {}
+    out, ref, ref_time = [], {}, {}
     finish = 0.0
     cells = 0
     busy = 0.0
@@ -704,12 +704,14 @@ def plain_replay(trace, fp64_reference=True, ref_max_side=1 << 30):
         cells += pb.cells * 3 * steps
         out.append({"U": Uh, "steps": steps, "latency": finish - r.arrival_s, "solve_s": solve})
         if fp64_reference and r.fp32 and r.side <= ref_max_side:
+            t0 = time.perf_counter()
             s = wcns.Solver.for_problem(pb, precision=wcns.FP64, cfl=0.5)
             U = torch.from_numpy(pb.U0.copy()).cuda()
-            s.advance(U, r.t_end, check_every=64)
+            _, steps64 = s.advance(U, r.t_end, check_every=64)
             ref[k] = U.cpu().numpy()
+            ref_time[k] = (time.perf_counter() - t0, pb.cells * 3 * steps64)
             s.close()
-    return {"results": out, "busy_s": busy, "cell_updates": cells, "fp64_of_fp32": ref}
+    return {"results": out, "busy_s": busy, "cell_updates": cells, "fp64_of_fp32": ref, "fp64_time": ref_time}
 
 
 def rel_l1(a, c):
@@ -745,6 +747,18 @@ def serving_summary(trace, served, plain):
     for r, res in zip(trace, plain["results"]):
         finish = max(r.arrival_s, finish) + res["solve_s"]
     statuses = [r["status"] for r in served["results"]]
+    # the FP32 requests that have an FP64 solution: their served share of the
+    # wall time is not separable, so the comparison is the plain FP32 path
+    # and the plain FP64 path on the same requests, one at a time
+    ks = sorted(plain["fp64_time"])
+    fp32_vs_fp64 = None
+    if ks:
+        t32 = sum(plain["results"][k]["solve_s"] for k in ks)
+        c32 = sum(trace[k].problem().cells * 3 * plain["results"][k]["steps"] for k in ks)
+        t64 = sum(plain["fp64_time"][k][0] for k in ks)
+        c64 = sum(plain["fp64_time"][k][1] for k in ks)
+        fp32_vs_fp64 = {"requests": len(ks), "plain_fp32_rate": c32 / t32, "plain_fp64_rate": c64 / t64,
+                        "speedup": (c32 / t32) / (c64 / t64)}
     return {
         "served": {"value": served["cell_updates"] / served["wall_s"], "unit": UNIT,
                    "latency_s": {"p50": float(np.percentile(sl, 50)), "p99": float(np.percentile(sl, 99)),
@@ -763,6 +777,7 @@ def serving_summary(trace, served, plain):
                                       "median": float(np.median(fp32_err)) if fp32_err else None,
                                       "requests": len(fp32_err),
                                       "reference": "FP64 path, equal to the FP64 oracle bit for bit"},
+        "fp32_requests_fp32_vs_fp64_plain": fp32_vs_fp64,
         "fp64_served_equal_plain_fp64": fp64_same,
         "fp32_served_equal_plain_fp32": fp32_same,
     }
