@@ -14,7 +14,7 @@ static cudaError_t go(const SweepArgs& a, long long ntiles, cudaStream_t s, bool
     if (prepare)
         return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_bytes());
     SweepArgs b = a;
-    b.alias_L = sweep_alias_L(a) ? 1 : 0;
+    b.alias_L = sweep_alias_L(a, G::FUSE_SMEM) ? 1 : 0;
     static std::atomic<int> resident[2] = {0, 0};
     return launch_tiles(k, G::THREADS, G::smem_bytes(b.alias_L != 0), b, ntiles, s, resident[b.alias_L]);
 }

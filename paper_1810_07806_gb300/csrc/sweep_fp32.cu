@@ -19,7 +19,7 @@ static cudaError_t go(const SweepArgs& a, cudaStream_t s, bool prepare)
     if (prepare)
         return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_bytes());
     SweepArgs b = a;
-    b.alias_L = sweep_alias_L(a) ? 1 : 0;
+    b.alias_L = sweep_alias_L(a, G::FUSE_SMEM) ? 1 : 0;
     const size_t smem = G::smem_bytes(b.alias_L != 0);
     dim3 grid;
     const int nd = a.n[DIR];

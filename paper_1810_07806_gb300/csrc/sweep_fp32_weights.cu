@@ -19,7 +19,7 @@ cudaError_t go(const SweepArgs& a, cudaStream_t s, bool prepare)
     if (prepare)
         return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_bytes());
     SweepArgs b = a;
-    b.alias_L = sweep_alias_L(a) ? 1 : 0;
+    b.alias_L = sweep_alias_L(a, G::FUSE_SMEM) ? 1 : 0;
     const size_t smem = G::smem_bytes(b.alias_L != 0);
     dim3 grid;
     const int nd = a.n[DIR];
@@ -60,7 +60,7 @@ cudaError_t go_batch(const SweepArgs& a, long long ntiles, cudaStream_t s, bool 
     if (prepare)
         return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_bytes());
     SweepArgs b = a;
-    b.alias_L = sweep_alias_L(a) ? 1 : 0;
+    b.alias_L = sweep_alias_L(a, G::FUSE_SMEM) ? 1 : 0;
     static std::atomic<int> resident[2] = {0, 0};
     return launch_tiles(k, G::THREADS, G::smem_bytes(b.alias_L != 0), b, ntiles, s, resident[b.alias_L]);
 }

@@ -107,16 +107,18 @@ struct SweepArgs {
     unsigned int* work;
     long long ntiles;
     // FP32: load L after the faces into the staged nodes' space (only for a
-    // plain Eq. 3 node phase without a source or a fused stage; the launch
-    // then passes TileGeom::smem_bytes(true))
+    // plain Eq. 3 node phase without a source, and without a fused stage
+    // whose arrays the tile stages in shared memory; the launch then passes
+    // TileGeom::smem_bytes(true))
     int alias_L;
 };
 
 // Whether a sweep with these arguments may share the staged nodes' space
-// with the prefetched L (see SweepArgs::alias_L).
-inline bool sweep_alias_L(const SweepArgs& a)
+// with the prefetched L (see SweepArgs::alias_L); fuse_smem: the tile stages
+// a fused stage's arrays in shared memory (TileGeom::FUSE_SMEM).
+inline bool sweep_alias_L(const SweepArgs& a, bool fuse_smem)
 {
-    return a.K.diff == DIFF_MD && !a.source && !a.fuse_stage;
+    return a.K.diff == DIFF_MD && !a.source && (!a.fuse_stage || !fuse_smem);
 }
 
 // 4-byte asynchronous global->shared copies (cp.async): the staging loads
@@ -138,12 +140,13 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 // Tile shapes: lines per tile (TL) x nodes per line (TS); TL * (TS + 5) faces
 // is a multiple of the 256 threads.  Configuration 0 is the default; the
-// autotuner (FP32, 2D/3D) may pick, per direction, 1 (x: 8 lines of 59, two
-// faces per thread, fewer tiles to set up; y/z: longer pencils, fewer
+// autotuner (FP32, 2D/3D) may pick, per direction, 1 (x: 16 lines of 59,
+// four faces per thread, a quarter of the tiles to set up, a fused stage's
+// arrays read straight from global memory; y/z: longer pencils, fewer
 // recomputed halo faces) or 2 (whole-line x pencils, narrower y/z tiles).
 constexpr int tile_lines(int nd, int dir, int cfg)
 {
-    return nd == 1 ? 1 : (dir == 0 ? (cfg == 0 ? 4 : (cfg == 1 ? 8 : 1)) : (cfg == 0 ? 16 : 8));
+    return nd == 1 ? 1 : (dir == 0 ? (cfg == 0 ? 4 : (cfg == 1 ? 16 : 1)) : (cfg == 0 ? 16 : 8));
 }
 constexpr int tile_nodes(int nd, int dir, int cfg)
 {
@@ -159,15 +162,17 @@ struct TileGeom {
     static constexpr int THREADS = 256;
     // FP32: at most 64 registers so four CTAs share an SM.  FP64: at most 128,
     // two CTAs (measured a little faster than one CTA with 175 registers).
-    // The 3D FP32 x tile of 8 lines (configuration 1) needs 59 KB of shared
-    // memory with its fused stage arrays, so only 3 CTAs fit anyway: it may
-    // use 85 registers.
-    static constexpr int MIN_CTAS = sizeof(T) == 4 ? (ND == 3 && DIR == 0 && CFG == 1 ? 3 : 4) : 2;
+    static constexpr int MIN_CTAS = sizeof(T) == 4 ? 4 : 2;
     // FP32 sweeps that accumulate prefetch the TS nodes of L they update
     static constexpr bool PREFETCH_L = sizeof(T) == 4;
     // The FP32 x sweep (the last of a step's stage) can fuse the stage
-    // combination: it prefetches the FP64 base state and the FP32 increment.
+    // combination.  The x tiles of configuration 0 prefetch its FP64 base
+    // state and FP32 increment into shared memory; the 16-line tile
+    // (configuration 1) would then fit only 2 CTAs on an SM, so it loads them
+    // from global memory in the node phase and shares the staged nodes' space
+    // with the prefetched L.
     static constexpr bool FUSE = sizeof(T) == 4 && DIR == 0;
+    static constexpr bool FUSE_SMEM = FUSE && CFG != 1;
     // Bytes of the staged nodes, faces and (unless it shares the staged
     // nodes' space, alias_L) the prefetched L, rounded up to 16 bytes, then
     // the fused stage arrays.  A launch passes the size of its own layout.
@@ -178,7 +183,8 @@ struct TileGeom {
     }
     static constexpr size_t smem_bytes(bool alias_L = false)
     {
-        return front_bytes(alias_L) + (FUSE ? (size_t)(ND + 2) * TL * TS * (sizeof(double) + sizeof(float)) : 0);
+        return front_bytes(alias_L) +
+               (FUSE_SMEM ? (size_t)(ND + 2) * TL * TS * (sizeof(double) + sizeof(float)) : 0);
     }
 };
 
@@ -443,7 +449,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
     const LT* Ub;
     T* Lb;
     long long N;
-    int nx, ny, nd, periodic, pos0, lfirst;
+    int nx, ny, nz, nd, periodic, pos0, lfirst;
     long long outer;
     const double* dtp;
     long long* fbp = a.fallback;
@@ -474,6 +480,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
         N = I.N;
         nx = I.n[0];
         ny = I.n[1];
+        nz = I.n[2];
         nd = I.n[DIR];
         periodic = I.periodic[DIR];
         if constexpr (sizeof(T) == 8) ih = I.inv_h[DIR];
@@ -489,6 +496,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
         N = a.N;
         nx = a.n[0];
         ny = a.n[1];
+        nz = a.n[2];
         nd = a.n[DIR];
         periodic = a.periodic;
         if constexpr (sizeof(T) == 8) ih = a.inv_h;
@@ -526,7 +534,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
     T* sL = aliasL ? sS : sF + NV * TL * NF;
     // fused stage combination (FP32 x sweep): prefetched base state and increment
     double* sU0 = reinterpret_cast<double*>(smem_raw + G::front_bytes(aliasL));
-    float* sD = reinterpret_cast<float*>(sU0 + (G::FUSE ? NV * TL * TS : 0));
+    float* sD = reinterpret_cast<float*>(sU0 + (G::FUSE_SMEM ? NV * TL * TS : 0));
     float* sUf = reinterpret_cast<float*>(sU0);   // stage 2: float(U0) in the same space
 
     long long sd;
@@ -534,7 +542,10 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
     long long base0, lstride;   // base offset of local line l = base0 + l * lstride
     long long line0;            // global line index of local line 0 (for flags)
     if (DIR == 0) {
-        const int rows = (int)(N / nx);
+        // rows of x lines: the product of the other extents (a 64-bit N / nx
+        // here, once per thread and tile, was a tenth of the x sweep's
+        // instructions)
+        const int rows = ND == 1 ? 1 : (ND == 2 ? ny : ny * nz);
         sd = 1;
         lcount = min(TL, rows - lfirst);
         base0 = (long long)lfirst * nx;
@@ -594,9 +605,9 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
         }
         const LT* src = U + base0 + l * lstride + (long long)p * sd;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            if constexpr (kAsyncStage) cp_async4(&sS[sidx<DIR, TL, P>(v, l, s)], src + v * N);
-            else sS[sidx<DIR, TL, P>(v, l, s)] = stage_cvt<T>(src[v * N]);
+        for (int v = 0; v < NV; ++v, src += N) {
+            if constexpr (kAsyncStage) cp_async4(&sS[sidx<DIR, TL, P>(v, l, s)], src);
+            else sS[sidx<DIR, TL, P>(v, l, s)] = stage_cvt<T>(*src);
         }
     }
     if constexpr (kAsync) cp_async_commit();   // group: staged nodes
@@ -615,26 +626,36 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
             if (l >= lcount || t >= tcount) continue;
             const T* src = Lg + base0 + l * lstride + (long long)(pos0 + t) * sd;
 #pragma unroll
-            for (int v = 0; v < NV; ++v) cp_async4(&sL[sidx<DIR, TL, TS>(v, l, t)], src + v * N);
+            for (int v = 0; v < NV; ++v, src += N) cp_async4(&sL[sidx<DIR, TL, TS>(v, l, t)], src);
         }
     };
     if constexpr (kPre) {
         if (a.accumulate && !aliasL) prefetch_L();   // group: lands while the faces are computed
-        if constexpr (G::FUSE) {
-            if (a.fuse_stage) {
+        if constexpr (G::FUSE_SMEM) {
+            // stage 1 needs float(U0) = its own staged input; stage 2 reads
+            // float(U0) from the output buffer it then overwrites; stage 3
+            // accumulates into the FP64 state
+            if (a.fuse_stage > 1) {
+                const bool s3 = a.fuse_stage == 3;
                 for (int e = threadIdx.x; e < TL * TS; e += blockDim.x) {
                     const int t = e % TS, l = e / TS;
                     if (l >= lcount || t >= tcount) continue;
                     const long long g = base0 + l * lstride + (long long)(pos0 + t) * sd;
+                    const float* Dp = Db + g;
+                    if (s3) {
+                        const double* U0p = U0b + g;
 #pragma unroll
-                    for (int v = 0; v < NV; ++v) {
-                        // stage 1 needs float(U0) = its own staged input; stage 2 reads
-                        // float(U0) from the output buffer it then overwrites; stage 3
-                        // accumulates into the FP64 state
-                        if (a.fuse_stage == 3) cp_async8(&sU0[sidx<DIR, TL, TS>(v, l, t)], U0b + v * N + g);
-                        else if (a.fuse_stage == 2)
-                            cp_async4(&sUf[sidx<DIR, TL, TS>(v, l, t)], Sob + v * N + g);
-                        if (a.fuse_stage > 1) cp_async4(&sD[sidx<DIR, TL, TS>(v, l, t)], Db + v * N + g);
+                        for (int v = 0; v < NV; ++v, U0p += N, Dp += N) {
+                            cp_async8(&sU0[sidx<DIR, TL, TS>(v, l, t)], U0p);
+                            cp_async4(&sD[sidx<DIR, TL, TS>(v, l, t)], Dp);
+                        }
+                    } else {
+                        const float* Sp = Sob + g;
+#pragma unroll
+                        for (int v = 0; v < NV; ++v, Sp += N, Dp += N) {
+                            cp_async4(&sUf[sidx<DIR, TL, TS>(v, l, t)], Sp);
+                            cp_async4(&sD[sidx<DIR, TL, TS>(v, l, t)], Dp);
+                        }
                     }
                 }
             }
@@ -722,9 +743,10 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
     __syncthreads();
 
     // (3) Eq. 3 (or Eq. 4, 5) at nodes pos0 .. pos0 + tcount - 1.  The node
-    // loop is instantiated twice so that the Eq. 3 loop carries no trace of
-    // the node fluxes Eq. 4-5 need.
-    T* L = Lb;
+    // loop is instantiated per variant (ALT, fused stage, accumulate) so that
+    // each carries no run-time branch per variable: the Eq. 3 loop has no
+    // trace of the node fluxes Eq. 4-5 need, and a fused stage only its own
+    // reads and writes.
     const int diff = a.K.diff;
     // dt of the fused stage in FP32, converted once per thread
     float dtf = 0.f;
@@ -732,14 +754,40 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
         if (a.fuse_stage) dtf = f64_to_f32_ftz(*dtp);
     }
     // ALT: Eq. 4-5 and / or the body-force source; the plain Eq. 3 instance
-    // carries neither
-    auto node_phase = [&](auto alt_tag) {
+    // carries neither.  STAGE: the fused SSP-RK3 stage (0: none, L written).
+    // ACC: L accumulates (every direction after the first).
+    auto node_phase = [&](auto alt_tag, auto stage_tag, auto acc_tag) {
         constexpr bool ALT = decltype(alt_tag)::value;
+        constexpr int STAGE = decltype(stage_tag)::value;
+        constexpr bool ACC = decltype(acc_tag)::value;
         for (int e = threadIdx.x; e < TL * TS; e += blockDim.x) {
             int l, t;
             if (DIR == 0) { t = e % TS; l = e / TS; } else { l = e % TL; t = e / TL; }
             if (l >= lcount || t >= tcount) continue;
             const long long g = base0 + l * lstride + (long long)(pos0 + t) * sd;
+            // this node's elements of variable v: pointer + v N, advanced per variable
+            T* Lp = Lb + g;
+            float* Dp = Db + g;
+            float* Sp = Sob + g;
+            double* U0p = U0b + g;
+            // a fused stage's operands when the tile does not stage them in
+            // shared memory: loaded here, all variables at once, so that the
+            // loads overlap one another and the Eq. 3 arithmetic below
+            float fa[STAGE != 0 && !G::FUSE_SMEM ? NV : 1], fd[STAGE != 0 && !G::FUSE_SMEM ? NV : 1];
+            double fu[STAGE == 3 && !G::FUSE_SMEM ? NV : 1];
+            if constexpr (STAGE != 0 && !G::FUSE_SMEM) {
+                const float* Dq = Dp;
+                const float* Sq = Sob + g;
+                const LT* Iq = Ub + g;
+                const double* Uq = U0b + g;
+#pragma unroll
+                for (int v = 0; v < NV; ++v, Dq += N, Sq += N, Iq += N, Uq += N) {
+                    if constexpr (STAGE == 1) fa[v] = (float)*Iq;   // the staged input float(U0)
+                    if constexpr (STAGE == 2) fa[v] = *Sq;          // float(U0)
+                    if constexpr (STAGE >= 2) fd[v] = *Dq;
+                    if constexpr (STAGE == 3) fu[v] = *Uq;
+                }
+            }
             // Eq. 4-5 also difference the physical fluxes of the nodes i+-1
             // (and i+-2): d1 = f_{i+1} - f_{i-1}, d2 = f_{i+2} - f_{i-2}
             T d1[NV], d2[NV], S[NV];
@@ -778,11 +826,13 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
                         q = diff == DIFF_MD ? md_fp64(f0, f1, f2, f3, f4, f5, ih)
                                             : mul_(diff_alt_fp64(diff, f1, f2, f3, f4, d1[v], d2[v]), ih);
                     else q = md_fp64(f0, f1, f2, f3, f4, f5, ih);
-                    double lval = a.accumulate ? sub_(L[v * N + g], q) : -q;
+                    double lval;
+                    if constexpr (ACC) lval = sub_(*Lp, q);
+                    else lval = -q;
                     if constexpr (ALT) {
                         if (source && v > 0) lval = add_(lval, S[v]);   // after every direction
                     }
-                    L[v * N + g] = lval;
+                    *Lp = lval;
                 } else {
                     T fp;
                     if constexpr (!ALT)
@@ -795,49 +845,74 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
                         fp = fma(T(MND_C1), f3 - f2, fma(T(MND_C2), d1[v], T(MND_C3) * (f4 - f1)));
                     // L = -f' (first direction) or L - f'
                     T lv;
-                    if (a.accumulate) {
+                    if constexpr (ACC) {
                         if constexpr (kPre) lv = fmaf(-fp, ih, sL[sidx<DIR, TL, TS>(v, l, t)]);
-                        else lv = fmaf(-fp, ih, L[v * N + g]);
+                        else lv = fmaf(-fp, ih, *Lp);
                     } else {
                         lv = -fp * ih;
                     }
                     if constexpr (ALT) {
                         if (source) lv += S[v];
                     }
-                    if constexpr (G::FUSE) {
-                        if (a.fuse_stage) {
-                            // SSP-RK3 stage on U = U0 + D (FP64 base, FP32 increment):
-                            //   D1 = dt L;  D2 = (D1 + dt L)/4;  U0 += 2/3 (D2 + dt L)
-                            // The next stage's input is float(U0) + D; float(U0) is
-                            // this stage's staged input in stage 1 and the prefetched
-                            // output buffer in stage 2 (the step starts from float(U0)).
-                            const float dt = dtf;
-                            const long long gi = v * N + g;
-                            if (a.fuse_stage == 1) {
-                                const float dd = dt * lv;
-                                Db[gi] = dd;
-                                Sob[gi] = sS[sidx<DIR, TL, P>(v, l, t + GHOST)] + dd;
-                            } else if (a.fuse_stage == 2) {
-                                const float dd = 0.25f * fmaf(dt, lv, sD[sidx<DIR, TL, TS>(v, l, t)]);
-                                Db[gi] = dd;
-                                Sob[gi] = sUf[sidx<DIR, TL, TS>(v, l, t)] + dd;
-                            } else {
-                                // the next step's first input float(U) comes from its
-                                // time-step pass, so stage 3 writes the FP64 state only
-                                const double u0 = sU0[sidx<DIR, TL, TS>(v, l, t)];
-                                const float dd = (2.0f / 3.0f) * fmaf(dt, lv, sD[sidx<DIR, TL, TS>(v, l, t)]);
-                                U0b[gi] = u0 + f32_to_f64_ftz(dd);
-                            }
-                            continue;
-                        }
+                    // SSP-RK3 stage on U = U0 + D (FP64 base, FP32 increment):
+                    //   D1 = dt L;  D2 = (D1 + dt L)/4;  U0 += 2/3 (D2 + dt L)
+                    // The next stage's input is float(U0) + D; float(U0) is
+                    // this stage's staged input in stage 1 and the prefetched
+                    // output buffer in stage 2 (the step starts from float(U0)).
+                    if constexpr (STAGE == 1) {
+                        const float dd = dtf * lv;
+                        const float u0f = G::FUSE_SMEM ? sS[sidx<DIR, TL, P>(v, l, t + GHOST)] : fa[G::FUSE_SMEM ? 0 : v];
+                        *Dp = dd;
+                        *Sp = u0f + dd;
+                    } else if constexpr (STAGE == 2) {
+                        const float d1 = G::FUSE_SMEM ? sD[sidx<DIR, TL, TS>(v, l, t)] : fd[G::FUSE_SMEM ? 0 : v];
+                        const float u0f = G::FUSE_SMEM ? sUf[sidx<DIR, TL, TS>(v, l, t)] : fa[G::FUSE_SMEM ? 0 : v];
+                        const float dd = 0.25f * fmaf(dtf, lv, d1);
+                        *Dp = dd;
+                        *Sp = u0f + dd;
+                    } else if constexpr (STAGE == 3) {
+                        // the next step's first input float(U) comes from its
+                        // time-step pass, so stage 3 writes the FP64 state only
+                        const double u0 = G::FUSE_SMEM ? sU0[sidx<DIR, TL, TS>(v, l, t)] : fu[G::FUSE_SMEM ? 0 : v];
+                        const float d2 = G::FUSE_SMEM ? sD[sidx<DIR, TL, TS>(v, l, t)] : fd[G::FUSE_SMEM ? 0 : v];
+                        const float dd = (2.0f / 3.0f) * fmaf(dtf, lv, d2);
+                        *U0p = u0 + f32_to_f64_ftz(dd);
+                    } else {
+                        *Lp = lv;
                     }
-                    L[v * N + g] = lv;
+                }
+                Lp += N;
+                if constexpr (STAGE != 0) {
+                    Dp += N;
+                    Sp += N;
+                    U0p += N;
                 }
             }
         }
     };
-    if (diff == DIFF_MD && !source) node_phase(std::false_type{});
-    else node_phase(std::true_type{});
+    using std::integral_constant;
+    auto run_nodes = [&](auto alt_tag) {
+        if constexpr (G::FUSE) {
+            if (a.fuse_stage != 0) {
+                const bool acc = a.accumulate != 0;
+                if (a.fuse_stage == 1) {
+                    if (acc) node_phase(alt_tag, integral_constant<int, 1>{}, std::true_type{});
+                    else node_phase(alt_tag, integral_constant<int, 1>{}, std::false_type{});
+                } else if (a.fuse_stage == 2) {
+                    if (acc) node_phase(alt_tag, integral_constant<int, 2>{}, std::true_type{});
+                    else node_phase(alt_tag, integral_constant<int, 2>{}, std::false_type{});
+                } else {
+                    if (acc) node_phase(alt_tag, integral_constant<int, 3>{}, std::true_type{});
+                    else node_phase(alt_tag, integral_constant<int, 3>{}, std::false_type{});
+                }
+                return;
+            }
+        }
+        if (a.accumulate) node_phase(alt_tag, integral_constant<int, 0>{}, std::true_type{});
+        else node_phase(alt_tag, integral_constant<int, 0>{}, std::false_type{});
+    };
+    if (diff == DIFF_MD && !source) run_nodes(std::false_type{});
+    else run_nodes(std::true_type{});
 }
 
 // The sweep kernel.  Single grids and tile-table batches run one tile per
