@@ -134,6 +134,12 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem)
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
+// 16-byte copy (both addresses 16-byte aligned), cached in L2 only.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int NW>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(NW) : "memory"); }
@@ -158,6 +164,9 @@ struct TileGeom {
     static constexpr int TL = tile_lines(ND, DIR, CFG);   // lines per tile
     static constexpr int TS = tile_nodes(ND, DIR, CFG);   // nodes per line
     static constexpr int P = TS + 2 * GHOST;                          // staged nodes
+    // pitch of a staged x line: room for the 16-byte aligned start (up to 3
+    // nodes before pos0 - 5) of the vectorised staging
+    static constexpr int SP = DIR == 0 ? (P + 3 + 3) / 4 * 4 : P;
     static constexpr int NF = TS + 5;                                 // faces
     static constexpr int THREADS = 256;
     // FP32: at most 64 registers so four CTAs share an SM.  FP64: at most 128,
@@ -178,7 +187,7 @@ struct TileGeom {
     // the fused stage arrays.  A launch passes the size of its own layout.
     static constexpr size_t front_bytes(bool alias_L)
     {
-        return (sizeof(T) * (size_t)(ND + 2) * TL * (P + NF + (PREFETCH_L && !alias_L ? TS : 0)) + 15) &
+        return (sizeof(T) * (size_t)(ND + 2) * TL * (SP + NF + (PREFETCH_L && !alias_L ? TS : 0)) + 15) &
                ~(size_t)15;
     }
     static constexpr size_t smem_bytes(bool alias_L = false)
@@ -440,7 +449,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
 {
     constexpr int NV = ND + 2;
     using G = TileGeom<T, ND, DIR, CFG>;
-    constexpr int TL = G::TL, TS = G::TS, P = G::P, NF = G::NF;
+    constexpr int TL = G::TL, TS = G::TS, P = G::P, SP = G::SP, NF = G::NF;
     constexpr bool kAsyncStage = sizeof(LT) == sizeof(T) && sizeof(T) == 4;
     constexpr bool kPre = G::PREFETCH_L;
     constexpr bool kAsync = kAsyncStage || kPre;
@@ -525,7 +534,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
     }
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sS = reinterpret_cast<T*>(smem_raw);
-    T* sF = sS + NV * TL * P;
+    T* sF = sS + NV * TL * SP;
     // prefetched L (FP32 accumulating sweeps).  A sweep whose node phase
     // needs neither the staged nodes (plain Eq. 3, no source) nor a fused
     // stage loads L after the faces into the staged nodes' space: the tile
@@ -561,20 +570,19 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
     const int tcount = min(TS, nd - pos0);
     const int nfaces = tcount + 5;
 
-    // (1) stage nodes pos0-5 .. pos0+TS+4 of each line: one boundary-mapped
-    // position per (line, node) pair, then its NV variables.  Positions lie in
+    // (1) stage nodes pos0-5 .. pos0+TS+4 of each line (the node of staged
+    // position s is p = pos0 - 5 + s, boundary-mapped).  Positions lie in
     // [pos0 - 5, pos0 + TS + 5), so one conditional wrap suffices unless the
-    // periodic axis is shorter than the staged window.
+    // periodic axis is shorter than the staged window.  The staged x lines
+    // may start up to 3 positions early (soff) so that their copies are
+    // 16-byte aligned; the faces read from sSr = sS + soff.
     const LT* U = Ub;
     const bool wrap_mod = periodic && nd < P;
     // reflecting walls (ghost -1-k mirrors node k, normal momentum negated;
     // the axis has at least 5 nodes) and fixed states: synchronous copies
     const bool bc_special = bcl >= BC_REFLECTING || bch >= BC_REFLECTING;
-    for (int e = threadIdx.x; e < TL * P; e += blockDim.x) {
-        int l, s;
-        if (DIR == 0) { s = e % P; l = e / P; } else { l = e % TL; s = e / TL; }
-        if (l >= lcount) continue;
-        int p = pos0 - GHOST + s;
+    // node p of line l into staged position sm
+    auto stage_pos = [&](int l, int sm, int p) {
         if (periodic) {
             if (wrap_mod) { p %= nd; if (p < 0) p += nd; }
             else p = p < 0 ? p + nd : (p >= nd ? p - nd : p);
@@ -585,19 +593,21 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
                     const double r = v == 0 ? ref_rho : (v == NV - 1 ? ref_E : 0.0);
-                    sS[sidx<DIR, TL, P>(v, l, s)] = stage_cvt<T>(st[v] - r);
+                    sS[sidx<DIR, TL, SP>(v, l, sm)] = stage_cvt<T>(st[v] - r);
                 }
-                continue;
+                return;
             }
             if (kind == BC_REFLECTING) {
-                const int q = p < 0 ? -1 - p : 2 * nd - 1 - p;
+                // (clamped: positions past the last node a face needs, in a
+                // short final tile, would mirror to before the line's start)
+                const int q = min(max(p < 0 ? -1 - p : 2 * nd - 1 - p, 0), nd - 1);
                 const LT* src = U + base0 + l * lstride + (long long)q * sd;
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
                     const T val = stage_cvt<T>(src[v * N]);
-                    sS[sidx<DIR, TL, P>(v, l, s)] = v == 1 + DIR ? -val : val;
+                    sS[sidx<DIR, TL, SP>(v, l, sm)] = v == 1 + DIR ? -val : val;
                 }
-                continue;
+                return;
             }
             p = p < 0 ? 0 : nd - 1;   // the other side is transmissive
         } else {
@@ -606,10 +616,77 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
         const LT* src = U + base0 + l * lstride + (long long)p * sd;
 #pragma unroll
         for (int v = 0; v < NV; ++v, src += N) {
-            if constexpr (kAsyncStage) cp_async4(&sS[sidx<DIR, TL, P>(v, l, s)], src);
-            else sS[sidx<DIR, TL, P>(v, l, s)] = stage_cvt<T>(*src);
+            if constexpr (kAsyncStage) cp_async4(&sS[sidx<DIR, TL, SP>(v, l, sm)], src);
+            else sS[sidx<DIR, TL, SP>(v, l, sm)] = stage_cvt<T>(*src);
+        }
+    };
+    // 16-byte copies need x extents a multiple of 4 (every line and variable
+    // block then starts 16-byte aligned) and a 16-byte aligned state
+    bool vec4 = false;
+    if constexpr (kAsyncStage)
+        vec4 = (nx & 3) == 0 && (reinterpret_cast<unsigned long long>(Ub) & 15ull) == 0;
+    int soff = 0;
+    bool staged = false;
+    if constexpr (kAsyncStage && DIR == 0) {
+        if (vec4) {
+            // x lines: aligned chunks of 4 nodes from x0 = floor4(pos0 - 5); a
+            // chunk inside the line is one copy per variable, one at an end of
+            // the line is staged node by node
+            const int x0 = (pos0 - GHOST) & ~3;
+            soff = pos0 - GHOST - x0;
+            constexpr int NC = SP / 4;
+            for (int e = threadIdx.x; e < TL * NC; e += blockDim.x) {
+                const int c = e % NC, l = e / NC;
+                if (l >= lcount) continue;
+                const int pc = x0 + 4 * c;
+                if (pc >= 0 && pc + 4 <= nd) {
+                    const LT* src = U + base0 + l * lstride + pc;
+#pragma unroll
+                    for (int v = 0; v < NV; ++v, src += N) cp_async16(&sS[sidx<DIR, TL, SP>(v, l, 4 * c)], src);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) stage_pos(l, 4 * c + i, pc + i);
+                }
+            }
+            staged = true;
+        }
+    } else if constexpr (kAsyncStage && DIR != 0 && TL % 4 == 0) {
+        if (vec4) {
+            // y/z: the lines are x-adjacent, so four lines of a node position are
+            // one copy per variable (lcount is a multiple of 4: lfirst is a
+            // multiple of TL)
+            constexpr int TLW = TL / 4;
+            for (int e = threadIdx.x; e < TLW * P; e += blockDim.x) {
+                const int l = (e % TLW) * 4, s = e / TLW;
+                if (l >= lcount) continue;
+                int p = pos0 - GHOST + s;
+                if (!periodic && bc_special && (p < 0 || p >= nd)) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) stage_pos(l + i, s, p);
+                    continue;
+                }
+                if (periodic) {
+                    if (wrap_mod) { p %= nd; if (p < 0) p += nd; }
+                    else p = p < 0 ? p + nd : (p >= nd ? p - nd : p);
+                } else {
+                    p = min(max(p, 0), nd - 1);
+                }
+                const LT* src = U + base0 + l + (long long)p * sd;
+#pragma unroll
+                for (int v = 0; v < NV; ++v, src += N) cp_async16(&sS[sidx<DIR, TL, SP>(v, l, s)], src);
+            }
+            staged = true;
         }
     }
+    if (!staged) {
+        for (int e = threadIdx.x; e < TL * P; e += blockDim.x) {
+            int l, s;
+            if (DIR == 0) { s = e % P; l = e / P; } else { l = e % TL; s = e / TL; }
+            if (l >= lcount) continue;
+            stage_pos(l, s, pos0 - GHOST + s);
+        }
+    }
+    const T* sSr = sS + soff;
     if constexpr (kAsync) cp_async_commit();   // group: staged nodes
     if constexpr (kAsyncStage) {
         if (dtp != nullptr && f64_is_zero(*dtp)) {
@@ -683,7 +760,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
 #pragma unroll
         for (int m = 0; m < 6; ++m)
 #pragma unroll
-            for (int v = 0; v < NV; ++v) u[m][v] = sS[sidx<DIR, TL, P>(v, l, f + m)];
+            for (int v = 0; v < NV; ++v) u[m][v] = sSr[sidx<DIR, TL, SP>(v, l, f + m)];
     };
     auto store_face = [&](int l, int f, const T (&F)[NV], const uint8_t (&fl)[NV], bool fell) {
         // faces shared with the next tile are owned (counted, flagged) by it
@@ -794,16 +871,16 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
             if constexpr (ALT) {
 #pragma unroll
                 for (int v = 0; v < NV; ++v) d1[v] = d2[v] = S[v] = T(0);
-                if (diff != DIFF_MD) node_flux_diff<ND, DIR, TL, P>(sS, l, t + GHOST, 1, a.K, R, d1);
-                if (diff == DIFF_HWCNS) node_flux_diff<ND, DIR, TL, P>(sS, l, t + GHOST, 2, a.K, R, d2);
+                if (diff != DIFF_MD) node_flux_diff<ND, DIR, TL, SP>(sSr, l, t + GHOST, 1, a.K, R, d1);
+                if (diff == DIFF_HWCNS) node_flux_diff<ND, DIR, TL, SP>(sSr, l, t + GHOST, 2, a.K, R, d2);
                 if (source) {
                     // (0, rho g_a, sum_a g_a m_a), the sum from 0 in axis order
-                    T rho = sS[sidx<DIR, TL, P>(0, l, t + GHOST)];
+                    T rho = sSr[sidx<DIR, TL, SP>(0, l, t + GHOST)];
                     if constexpr (sizeof(T) == 4) rho = rho + R.rho;
                     T se = T(0);
 #pragma unroll
                     for (int b = 0; b < ND; ++b) {
-                        const T gb = T(gravp[b]), mb = sS[sidx<DIR, TL, P>(1 + b, l, t + GHOST)];
+                        const T gb = T(gravp[b]), mb = sSr[sidx<DIR, TL, SP>(1 + b, l, t + GHOST)];
                         if constexpr (sizeof(T) == 8) {
                             S[1 + b] = mul_(gb, rho);
                             se = add_(se, mul_(gb, mb));
@@ -861,7 +938,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
                     // output buffer in stage 2 (the step starts from float(U0)).
                     if constexpr (STAGE == 1) {
                         const float dd = dtf * lv;
-                        const float u0f = G::FUSE_SMEM ? sS[sidx<DIR, TL, P>(v, l, t + GHOST)] : fa[G::FUSE_SMEM ? 0 : v];
+                        const float u0f = G::FUSE_SMEM ? sSr[sidx<DIR, TL, SP>(v, l, t + GHOST)] : fa[G::FUSE_SMEM ? 0 : v];
                         *Dp = dd;
                         *Sp = u0f + dd;
                     } else if constexpr (STAGE == 2) {
