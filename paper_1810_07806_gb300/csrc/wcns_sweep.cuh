@@ -147,16 +147,16 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // Tile shapes: lines per tile (TL) x nodes per line (TS); TL * (TS + 5) faces
 // is a multiple of the 256 threads.  Configuration 0 is the default; the
 // autotuner (FP32, 2D/3D) may pick, per direction, 1 (x: 16 lines of 59,
-// four faces per thread, a quarter of the tiles to set up, a fused stage's
-// arrays read straight from global memory; y/z: longer pencils, fewer
-// recomputed halo faces) or 2 (whole-line x pencils, narrower y/z tiles).
+// four faces per thread, a quarter of the tiles to set up; y/z: longer
+// pencils, fewer recomputed halo faces) or 2 (x: 8 lines of 123, fewer
+// recomputed halo faces; y/z: narrower tiles).
 constexpr int tile_lines(int nd, int dir, int cfg)
 {
-    return nd == 1 ? 1 : (dir == 0 ? (cfg == 0 ? 4 : (cfg == 1 ? 16 : 1)) : (cfg == 0 ? 16 : 8));
+    return nd == 1 ? 1 : (dir == 0 ? (cfg == 0 ? 4 : (cfg == 1 ? 16 : 8)) : (cfg == 0 ? 16 : 8));
 }
 constexpr int tile_nodes(int nd, int dir, int cfg)
 {
-    return nd == 1 ? 251 : (dir == 0 ? (cfg == 0 ? 59 : (cfg == 1 ? 59 : 251)) : (cfg == 1 ? 123 : 59));
+    return nd == 1 ? 251 : (dir == 0 ? (cfg == 0 ? 59 : (cfg == 1 ? 59 : 123)) : (cfg == 1 ? 123 : 59));
 }
 
 template <typename T, int ND, int DIR, int CFG = 0>
@@ -175,13 +175,13 @@ struct TileGeom {
     // FP32 sweeps that accumulate prefetch the TS nodes of L they update
     static constexpr bool PREFETCH_L = sizeof(T) == 4;
     // The FP32 x sweep (the last of a step's stage) can fuse the stage
-    // combination.  The x tiles of configuration 0 prefetch its FP64 base
-    // state and FP32 increment into shared memory; the 16-line tile
-    // (configuration 1) would then fit only 2 CTAs on an SM, so it loads them
-    // from global memory in the node phase and shares the staged nodes' space
-    // with the prefetched L.
+    // combination.  The small x tiles of configuration 0 prefetch its FP64
+    // base state and FP32 increment into shared memory; the larger tiles
+    // (configurations 1 and 2) would then fit only 2 CTAs on an SM, so they
+    // load them from global memory in the node phase and share the staged
+    // nodes' space with the prefetched L.
     static constexpr bool FUSE = sizeof(T) == 4 && DIR == 0;
-    static constexpr bool FUSE_SMEM = FUSE && CFG != 1;
+    static constexpr bool FUSE_SMEM = FUSE && CFG == 0;
     // Bytes of the staged nodes, faces and (unless it shares the staged
     // nodes' space, alias_L) the prefetched L, rounded up to 16 bytes, then
     // the fused stage arrays.  A launch passes the size of its own layout.
