@@ -695,8 +695,27 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
         }
     }
     // the L values this tile adds to (cp.async into sL)
+    // y/z sweeps with 16-byte copies and a 16-byte aligned L: four x-adjacent
+    // lines of a node per copy, and four lines per thread in the Eq. 3 node
+    // phase (128-bit shared and global accesses, packed arithmetic)
+    bool vecL = false;
+    if constexpr (sizeof(T) == 4 && DIR != 0 && TL % 4 == 0)
+        vecL = vec4 && (reinterpret_cast<unsigned long long>(Lb) & 15ull) == 0;
     auto prefetch_L = [&]() {
         const T* Lg = Lb;
+        if constexpr (sizeof(T) == 4 && DIR != 0 && TL % 4 == 0) {
+            if (vecL) {
+                constexpr int TLW = TL / 4;
+                for (int e = threadIdx.x; e < TLW * TS; e += blockDim.x) {
+                    const int l = (e % TLW) * 4, t = e / TLW;
+                    if (l >= lcount || t >= tcount) continue;
+                    const T* src = Lg + base0 + l + (long long)(pos0 + t) * sd;
+#pragma unroll
+                    for (int v = 0; v < NV; ++v, src += N) cp_async16(&sL[sidx<DIR, TL, TS>(v, l, t)], src);
+                }
+                return;
+            }
+        }
         for (int e = threadIdx.x; e < TL * TS; e += blockDim.x) {
             int l, t;
             if (DIR == 0) { t = e % TS; l = e / TS; } else { l = e % TL; t = e / TL; }
@@ -837,6 +856,50 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
         constexpr bool ALT = decltype(alt_tag)::value;
         constexpr int STAGE = decltype(stage_tag)::value;
         constexpr bool ACC = decltype(acc_tag)::value;
+        if constexpr (sizeof(T) == 4 && DIR != 0 && TL % 4 == 0 && !ALT && STAGE == 0) {
+            if (vecL) {
+                // lanes = the four lines; every lane rounds as the scalar loop
+                // (the negated coefficients give -f' exactly: rounding to
+                // nearest is symmetric)
+                constexpr int TLW = TL / 4;
+                const float2 ih2 = bc2(ih), a1 = bc2(-T(MD_A1)), a2 = bc2(-T(MD_A2)), a3 = bc2(-T(MD_A3));
+                for (int e = threadIdx.x; e < TLW * TS; e += blockDim.x) {
+                    const int l = (e % TLW) * 4, t = e / TLW;
+                    if (l >= lcount || t >= tcount) continue;
+                    float4* Lp = reinterpret_cast<float4*>(Lb + base0 + l + (long long)(pos0 + t) * sd);
+                    const long long N4 = N / 4;
+#pragma unroll
+                    for (int v = 0; v < NV; ++v, Lp += N4) {
+                        float2 f[6][2];
+#pragma unroll
+                        for (int m = 0; m < 6; ++m) {
+                            const float4 q = *reinterpret_cast<const float4*>(&sF[sidx<DIR, TL, NF>(v, l, t + m)]);
+                            f[m][0] = make_float2(q.x, q.y);
+                            f[m][1] = make_float2(q.z, q.w);
+                        }
+                        float4 prev;
+                        if constexpr (ACC) {
+                            if constexpr (kPre) prev = *reinterpret_cast<const float4*>(&sL[sidx<DIR, TL, TS>(v, l, t)]);
+                            else prev = *Lp;
+                        }
+                        float2 out[2];
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const float2 nfp = fma2(a1, sub2(f[3][h], f[2][h]),
+                                                    fma2(a2, sub2(f[4][h], f[1][h]), mul2(a3, sub2(f[5][h], f[0][h]))));
+                            if constexpr (ACC) {
+                                const float2 pv = h == 0 ? make_float2(prev.x, prev.y) : make_float2(prev.z, prev.w);
+                                out[h] = fma2(nfp, ih2, pv);
+                            } else {
+                                out[h] = mul2(nfp, ih2);
+                            }
+                        }
+                        *Lp = make_float4(out[0].x, out[0].y, out[1].x, out[1].y);
+                    }
+                }
+                return;
+            }
+        }
         for (int e = threadIdx.x; e < TL * TS; e += blockDim.x) {
             int l, t;
             if (DIR == 0) { t = e % TS; l = e / TS; } else { l = e % TL; t = e / TL; }
