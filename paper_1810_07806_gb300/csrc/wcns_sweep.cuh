@@ -701,6 +701,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
     bool vecL = false;
     if constexpr (sizeof(T) == 4 && DIR != 0 && TL % 4 == 0)
         vecL = vec4 && (reinterpret_cast<unsigned long long>(Lb) & 15ull) == 0;
+    const bool diff_md = a.K.diff == DIFF_MD;
     auto prefetch_L = [&]() {
         const T* Lg = Lb;
         if constexpr (sizeof(T) == 4 && DIR != 0 && TL % 4 == 0) {
@@ -726,7 +727,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
         }
     };
     if constexpr (kPre) {
-        if (a.accumulate && !aliasL) prefetch_L();   // group: lands while the faces are computed
+        if (a.accumulate && !aliasL && !(vecL && diff_md && !source))
+            prefetch_L();                      // group: lands while the faces are computed
         if constexpr (G::FUSE_SMEM) {
             // stage 1 needs float(U0) = its own staged input; stage 2 reads
             // float(U0) from the output buffer it then overwrites; stage 3
@@ -761,6 +763,11 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
     } else if constexpr (kAsync) {
         cp_async_wait<0>();
     }
+    // the deferred-face list of step (2), emptied before this barrier
+    constexpr bool kDefer = sizeof(T) == 4 && WT == W_TENO && ND == 3;
+    __shared__ int s_slow[kDefer ? TL * NF : 1];
+    __shared__ int s_nslow;
+    if (kDefer && threadIdx.x == 0) s_nslow = 0;
     __syncthreads();
 
     // (2) midpoint fluxes of faces j + 1/2, j = pos0 - 3 + f.  3D FP32 TENO
@@ -770,10 +777,6 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
     // side by side in whole warps instead of as divergent branches (5% off
     // the Taylor-Green step).  A deferred face is evaluated twice, so where
     // cuts are frequent (shocked 1D batches: 5% slower) the single pass stays.
-    constexpr bool kDefer = sizeof(T) == 4 && WT == W_TENO && ND == 3;
-    __shared__ int s_slow[kDefer ? TL * NF : 1];
-    __shared__ int s_nslow;
-    if (kDefer && threadIdx.x == 0) s_nslow = 0;
     int fb = 0;
     auto load_face = [&](int l, int f, T (&u)[6][NV]) {
 #pragma unroll
@@ -795,7 +798,6 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
                 a.flags[((long long)k * lines + line0 + l) * (nd + 5) + j3] = fl[k];
         }
     };
-    if constexpr (kDefer) __syncthreads();   // s_nslow is set
     for (int e = threadIdx.x; e < TL * NF; e += blockDim.x) {
         int l, f;
         if (DIR == 0) { f = e % NF; l = e / NF; } else { l = e % TL; f = e / TL; }
@@ -811,9 +813,14 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
         }
         store_face(l, f, F, fl, fell);
     }
+    // synced: every face is stored and every staged node read, as of the
+    // last barrier (a tile with no deferred face needs no other barrier
+    // unless the node phase reads asynchronously copied data)
+    bool synced = false;
     if constexpr (kDefer) {
         __syncthreads();
         const int nslow = s_nslow;
+        synced = nslow == 0;
         for (int k = threadIdx.x; k < nslow; k += blockDim.x) {
             const int e = s_slow[k];
             int l, f;
@@ -829,14 +836,23 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
     }
     if (fb) atomicAdd((unsigned long long*)fbp, (unsigned long long)fb);
     if constexpr (kPre) {
-        if (aliasL && a.accumulate) {
-            __syncthreads();                   // every face has read the staged nodes
+        // the accumulated L: read straight from global memory by the y/z
+        // node phase of four lines per thread, else copied into sL
+        const bool directL = vecL && diff_md && !source;
+        bool pending = a.accumulate && !aliasL && !directL;   // prefetched before the faces
+        if constexpr (G::FUSE_SMEM) pending = pending || a.fuse_stage > 1;
+        if (aliasL && a.accumulate && !directL) {
+            if (!synced) __syncthreads();      // every face has read the staged nodes
             prefetch_L();
             cp_async_commit();
+            pending = true;
         }
-        cp_async_wait<0>();                    // prefetched L has landed
+        if (pending) {
+            cp_async_wait<0>();                // the copies have landed
+            synced = false;
+        }
     }
-    __syncthreads();
+    if (!synced) __syncthreads();
 
     // (3) Eq. 3 (or Eq. 4, 5) at nodes pos0 .. pos0 + tcount - 1.  The node
     // loop is instantiated per variant (ALT, fused stage, accumulate) so that
@@ -868,6 +884,12 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
                     if (l >= lcount || t >= tcount) continue;
                     float4* Lp = reinterpret_cast<float4*>(Lb + base0 + l + (long long)(pos0 + t) * sd);
                     const long long N4 = N / 4;
+                    // the L being accumulated, all variables loaded at once
+                    float4 pv4[ACC ? NV : 1];
+                    if constexpr (ACC) {
+#pragma unroll
+                        for (int v = 0; v < NV; ++v) pv4[v] = Lp[v * N4];
+                    }
 #pragma unroll
                     for (int v = 0; v < NV; ++v, Lp += N4) {
                         float2 f[6][2];
@@ -877,11 +899,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
                             f[m][0] = make_float2(q.x, q.y);
                             f[m][1] = make_float2(q.z, q.w);
                         }
-                        float4 prev;
-                        if constexpr (ACC) {
-                            if constexpr (kPre) prev = *reinterpret_cast<const float4*>(&sL[sidx<DIR, TL, TS>(v, l, t)]);
-                            else prev = *Lp;
-                        }
+                        const float4 prev = ACC ? pv4[v] : make_float4(0.f, 0.f, 0.f, 0.f);
                         float2 out[2];
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
