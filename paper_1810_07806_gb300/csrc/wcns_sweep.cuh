@@ -727,8 +727,9 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
         }
     };
     if constexpr (kPre) {
-        if (a.accumulate && !aliasL && !(vecL && diff_md && !source))
-            prefetch_L();                      // group: lands while the faces are computed
+        bool direct = vecL && diff_md && !source;   // as directL below
+        if constexpr (G::FUSE && !G::FUSE_SMEM) direct = direct || a.fuse_stage != 0;
+        if (a.accumulate && !aliasL && !direct) prefetch_L();   // group: lands while the faces are computed
         if constexpr (G::FUSE_SMEM) {
             // stage 1 needs float(U0) = its own staged input; stage 2 reads
             // float(U0) from the output buffer it then overwrites; stage 3
@@ -837,8 +838,10 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
     if (fb) atomicAdd((unsigned long long*)fbp, (unsigned long long)fb);
     if constexpr (kPre) {
         // the accumulated L: read straight from global memory by the y/z
-        // node phase of four lines per thread, else copied into sL
-        const bool directL = vecL && diff_md && !source;
+        // node phase of four lines per thread and by a fused stage that reads
+        // its operands from global memory, else copied into sL
+        bool directL = vecL && diff_md && !source;
+        if constexpr (G::FUSE && !G::FUSE_SMEM) directL = directL || a.fuse_stage != 0;
         bool pending = a.accumulate && !aliasL && !directL;   // prefetched before the faces
         if constexpr (G::FUSE_SMEM) pending = pending || a.fuse_stage > 1;
         if (aliasL && a.accumulate && !directL) {
@@ -931,15 +934,20 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
             // a fused stage's operands when the tile does not stage them in
             // shared memory: loaded here, all variables at once, so that the
             // loads overlap one another and the Eq. 3 arithmetic below
+            // (with the L being accumulated)
+            constexpr bool kDirectL = ACC && STAGE != 0 && !G::FUSE_SMEM;
             float fa[STAGE != 0 && !G::FUSE_SMEM ? NV : 1], fd[STAGE != 0 && !G::FUSE_SMEM ? NV : 1];
             double fu[STAGE == 3 && !G::FUSE_SMEM ? NV : 1];
+            T fl0[kDirectL ? NV : 1];
             if constexpr (STAGE != 0 && !G::FUSE_SMEM) {
                 const float* Dq = Dp;
                 const float* Sq = Sob + g;
                 const LT* Iq = Ub + g;
                 const double* Uq = U0b + g;
+                const T* Lq = Lp;
 #pragma unroll
-                for (int v = 0; v < NV; ++v, Dq += N, Sq += N, Iq += N, Uq += N) {
+                for (int v = 0; v < NV; ++v, Dq += N, Sq += N, Iq += N, Uq += N, Lq += N) {
+                    if constexpr (kDirectL) fl0[v] = *Lq;
                     if constexpr (STAGE == 1) fa[v] = (float)*Iq;   // the staged input float(U0)
                     if constexpr (STAGE == 2) fa[v] = *Sq;          // float(U0)
                     if constexpr (STAGE >= 2) fd[v] = *Dq;
@@ -1004,7 +1012,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
                     // L = -f' (first direction) or L - f'
                     T lv;
                     if constexpr (ACC) {
-                        if constexpr (kPre) lv = fmaf(-fp, ih, sL[sidx<DIR, TL, TS>(v, l, t)]);
+                        if constexpr (kDirectL) lv = fmaf(-fp, ih, fl0[kDirectL ? v : 0]);
+                        else if constexpr (kPre) lv = fmaf(-fp, ih, sL[sidx<DIR, TL, TS>(v, l, t)]);
                         else lv = fmaf(-fp, ih, *Lp);
                     } else {
                         lv = -fp * ih;
