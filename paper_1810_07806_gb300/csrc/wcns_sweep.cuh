@@ -936,19 +936,19 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
             // loads overlap one another and the Eq. 3 arithmetic below
             // (with the L being accumulated)
             constexpr bool kDirectL = ACC && STAGE != 0 && !G::FUSE_SMEM;
-            float fa[STAGE != 0 && !G::FUSE_SMEM ? NV : 1], fd[STAGE != 0 && !G::FUSE_SMEM ? NV : 1];
+            // (stage 1's float(U0), its own staged input, is still in sS: a
+            // fused stage's L is never copied there)
+            float fa[STAGE == 2 && !G::FUSE_SMEM ? NV : 1], fd[STAGE != 0 && !G::FUSE_SMEM ? NV : 1];
             double fu[STAGE == 3 && !G::FUSE_SMEM ? NV : 1];
             T fl0[kDirectL ? NV : 1];
             if constexpr (STAGE != 0 && !G::FUSE_SMEM) {
                 const float* Dq = Dp;
                 const float* Sq = Sob + g;
-                const LT* Iq = Ub + g;
                 const double* Uq = U0b + g;
                 const T* Lq = Lp;
 #pragma unroll
-                for (int v = 0; v < NV; ++v, Dq += N, Sq += N, Iq += N, Uq += N, Lq += N) {
+                for (int v = 0; v < NV; ++v, Dq += N, Sq += N, Uq += N, Lq += N) {
                     if constexpr (kDirectL) fl0[v] = *Lq;
-                    if constexpr (STAGE == 1) fa[v] = (float)*Iq;   // the staged input float(U0)
                     if constexpr (STAGE == 2) fa[v] = *Sq;          // float(U0)
                     if constexpr (STAGE >= 2) fd[v] = *Dq;
                     if constexpr (STAGE == 3) fu[v] = *Uq;
@@ -1028,7 +1028,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
                     // output buffer in stage 2 (the step starts from float(U0)).
                     if constexpr (STAGE == 1) {
                         const float dd = dtf * lv;
-                        const float u0f = G::FUSE_SMEM ? sSr[sidx<DIR, TL, SP>(v, l, t + GHOST)] : fa[G::FUSE_SMEM ? 0 : v];
+                        const float u0f = sSr[sidx<DIR, TL, SP>(v, l, t + GHOST)];
                         *Dp = dd;
                         *Sp = u0f + dd;
                     } else if constexpr (STAGE == 2) {
