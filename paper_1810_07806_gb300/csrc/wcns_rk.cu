@@ -79,34 +79,68 @@ __global__ void __launch_bounds__(256) cfl_reduce_fast_kernel(const double* __re
     float ih[ND];
 #pragma unroll
     for (int a = 0; a < ND; ++a) ih[a] = (float)(1.0 / hh.v[a]);
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
-         i += (long long)gridDim.x * blockDim.x) {
-        const double rho_d = U[i], E_d = U[(ND + 1) * N + i];
+    // one node: its wave-speed sum, and (S non-null) its float(U - U_r)
+    auto node = [&](double rho_d, const double (&mv_d)[ND], double E_d, float (&out)[ND + 2]) {
         const float rho = f64_to_f32_ftz(rho_d);
         const float ir = __frcp_rn(rho);
-        float m2 = 0.f, s = 0.f, c = 0.f;
+        float m2 = 0.f, s = 0.f;
         float vel[ND];
-        float mvs[ND];
 #pragma unroll
         for (int a = 0; a < ND; ++a) {
-            const float mv = f64_to_f32_ftz(U[(1 + a) * N + i]);
-            mvs[a] = mv;
+            const float mv = f64_to_f32_ftz(mv_d[a]);
+            out[1 + a] = mv;
             m2 = fmaf(mv, mv, m2);
             vel[a] = fabsf(mv) * ir;
         }
         const float E = f64_to_f32_ftz(E_d);
         if (S != nullptr) {
             // the first stage's input, relative to the reference state
-            S[i] = f64_to_f32_ftz(rho_d - rr);
-#pragma unroll
-            for (int a = 0; a < ND; ++a) S[(1 + a) * N + i] = mvs[a];
-            S[(ND + 1) * N + i] = f64_to_f32_ftz(E_d - er);
+            out[0] = f64_to_f32_ftz(rho_d - rr);
+            out[ND + 1] = f64_to_f32_ftz(E_d - er);
         }
         const float p = gm1 * fmaf(-0.5f * m2, ir, E);
-        c = sqrtf(gamma * p * ir);
+        const float c = sqrtf(gamma * p * ir);
 #pragma unroll
         for (int a = 0; a < ND; ++a) s = fmaf(vel[a] + c, ih[a], s);
-        m = fmaxf(m, s);
+        return s;
+    };
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    // two nodes per thread and step with 16-byte loads (8-byte stores) where
+    // the arrays allow it
+    const bool pairs = (N & 1) == 0 && (reinterpret_cast<unsigned long long>(U) & 15ull) == 0 &&
+                       (reinterpret_cast<unsigned long long>(S) & 7ull) == 0;
+    if (pairs) {
+        for (long long k = i0; k < N / 2; k += stride) {
+            const long long i = 2 * k;
+            const double2 r2 = *reinterpret_cast<const double2*>(U + i);
+            const double2 e2 = *reinterpret_cast<const double2*>(U + (ND + 1) * N + i);
+            double2 m2[ND];
+#pragma unroll
+            for (int a = 0; a < ND; ++a) m2[a] = *reinterpret_cast<const double2*>(U + (1 + a) * N + i);
+            double mx[ND], my[ND];
+#pragma unroll
+            for (int a = 0; a < ND; ++a) { mx[a] = m2[a].x; my[a] = m2[a].y; }
+            float ox[ND + 2], oy[ND + 2];
+            m = fmaxf(m, node(r2.x, mx, e2.x, ox));
+            m = fmaxf(m, node(r2.y, my, e2.y, oy));
+            if (S != nullptr) {
+#pragma unroll
+                for (int v = 0; v < ND + 2; ++v) *reinterpret_cast<float2*>(S + v * N + i) = make_float2(ox[v], oy[v]);
+            }
+        }
+    } else {
+        for (long long i = i0; i < N; i += stride) {
+            double mv[ND];
+#pragma unroll
+            for (int a = 0; a < ND; ++a) mv[a] = U[(1 + a) * N + i];
+            float o[ND + 2];
+            m = fmaxf(m, node(U[i], mv, U[(ND + 1) * N + i], o));
+            if (S != nullptr) {
+#pragma unroll
+                for (int v = 0; v < ND + 2; ++v) S[v * N + i] = o[v];
+            }
+        }
     }
     double md = (double)m * (1.0 + 1.0 / 65536.0);
     md = warp_max(md);
