@@ -176,16 +176,20 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- profiles
-def profile_traffic(kernel_tag):
+def profile_traffic(workload_name):
     """Per-launch DRAM bytes of the dominant kernel from the committed ncu
-    summary, or None when the kernel source changed since that capture."""
+    summary, or None when the kernel source changed since that capture or
+    the summary covers another workload."""
     path = os.path.join(ROOT, "profiles", "sweep_fp32_tgv.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
     m = re.search(r"traffic_bytes_per_full_launch:\s*([0-9.eE+]+)", txt)
     h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", txt)
+    w = re.search(r"traffic_workload:\s*(\S+)", txt)
     if not m or not h or h.group(1) != kernel_source_hash():
+        return None
+    if not w or w.group(1) != workload_name:
         return None
     return float(m.group(1))
 
@@ -396,7 +400,7 @@ def ours_arm(args, world, rank, local):
     flops_launch = nodes * (FACE_FLOPS[nd] + NODE_FLOPS[nd])
     achieved_tflops = flops_launch / (avg_ms / 1e3) / 1e12
     peak = pk["fp32_tflops"] if fp32 else pk["fp64_tflops"]
-    traffic = profile_traffic("sweep") if fp32 else None
+    traffic = profile_traffic(cfg["workload"]) if fp32 else None
     w = 4 if fp32 else 8
     bytes_launch = nodes * pb.nv * w * 2 / nd
     # measured FMA-chain throughput of this GPU, beside the derived peak

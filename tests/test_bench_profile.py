@@ -1,6 +1,7 @@
 """bench.py reports the dominant kernel's DRAM traffic from the committed
 ncu summary only while the summary's source hash matches the FP32 sweep's
-code: a change to the code must void it, a comment edit must not."""
+code (a change to the code must void it, a comment edit must not) and only
+on the workload the summary was captured on."""
 import os
 import shutil
 
@@ -27,12 +28,16 @@ def test_comment_edit_keeps_and_code_edit_voids_the_profile(tmp_path, monkeypatc
     prof = tmp_path / "profiles"
     prof.mkdir()
     (prof / "sweep_fp32_tgv.md").write_text(
-        "kernel_source_sha256: %s\ntraffic_bytes_per_full_launch: 1.5e9\n" % h0)
-    assert bench.profile_traffic("sweep") == 1.5e9
+        "kernel_source_sha256: %s\ntraffic_bytes_per_full_launch: 1.5e9\n"
+        "traffic_workload: taylor_green_3d_256^3_periodic\n" % h0)
+    assert bench.profile_traffic("taylor_green_3d_256^3_periodic") == 1.5e9
+    # another workload (another grid, another dimension) has no captured traffic
+    assert bench.profile_traffic("four_quadrant_riemann_2d_1024^2_lax_liu_3") is None
     f = csrc / "wcns_sweep.cuh"
     src = f.read_text()
     f.write_text(src + "\n// a comment\n\n")
     assert bench.kernel_source_hash() == h0
+    assert bench.profile_traffic("taylor_green_3d_256^3_periodic") == 1.5e9
     f.write_text(src.replace("static constexpr int THREADS = 256;", "static constexpr int THREADS = 128;", 1))
     assert bench.kernel_source_hash() != h0
-    assert bench.profile_traffic("sweep") is None
+    assert bench.profile_traffic("taylor_green_3d_256^3_periodic") is None
