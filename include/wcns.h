@@ -206,11 +206,16 @@ wcns_status wcns_autotune(wcns_handle* h, const void* U, int* chosen, void* stre
 wcns_status wcns_tile_config(wcns_handle* h, const int* set, int* get);
 
 /* Kernel timing for measurement (no counterpart in the paper).  While
- * enabled, every sweep launch of this handle is bracketed by a pair of CUDA
- * events recorded on the launch stream.  wcns_profile_read synchronises
- * those events and returns the summed duration (ms) and the number of sweep
- * launches since the last read, then clears them.  Enabling costs two
- * event records per sweep; disabled by default. */
+ * enabled, the sweep launches of each right-hand side of this handle (one
+ * per direction) are bracketed by a pair of CUDA events recorded on the
+ * launch stream: in FP32 the sweeps after the first of a right-hand side
+ * start as programmatic dependents of the previous one and overlap its last
+ * wave, so the right-hand side, not the single sweep, is what events can
+ * time.  wcns_profile_read synchronises those events and returns the summed
+ * duration (ms) and the number of sweep launches they cover since the last
+ * read (so the ratio is the average sweep launch), then clears them.
+ * Enabling costs two event records per right-hand side and disables the
+ * CUDA-graph form of steps; disabled by default. */
 wcns_status wcns_profile(wcns_handle* h, int enable);
 wcns_status wcns_profile_read(wcns_handle* h, double* sweep_ms, long long* sweep_launches);
 

@@ -111,6 +111,10 @@ struct SweepArgs {
     // whose arrays the tile stages in shared memory; the launch then passes
     // TileGeom::smem_bytes(true))
     int alias_L;
+    // launched as a programmatic dependent of the previous sweep of the same
+    // RHS: stage and compute the faces (which read only the RHS's input),
+    // then wait for that sweep before the first access to L
+    int pdl;
 };
 
 // Whether a sweep with these arguments may share the staged nodes' space
@@ -702,6 +706,14 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
     if constexpr (sizeof(T) == 4 && DIR != 0 && TL % 4 == 0)
         vecL = vec4 && (reinterpret_cast<unsigned long long>(Lb) & 15ull) == 0;
     const bool diff_md = a.K.diff == DIFF_MD;
+    // the previous sweep of this RHS has finished (and its L is visible)
+    bool dep_done = a.pdl == 0;
+    auto dep_wait = [&]() {
+        if (!dep_done) {
+            asm volatile("griddepcontrol.wait;\n" ::: "memory");
+            dep_done = true;
+        }
+    };
     auto prefetch_L = [&]() {
         const T* Lg = Lb;
         if constexpr (sizeof(T) == 4 && DIR != 0 && TL % 4 == 0) {
@@ -729,7 +741,10 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
     if constexpr (kPre) {
         bool direct = vecL && diff_md && !source;   // as directL below
         if constexpr (G::FUSE && !G::FUSE_SMEM) direct = direct || a.fuse_stage != 0;
-        if (a.accumulate && !aliasL && !direct) prefetch_L();   // group: lands while the faces are computed
+        if (a.accumulate && !aliasL && !direct) {
+            dep_wait();
+            prefetch_L();                      // group: lands while the faces are computed
+        }
         if constexpr (G::FUSE_SMEM) {
             // stage 1 needs float(U0) = its own staged input; stage 2 reads
             // float(U0) from the output buffer it then overwrites; stage 3
@@ -846,6 +861,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
         if constexpr (G::FUSE_SMEM) pending = pending || a.fuse_stage > 1;
         if (aliasL && a.accumulate && !directL) {
             if (!synced) __syncthreads();      // every face has read the staged nodes
+            dep_wait();
             prefetch_L();
             cp_async_commit();
             pending = true;
@@ -1078,6 +1094,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
         if (a.accumulate) node_phase(alt_tag, integral_constant<int, 0>{}, std::true_type{});
         else node_phase(alt_tag, integral_constant<int, 0>{}, std::false_type{});
     };
+    dep_wait();
     if (diff == DIFF_MD && !source) run_nodes(std::false_type{});
     else run_nodes(std::true_type{});
 }
@@ -1089,6 +1106,10 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
 template <typename T, typename LT, int ND, int DIR, int FLUX, bool BATCH = false, int CFG = 0, int WT = 0>
 __global__ void __launch_bounds__(256, TileGeom<T, ND, DIR, CFG>::MIN_CTAS) sweep_kernel(const SweepArgs a)
 {
+    // a sweep launched as this one's programmatic dependent may start as
+    // soon as every CTA of this grid is running (it waits for this grid's
+    // completion itself before it touches L)
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
     if constexpr (BATCH) {
         if (a.work != nullptr) {
             __shared__ long long s_tile;
