@@ -30,22 +30,7 @@ static cudaError_t go(const SweepArgs& a, cudaStream_t s, bool prepare)
         grid = dim3((a.n[0] + G::TL - 1) / G::TL, (nd + G::TS - 1) / G::TS,
                     DIR == 1 ? (ND == 3 ? a.n[2] : 1) : a.n[1]);
     }
-    if (!b.pdl) {
-        k<<<grid, G::THREADS, smem, s>>>(b);
-        return cudaGetLastError();
-    }
-    // programmatic dependent of the previous sweep on the stream
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = grid;
-    cfg.blockDim = dim3(G::THREADS);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k, b);
+    return launch_sweep_kernel(k, grid, G::THREADS, smem, s, b);
 }
 
 template <int FLUX>

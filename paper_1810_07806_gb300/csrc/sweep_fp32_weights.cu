@@ -30,8 +30,7 @@ cudaError_t go(const SweepArgs& a, cudaStream_t s, bool prepare)
         grid = dim3((a.n[0] + G::TL - 1) / G::TL, (nd + G::TS - 1) / G::TS,
                     DIR == 1 ? (ND == 3 ? a.n[2] : 1) : a.n[1]);
     }
-    k<<<grid, G::THREADS, smem, s>>>(b);
-    return cudaGetLastError();
+    return launch_sweep_kernel(k, grid, G::THREADS, smem, s, b);
 }
 
 template <int FLUX>

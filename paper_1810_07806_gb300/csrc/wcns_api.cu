@@ -242,10 +242,10 @@ static cudaError_t run_rhs(wcns_handle* h, const void* U, void* L, uint8_t* flag
                            double* U0 = nullptr, float* S_out = nullptr)
 {
     const bool fp32 = h->p.precision == WCNS_FP32;
-    // FP32 TENO sweeps after the first run as programmatic dependents of the
+    // FP32 sweeps after the first run as programmatic dependents of the
     // previous one (their staging and faces overlap its last wave); the time
     // of the whole RHS is then what the profile events can measure
-    const bool pdl = fp32 && h->p.weights == WCNS_W_TENO;
+    const bool pdl = fp32;
     cudaError_t e;
     if (h->profiling && (e = timed_event(h, s)) != cudaSuccess) return e;
     for (int k = 0; k < h->ndim; ++k) {

@@ -389,6 +389,9 @@ cudaError_t sweeps(wcns_batch* b, const void* Uin, void* L, cudaStream_t s, int 
             a.D = b->D;
             a.S_out = S_out;
         }
+        // FP32 sweeps after the first of an RHS: programmatic dependents of
+        // the previous one (as on single grids)
+        a.pdl = fp32 && k > 0;
         cudaError_t e = fp32 ? launch_sweep_batch_fp32(b->ndim, d, b->flux, a, b->ntiles[d], s)
                              : launch_sweep_batch_fp64(b->ndim, d, b->flux, a, b->ntiles[d], s);
         if (e != cudaSuccess) return e;

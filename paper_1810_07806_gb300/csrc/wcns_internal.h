@@ -147,6 +147,30 @@ inline SchemeConst make_scheme_const(const wcns_scheme_params* p, double gamma)
     return K;
 }
 
+// Launch one sweep kernel; a.pdl: as a programmatic dependent of the
+// previous kernel on the stream (the sweep waits for it before its first
+// access to L, see SweepArgs::pdl).
+template <typename Kernel>
+inline cudaError_t launch_sweep_kernel(Kernel k, dim3 grid, int threads, size_t smem, cudaStream_t s,
+                                       const SweepArgs& a)
+{
+    if (!a.pdl) {
+        k<<<grid, threads, smem, s>>>(a);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, a);
+}
+
 // Launch a batched sweep kernel k over ntiles tiles: one CTA per tile, or
 // (a.work set) the persistent form with as many CTAs as are resident on the
 // device (`resident`: a per-kernel cache, 0 until first computed; atomic, so
@@ -170,8 +194,7 @@ inline cudaError_t launch_tiles(Kernel k, int threads, size_t smem, const SweepA
         }
         if (grid > res) grid = res;
     }
-    k<<<(unsigned)grid, threads, smem, s>>>(a);
-    return cudaGetLastError();
+    return launch_sweep_kernel(k, dim3((unsigned)grid), threads, smem, s, a);
 }
 
 // Launch one sweep of direction dir, FP64 or FP32 (input and output in the
