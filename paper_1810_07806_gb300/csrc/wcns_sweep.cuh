@@ -556,7 +556,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
     long long line0;            // global line index of local line 0 (for flags)
     if (DIR == 0) {
         // rows of x lines: the product of the other extents (a 64-bit N / nx
-        // here, once per thread and tile, was a tenth of the x sweep's
+        // here, once per thread and tile, cost 1% of the x sweep's
         // instructions)
         const int rows = ND == 1 ? 1 : (ND == 2 ? ny : ny * nz);
         sd = 1;
@@ -698,7 +698,6 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
             return;
         }
     }
-    // the L values this tile adds to (cp.async into sL)
     // y/z sweeps with 16-byte copies and a 16-byte aligned L: four x-adjacent
     // lines of a node per copy, and four lines per thread in the Eq. 3 node
     // phase (128-bit shared and global accesses, packed arithmetic)
@@ -714,6 +713,12 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
             dep_done = true;
         }
     };
+    // the accumulated L: read straight from global memory by the y/z node
+    // phase of four lines per thread and by a fused stage that reads its
+    // operands from global memory, else copied into sL
+    bool directL = vecL && diff_md && !source;
+    if constexpr (G::FUSE && !G::FUSE_SMEM) directL = directL || a.fuse_stage != 0;
+    // the L values this tile adds to (cp.async into sL)
     auto prefetch_L = [&]() {
         const T* Lg = Lb;
         if constexpr (sizeof(T) == 4 && DIR != 0 && TL % 4 == 0) {
@@ -739,9 +744,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
         }
     };
     if constexpr (kPre) {
-        bool direct = vecL && diff_md && !source;   // as directL below
-        if constexpr (G::FUSE && !G::FUSE_SMEM) direct = direct || a.fuse_stage != 0;
-        if (a.accumulate && !aliasL && !direct) {
+        if (a.accumulate && !aliasL && !directL) {
             dep_wait();
             prefetch_L();                      // group: lands while the faces are computed
         }
@@ -852,11 +855,6 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, long long tile)
     }
     if (fb) atomicAdd((unsigned long long*)fbp, (unsigned long long)fb);
     if constexpr (kPre) {
-        // the accumulated L: read straight from global memory by the y/z
-        // node phase of four lines per thread and by a fused stage that reads
-        // its operands from global memory, else copied into sL
-        bool directL = vecL && diff_md && !source;
-        if constexpr (G::FUSE && !G::FUSE_SMEM) directL = directL || a.fuse_stage != 0;
         bool pending = a.accumulate && !aliasL && !directL;   // prefetched before the faces
         if constexpr (G::FUSE_SMEM) pending = pending || a.fuse_stage > 1;
         if (aliasL && a.accumulate && !directL) {
