@@ -24,6 +24,8 @@ struct NodeChunk {      // nodes [begin, begin + count) of one instance
     int inst;
     int count;
     long long begin;
+    long long off;      // the instance's element offset and node count (copies
+    long long N;        // of its BatchInst's, so the state loads need no other load)
 };
 
 struct ElemChunk {      // batch-array elements [begin, begin + count), one instance
@@ -32,7 +34,7 @@ struct ElemChunk {      // batch-array elements [begin, begin + count), one inst
     long long begin;
 };
 
-constexpr int kNodeChunk = 1024;
+constexpr int kNodeChunk = 1024;   // a multiple of the 256 threads of the time-step pass
 constexpr int kElemChunk = 4096;
 constexpr int kDtStride = (int)(sizeof(StepScalars) / sizeof(double));
 static_assert(sizeof(StepScalars) % sizeof(double) == 0, "StepScalars must be a whole number of doubles");
@@ -42,6 +44,12 @@ __device__ __forceinline__ double bwarp_max(double x)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+__device__ __forceinline__ float bwarp_maxf(float x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
     return x;
 }
 
@@ -58,16 +66,36 @@ __global__ void __launch_bounds__(256) batch_cfl_kernel(const double* __restrict
                                                         float* __restrict__ S)
 {
     const NodeChunk ch = chunks[blockIdx.x];
+    // the state of this thread's nodes (at most KU: kNodeChunk = KU x 256),
+    // loaded before anything else is waited for
+    constexpr int KU = kNodeChunk / 256;
+    const double* Ui = U + ch.off;
+    const long long N = ch.N;
+    double Uv[KU][ND + 2];
+#pragma unroll
+    for (int j = 0; j < KU; ++j) {
+        const int k = threadIdx.x + j * 256;
+        if (k < ch.count) {
+#pragma unroll
+            for (int v = 0; v < ND + 2; ++v) Uv[j][v] = Ui[v * N + ch.begin + k];
+        }
+    }
+    // the instance still runs (one FP64 compare per block, not per thread:
+    // the FP64 pipe runs at a small fraction of the FP32 rate)
     StepScalars* s = sc + ch.inst;
-    if (!(s->t < s->t_end)) return;
+    __shared__ int s_run;
+    if (threadIdx.x == 0) s_run = s->t < s->t_end;
+    __syncthreads();
+    if (!s_run) return;
     const BatchInst& I = insts[ch.inst];
-    const double* Ui = U + I.off;
-    const long long N = I.N;
     double m = 0.0;
     float mf = 0.f;
     const float gf = (float)gamma;
     const double rr = s->ref_rho, er = s->ref_E;
-    for (int k = threadIdx.x; k < ch.count; k += blockDim.x) {
+#pragma unroll
+    for (int j = 0; j < KU; ++j) {
+        const int k = threadIdx.x + j * 256;
+        if (k >= ch.count) continue;
         const long long i = ch.begin + k;
         if constexpr (FAST) {
             // the same FP32 expressions as the single-grid rule; the stage
@@ -75,10 +103,10 @@ __global__ void __launch_bounds__(256) batch_cfl_kernel(const double* __restrict
             float Uf[ND + 2];
 #pragma unroll
             for (int v = 0; v < ND + 2; ++v) {
-                const double x = Ui[v * N + i];
+                const double x = Uv[j][v];
                 Uf[v] = f64_to_f32_ftz(x);
                 const double r = v == 0 ? rr : (v == ND + 1 ? er : 0.0);
-                S[I.off + v * N + i] = (v == 0 || v == ND + 1) ? f64_to_f32_ftz(x - r) : Uf[v];
+                S[ch.off + v * N + i] = (v == 0 || v == ND + 1) ? f64_to_f32_ftz(x - r) : Uf[v];
             }
             const float ir = __frcp_rn(Uf[0]);
             float m2 = 0.f, sum = 0.f, vel[ND];
@@ -93,21 +121,32 @@ __global__ void __launch_bounds__(256) batch_cfl_kernel(const double* __restrict
             for (int a = 0; a < ND; ++a) sum = fmaf(vel[a] + c, I.inv_hf[a], sum);
             mf = fmaxf(mf, sum);
         } else {
-            double Uv[ND + 2];
-#pragma unroll
-            for (int v = 0; v < ND + 2; ++v) Uv[v] = Ui[v * N + i];
-            const double c = sqrt_(div_(mul_(gamma, pressure_exact<ND>(Uv, gm1)), Uv[0]));
+            const double c = sqrt_(div_(mul_(gamma, pressure_exact<ND>(Uv[j], gm1)), Uv[j][0]));
             double sum = 0.0;
 #pragma unroll
             for (int a = 0; a < ND; ++a) {
-                const double q = div_(add_(fabs(div_(Uv[1 + a], Uv[0])), c), I.h[a]);
+                const double q = div_(add_(fabs(div_(Uv[j][1 + a], Uv[j][0])), c), I.h[a]);
                 sum = a == 0 ? q : add_(sum, q);
             }
             m = fmax(m, sum);
         }
     }
-    // (scaling by 1 + 2^-16 is exact on a float and commutes with the max)
-    if constexpr (FAST) m = (double)mf * (1.0 + 1.0 / 65536.0);
+    if constexpr (FAST) {
+        // the maximum in FP32, scaled once by 1 + 2^-16 (exact on a float,
+        // and it commutes with the max): no FP64 work per thread
+        mf = bwarp_maxf(mf);
+        __shared__ float redf[8];
+        if ((threadIdx.x & 31) == 0) redf[threadIdx.x >> 5] = mf;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            mf = threadIdx.x < (blockDim.x >> 5) ? redf[threadIdx.x] : 0.f;
+            mf = bwarp_maxf(mf);
+            if (threadIdx.x == 0)
+                atomicMax(&s->lam_bits,
+                          (unsigned long long)__double_as_longlong((double)mf * (1.0 + 1.0 / 65536.0)));
+        }
+        return;
+    }
     m = bwarp_max(m);
     __shared__ double red[8];
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
@@ -324,7 +363,7 @@ wcns_status rebuild(wcns_batch* b)
             else build_tiles<double>(b->ndim, d, tiles[d], i, s);
         }
         for (long long k = 0; k < s.N; k += kNodeChunk)
-            nch.push_back(NodeChunk{i, (int)std::min<long long>(kNodeChunk, s.N - k), k});
+            nch.push_back(NodeChunk{i, (int)std::min<long long>(kNodeChunk, s.N - k), k, s.off, s.N});
         const long long M = (long long)b->nv * s.N;
         for (long long k = 0; k < M; k += kElemChunk)
             ech.push_back(ElemChunk{i, (int)std::min<long long>(kElemChunk, M - k), s.off + k});

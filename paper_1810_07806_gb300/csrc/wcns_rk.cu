@@ -13,6 +13,12 @@ struct InvH {
     double v[3];
 };
 
+__device__ __forceinline__ float warp_maxf(float x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
 __device__ __forceinline__ double warp_max(double x)
 {
 #pragma unroll
@@ -142,16 +148,17 @@ __global__ void __launch_bounds__(256) cfl_reduce_fast_kernel(const double* __re
             }
         }
     }
-    double md = (double)m * (1.0 + 1.0 / 65536.0);
-    md = warp_max(md);
-    __shared__ double red[8];
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = md;
+    // the maximum in FP32, scaled once by 1 + 2^-16 (exact on a float, and
+    // it commutes with the max)
+    m = warp_maxf(m);
+    __shared__ float red[8];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
     __syncthreads();
     if (threadIdx.x < 32) {
-        md = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-        md = warp_max(md);
+        m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+        m = warp_maxf(m);
         if (threadIdx.x == 0)
-            atomicMax(&sc->lam_bits, (unsigned long long)__double_as_longlong(md));
+            atomicMax(&sc->lam_bits, (unsigned long long)__double_as_longlong((double)m * (1.0 + 1.0 / 65536.0)));
     }
 }
 
