@@ -9,8 +9,8 @@ namespace wcns {
 template <int ND, int DIR, int FLUX>
 static cudaError_t go(const SweepArgs& a, long long ntiles, cudaStream_t s, bool prepare)
 {
-    using G = TileGeom<float, ND, DIR>;
-    auto k = sweep_kernel<float, float, ND, DIR, FLUX, true>;
+    using G = TileGeom<float, ND, DIR, batch_cfg<float>(ND)>;
+    auto k = sweep_kernel<float, float, ND, DIR, FLUX, true, batch_cfg<float>(ND)>;
     if (prepare)
         return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_bytes());
     SweepArgs b = a;

@@ -9,8 +9,8 @@ namespace wcns {
 template <int ND, int DIR, int FLUX>
 static cudaError_t go(const SweepArgs& a, long long ntiles, cudaStream_t s, bool prepare)
 {
-    using G = TileGeom<double, ND, DIR>;
-    auto k = sweep_kernel<double, double, ND, DIR, FLUX, true>;
+    using G = TileGeom<double, ND, DIR, batch_cfg<double>(ND)>;
+    auto k = sweep_kernel<double, double, ND, DIR, FLUX, true, batch_cfg<double>(ND)>;
     const size_t smem = G::smem_bytes();
     if (prepare) return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     static std::atomic<int> resident{0};

@@ -54,8 +54,8 @@ cudaError_t run(int nd, int dir, int flux, const SweepArgs& a, cudaStream_t s, b
 template <int ND, int DIR, int FLUX>
 cudaError_t go_batch(const SweepArgs& a, long long ntiles, cudaStream_t s, bool prepare)
 {
-    using G = TileGeom<float, ND, DIR, 0>;
-    auto k = sweep_kernel<float, float, ND, DIR, FLUX, true, 0, SWEEP_WT>;
+    using G = TileGeom<float, ND, DIR, batch_cfg<float>(ND)>;
+    auto k = sweep_kernel<float, float, ND, DIR, FLUX, true, batch_cfg<float>(ND), SWEEP_WT>;
     if (prepare)
         return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_bytes());
     SweepArgs b = a;

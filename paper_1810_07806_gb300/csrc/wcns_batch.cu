@@ -302,7 +302,7 @@ cudaError_t ensure(T*& p, size_t& cap, size_t need)
 template <typename T, int ND, int DIR>
 void add_tiles(std::vector<BatchTile>& out, int inst, const BatchSlot& s)
 {
-    using G = TileGeom<T, ND, DIR>;
+    using G = TileGeom<T, ND, DIR, batch_cfg<T>(ND)>;
     const int nd = s.n[DIR];
     const int ptiles = (nd + G::TS - 1) / G::TS;
     if (DIR == 0) {
