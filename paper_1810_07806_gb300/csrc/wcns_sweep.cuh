@@ -160,15 +160,16 @@ constexpr int tile_lines(int nd, int dir, int cfg)
 }
 constexpr int tile_nodes(int nd, int dir, int cfg)
 {
-    return nd == 1 ? (cfg == 1 ? 507 : 251)
+    return nd == 1 ? (cfg == 1 ? 1019 : 251)
                    : (dir == 0 ? (cfg == 0 ? 59 : (cfg == 1 ? 59 : 123)) : (cfg == 1 ? 123 : 59));
 }
 // The tile configuration of batched sweeps: FP32 1D batches take tiles of
-// 507 nodes (two faces per thread, half the tiles to set up: 16% off the
-// step of 4096 Shu-Osher instances), while a single 1D grid keeps 251 (a
-// grid of a few hundred nodes would otherwise run each sweep in one CTA)
-// and so do FP64 batches (bound by the FP64 pipe, 3% slower with 507); 2D
-// and 3D batches take the default.
+// 1019 nodes (four faces per thread, a quarter of the tiles to set up: 19%
+// off the step of 4096 Shu-Osher instances of 200-4000 nodes; 507 and 2043
+// measured slower), while a single 1D grid keeps 251 (a grid of a few
+// hundred nodes would otherwise run each sweep in one CTA) and so do FP64
+// batches (bound by the FP64 pipe, 3% slower with 507); 2D and 3D batches
+// take the default.
 template <typename T>
 constexpr int batch_cfg(int nd) { return nd == 1 && sizeof(T) == 4 ? 1 : 0; }
 
