@@ -147,6 +147,34 @@ inline SchemeConst make_scheme_const(const wcns_scheme_params* p, double gamma)
     return K;
 }
 
+// Invariants of every tile shape a sweep is compiled for: the TL x (TS + 5)
+// face slots fill whole passes of the CTA's threads (the face and node loops
+// stride by them), a staged x line has a 16-byte multiple pitch with room for
+// its aligned start (up to 3 nodes before pos0 - 5; y/z lines are the fast
+// index, so there TL a multiple of 4 gives the 16-byte alignment), and the
+// 16-line x tile leaves room for 4 CTAs per SM.
+template <typename T, int ND, int DIR, int CFG>
+constexpr bool tile_shape_ok()
+{
+    using G = TileGeom<T, ND, DIR, CFG>;
+    return (G::TL * G::NF) % G::THREADS == 0 &&
+           (DIR == 0 ? G::SP % 4 == 0 && G::SP >= G::P + 3 : G::SP == G::P && G::TL % 4 == 0) && G::TS >= 1 &&
+           G::TL >= 1;
+}
+template <typename T>
+constexpr bool all_tile_shapes_ok()
+{
+    return tile_shape_ok<T, 1, 0, 0>() && tile_shape_ok<T, 1, 0, 1>() &&
+           tile_shape_ok<T, 2, 0, 0>() && tile_shape_ok<T, 2, 0, 1>() && tile_shape_ok<T, 2, 0, 2>() &&
+           tile_shape_ok<T, 2, 1, 0>() && tile_shape_ok<T, 2, 1, 1>() && tile_shape_ok<T, 2, 1, 2>() &&
+           tile_shape_ok<T, 3, 0, 0>() && tile_shape_ok<T, 3, 0, 1>() && tile_shape_ok<T, 3, 0, 2>() &&
+           tile_shape_ok<T, 3, 1, 0>() && tile_shape_ok<T, 3, 1, 1>() && tile_shape_ok<T, 3, 1, 2>() &&
+           tile_shape_ok<T, 3, 2, 0>() && tile_shape_ok<T, 3, 2, 1>() && tile_shape_ok<T, 3, 2, 2>();
+}
+static_assert(all_tile_shapes_ok<float>() && all_tile_shapes_ok<double>(), "sweep tile shape invariants");
+static_assert(TileGeom<float, 3, 0, 1>::smem_bytes(true) + 4096 <= 56 * 1024,
+              "the 16-line x tile must leave room for 4 CTAs per SM");
+
 // Launch one sweep kernel; a.pdl: as a programmatic dependent of the
 // previous kernel on the stream (the sweep waits for it before its first
 // access to L, see SweepArgs::pdl).
