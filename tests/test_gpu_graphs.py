@@ -70,3 +70,23 @@ def test_advance_graph_equals_stepping():
     assert (t, n) == (t2, n2)
     assert torch.equal(U1, U2)
     s.close()
+
+
+@pytest.mark.parametrize("precision", [wcns.FP32, wcns.FP64])
+def test_profile_counts_every_sweep_launch(precision):
+    """wcns_profile_read reports the sweep launches its events cover (one
+    event pair per RHS, ndim sweeps each: the FP32 sweeps of an RHS overlap,
+    so only the whole RHS can be timed) and a positive total, then clears."""
+    pb = inputs.four_quadrant(96, ny=64)
+    s = wcns.Solver.for_problem(pb, precision=precision)
+    U = torch.from_numpy(pb.U0.copy()).to(DEV)
+    s.profile(True)
+    for _ in range(3):
+        s.step(U, 1e-4)
+    ms, n = s.profile_read()
+    assert n == 3 * 3 * pb.ndim and ms > 0.0
+    ms2, n2 = s.profile_read()
+    assert n2 == 0 and ms2 == 0.0
+    s.profile(False)
+    s.close()
+
